@@ -1,0 +1,128 @@
+"""Halo model ingredients (oracle, FP64): Sec. 4 of the paper.
+
+* Sheth-Tormen mass function f_m(m) = dn/dm with nu = (delta_c/sigma)^2
+  (Sec. 4.4, Eq. BoundinMass context).  Parameters q = 0.707, p = 0.3,
+  A from the normalisation int f(nu) dnu = 1; delta_c = 1.686.
+* Peak-background-split biases b1, b2 (Sec. 4.2.1, Eq. TidalKernel context):
+  Lagrangian b_n^L = (1/G) d^n G/d delta_b^n with delta_c -> delta_c - delta_b
+  in G(nu) = nu f(nu), then the spherical-collapse Eulerian mapping
+  b1 = 1 + b1^L, b2 = (8/21) b1^L + b2^L.
+* Regularisation at m_min (Eq. effectiveMasBias): a delta of weight alpha_0 at
+  the first mass node and the node-0 biases replaced by alpha_1, alpha_2 so
+  that the discrete consistency relations (Eq. BoundinMass) hold exactly.
+* Concentration: Duffy et al. (2008) mean-density fit c = 10.14
+  (m / 2e12)^-0.081 (1+z)^-1.01 with r_200m = (3m/(4 pi 200 rho_com))^(1/3).
+* NFW Fourier profile u(k, m) in sine/cosine integrals, u(0) = 1.
+
+Mass rule: N_M nodes m_q log-spaced over [m_min, m_max] (both included),
+trapezoid weights in ln m: omega_q = dlnm * m_q * (1/2 at both ends), so that
+int dm g(m) ~ sum_q omega_q g(m_q).
+"""
+import math
+
+import numpy as np
+from scipy.special import sici
+
+ST_Q = 0.707
+ST_P = 0.3
+DELTA_C = 1.686
+DUFFY_A = 10.14
+DUFFY_B = -0.081
+DUFFY_C = -1.01
+DUFFY_MPIVOT = 2.0e12
+DELTA_VIR = 200.0
+
+
+def st_amplitude():
+    """A such that int_0^inf f(nu) dnu = 1: A = 1/(1 + 2^-p Gamma(1/2-p)/sqrt(pi))."""
+    return 1.0 / (1.0 + 2.0 ** (-ST_P) * math.gamma(0.5 - ST_P) / math.sqrt(math.pi))
+
+
+def st_G(nu):
+    """Multiplicity G(nu) = nu f(nu) of Sheth & Tormen."""
+    nu = np.asarray(nu, dtype=np.float64)
+    qn = ST_Q * nu
+    return st_amplitude() * np.sqrt(qn / (2.0 * math.pi)) * (1.0 + qn ** (-ST_P)) * np.exp(-0.5 * qn)
+
+
+def st_dlnG_dnu(nu):
+    qn = ST_Q * nu
+    return 0.5 / nu - ST_P / (nu * (1.0 + qn ** ST_P)) - 0.5 * ST_Q
+
+
+def st_d2lnG_dnu2(nu):
+    qn = ST_Q * nu
+    return -0.5 / nu ** 2 + ST_P * (1.0 + (ST_P + 1.0) * qn ** ST_P) / (nu ** 2 * (1.0 + qn ** ST_P) ** 2)
+
+
+def st_biases(nu):
+    """Eulerian (b1, b2) from the peak-background split of G(nu)."""
+    nu = np.asarray(nu, dtype=np.float64)
+    a = st_dlnG_dnu(nu)
+    ap = st_d2lnG_dnu2(nu)
+    b1L = -2.0 * nu * a / DELTA_C
+    b2L = (a * a + ap) * 4.0 * nu * nu / DELTA_C ** 2 + a * 2.0 * nu / DELTA_C ** 2
+    return 1.0 + b1L, (8.0 / 21.0) * b1L + b2L
+
+
+def mass_nodes(n_mass, m_min, m_max):
+    """Log-spaced nodes and trapezoid weights in ln m (includes both ends)."""
+    dl = math.log(m_max / m_min) / (n_mass - 1)
+    m = m_min * np.exp(dl * np.arange(n_mass))
+    om = dl * m
+    om[0] *= 0.5
+    om[-1] *= 0.5
+    return m, om
+
+
+def mass_function(m, sigma, dlnsigma_dlnm, rho):
+    """f_m(m) = dn/dm = (rho/m^2) G(nu) d ln nu / d ln m, nu = (delta_c/sigma)^2."""
+    nu = (DELTA_C / sigma) ** 2
+    return rho / m ** 2 * st_G(nu) * (-2.0 * dlnsigma_dlnm), nu
+
+
+def regularise(m, om, fm, b1, b2, rho):
+    """Eq. effectiveMasBias on the discrete mass rule (one redshift).
+
+    Returns (f~, b1~, b2~): alpha_0 folded into node 0 so that
+    sum omega (m/rho) f~ = 1, and node-0 biases alpha_1, alpha_2 so that the
+    beta = 1 sum is 1 and the beta = 2 sum is 0 (Eq. BoundinMass).
+    """
+    mr = m / rho
+    s0 = np.sum(om * mr * fm)
+    alpha0 = (1.0 - s0) / mr[0]
+    ft = fm.copy()
+    ft[0] = fm[0] + alpha0 / om[0]
+    den = om[0] * mr[0] * ft[0]
+    a1 = (1.0 - np.sum(om[1:] * mr[1:] * fm[1:] * b1[1:])) / den
+    a2 = (0.0 - np.sum(om[1:] * mr[1:] * fm[1:] * b2[1:])) / den
+    b1t = b1.copy()
+    b2t = b2.copy()
+    b1t[0] = a1
+    b2t[0] = a2
+    return ft, b1t, b2t
+
+
+def concentration(m, z):
+    """Duffy et al. (2008) c(m, z) for the 200 x mean-density mass definition."""
+    return DUFFY_A * (np.asarray(m) / DUFFY_MPIVOT) ** DUFFY_B * (1.0 + z) ** DUFFY_C
+
+
+def r_vir(m, rho):
+    return (3.0 * np.asarray(m) / (4.0 * math.pi * DELTA_VIR * rho)) ** (1.0 / 3.0)
+
+
+def nfw_u(k, m, z, rho):
+    """Normalised Fourier transform u(k|m) of a truncated NFW profile.
+
+    u = [sin x (Si((1+c)x) - Si(x)) - sin(cx)/((1+c)x)
+         + cos x (Ci((1+c)x) - Ci(x))] / (ln(1+c) - c/(1+c)),  x = k r_s.
+    scipy.special.sici is the Si/Ci step.
+    """
+    c = concentration(m, z)
+    rs = r_vir(m, rho) / c
+    x = np.asarray(k, dtype=np.float64) * rs
+    si1, ci1 = sici(x)
+    si2, ci2 = sici((1.0 + c) * x)
+    num = np.sin(x) * (si2 - si1) - np.sin(c * x) / ((1.0 + c) * x) + np.cos(x) * (ci2 - ci1)
+    return num / (np.log(1.0 + c) - c / (1.0 + c))

@@ -1,0 +1,65 @@
+"""Synthetic Euclid-like workloads (parameters only; no arithmetic of the method).
+
+Both the CUDA path and the CPU oracle are driven from these dictionaries.
+They stand in for the Euclid-like survey of the paper's Appendix A with the
+cosmology and binning of the benchmark configurations:
+
+* ``cfg1_1bin``  1 tomographic bin, 8 log ell bins in [20, 3000], N_chi = 64,
+  N_M = 64, Gaussian + 1-halo terms only.
+* ``cfg2_5bin``  5 equipopulated bins with photo-z scatter 0.05 (1+z), 12 log
+  ell bins in [10, 5000], N_chi = 128, N_M = 96, every covariance term.
+* ``cfg3_10bin`` 10 equipopulated bins (same n(z) and photo-z), 20 log ell
+  bins in [10, 5000], N_chi = 256, N_M = 128, every term.
+* ``tiny_*`` / ``mid_*`` small cases that the oracle finishes in seconds but
+  that still span several kernel tiles and a ragged tail.
+
+Fixed choices where the configurations are silent: Omega_b = 0.049,
+T_CMB = 2.7255 K, w0 = -1, k_max = 50 h/Mpc, m in [1e10, 1e16] Msun/h.
+"""
+import copy
+
+TERM_G = 1
+TERM_1H = 2
+TERM_BBPT = 4
+TERM_PB = 8
+TERM_SSC = 16
+TERMS_ALL = 31
+
+FIDUCIAL = dict(Om=0.31, Ob=0.049, h=0.68, ns=0.96, sigma8=0.83, w0=-1.0, Tcmb=2.7255)
+
+
+def _nz(n_tomo, photoz):
+    return dict(n_tomo=n_tomo, z0=0.636, alpha=1.5, zmin=0.0, zmax=3.0,
+                photoz_sigma0=photoz, n_gal_arcmin2=30.0, sigma_e=0.3)
+
+
+def _bins(n_ell, ell_min, ell_max, n_chi, n_mass):
+    return dict(n_ell=n_ell, ell_min=ell_min, ell_max=ell_max, f_sky=0.36,
+                n_chi=n_chi, n_mass=n_mass, m_min=1.0e10, m_max=1.0e16, k_max=50.0)
+
+
+def _wl(name, n_tomo, photoz, n_ell, ell_min, ell_max, n_chi, n_mass, terms):
+    return dict(name=name, cosmology=dict(FIDUCIAL), nz=_nz(n_tomo, photoz),
+                bins=_bins(n_ell, ell_min, ell_max, n_chi, n_mass), terms=terms)
+
+
+WORKLOADS = {
+    "cfg1_1bin": _wl("cfg1_1bin", 1, 0.0, 8, 20.0, 3000.0, 64, 64, TERM_G | TERM_1H),
+    "cfg2_5bin": _wl("cfg2_5bin", 5, 0.05, 12, 10.0, 5000.0, 128, 96, TERMS_ALL),
+    "cfg3_10bin": _wl("cfg3_10bin", 10, 0.05, 20, 10.0, 5000.0, 256, 128, TERMS_ALL),
+    # small cases for element-by-element parity of whole matrices
+    "tiny_2bin": _wl("tiny_2bin", 2, 0.05, 5, 100.0, 800.0, 16, 12, TERMS_ALL),
+    "mid_2bin": _wl("mid_2bin", 2, 0.0, 8, 20.0, 3000.0, 40, 36, TERMS_ALL),
+    "mid_3bin": _wl("mid_3bin", 3, 0.05, 6, 30.0, 4000.0, 48, 40, TERMS_ALL),
+}
+
+
+def get(name, **overrides):
+    """A deep copy of a named workload, with top-level or nested overrides."""
+    wl = copy.deepcopy(WORKLOADS[name])
+    for key, val in overrides.items():
+        if isinstance(val, dict):
+            wl[key].update(val)
+        else:
+            wl[key] = val
+    return wl
