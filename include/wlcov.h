@@ -1,0 +1,148 @@
+/*
+ * wlcov.h -- C ABI of the GB300 library for the joint tomographic weak-lensing
+ * power spectrum + bispectrum covariance (Rizzato, Benabed, Bernardeau &
+ * Lacasa, arXiv:1812.07437).
+ *
+ * One handle holds every device-resident table for one survey set-up
+ * (cosmology, source distribution, binning).  All device pointers passed in
+ * are caller-owned CUDA device memory; the handle owns its internal tables
+ * and workspaces.  Calls taking a stream are ordered on that stream
+ * (``stream`` is a cudaStream_t passed as void*, NULL = legacy default
+ * stream).  A handle is not thread-safe: use one handle per host thread /
+ * stream.
+ *
+ * Every call returns COV_OK (0) or a negative COV_ERR_* code; the message of
+ * the last failure is available from cov_last_error().  No call aborts the
+ * process; device-side failures (a non-positive pivot) are reported through a
+ * device status word read back by the call that needs it.
+ *
+ * Matrix layout: covariance matrices are dense FP64, row-major, M x M with a
+ * leading dimension ldc >= M; only the lower triangle (row >= column) is
+ * written by cov_assemble and read by cov_snr.
+ */
+#ifndef WLCOV_H
+#define WLCOV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define COV_OK 0
+#define COV_ERR_INVALID (-1) /* bad argument or size                        */
+#define COV_ERR_NOMEM (-2)   /* device allocation failed / over hbm_budget   */
+#define COV_ERR_NOT_PD (-3)  /* Cholesky met a non-positive pivot            */
+#define COV_ERR_TIMEOUT (-4) /* a bounded device wait gave up                */
+#define COV_ERR_CUDA (-5)    /* any other CUDA runtime error                 */
+
+/* covariance terms (bitmask), Sec. 3.2 and Appendix B of the paper */
+#define COV_TERM_G 1u    /* Gaussian PP (Eq. CovPPG) and BB (App. B)          */
+#define COV_TERM_1H 2u   /* 1-halo 4/5/6-point (Eqs. CovPPNG, Ins5P, Ins6P)   */
+#define COV_TERM_BBPT 4u /* BB and PT products (Eq. CovBB)                    */
+#define COV_TERM_PB 8u   /* PB products (Eq. Covpb)                           */
+#define COV_TERM_SSC 16u /* super-sample term (Eq. WLSSCflatskyLimber)        */
+#define COV_TERMS_ALL 31u
+
+/* arithmetic of the (chi, M) contractions */
+#define COV_FP64 0       /* plain FP64 on CUDA cores                          */
+#define COV_SPLIT_BF16 1 /* tcgen05 tensor cores, A = hi + lo in BF16, FP32 acc */
+
+/* selection for the signal-to-noise (Sec. 5, Eq. eq:SN2) */
+#define COV_WHICH_P 0
+#define COV_WHICH_B 1
+#define COV_WHICH_JOINT 2
+
+/* flat w0-CDM cosmology, c = 1, lengths in Mpc/h (Sec. 1) */
+typedef struct {
+  double Om, Ob, h, ns, sigma8, w0, Tcmb;
+} cov_cosmology;
+
+/* source distribution n(z) ~ z^2 exp(-(z/z0)^alpha) split into n_tomo
+ * equipopulated bins with Gaussian photo-z scatter photoz_sigma0 (1+z)
+ * (Sec. 2, Appendix A); shape noise sigma_e with n_gal_arcmin2 sources per
+ * arcmin^2 in total (Eq. ShotNoise).  alpha must be 1.5. */
+typedef struct {
+  int n_tomo;
+  double z0, alpha, zmin, zmax, photoz_sigma0, n_gal_arcmin2, sigma_e;
+} cov_nz;
+
+/* n_ell log-spaced ell bins on [ell_min, ell_max] (Sec. 3.2.1, App. A), sky
+ * fraction f_sky, n_chi Gauss-Legendre line-of-sight nodes, n_mass log mass
+ * nodes on [m_min, m_max] Msun/h, 3D cut k_max h/Mpc (Sec. 4.4). */
+typedef struct {
+  int n_ell;
+  double ell_min, ell_max, f_sky;
+  int n_chi, n_mass;
+  double m_min, m_max, k_max;
+} cov_bins;
+
+typedef struct {
+  int device;        /* CUDA device ordinal                                  */
+  size_t hbm_budget; /* bytes the handle may allocate; 0 = no limit          */
+} cov_opts;
+
+typedef struct cov_handle cov_handle;
+
+/* Plan the data vector (layout of Sec. 5), allocate the device tables and
+ * build every table of the path for this cosmology: background, growth,
+ * P_lin, halo mass function, biases and regularisation (Sec. 4), NFW
+ * profiles on the Limber grid k = l/chi, lensing kernels (Eqs.
+ * KernelLensing1, LensEff), sigma_W^2 (App. B) and the exact integer mode and
+ * triangle counts.  Synchronous.  *out receives the handle (NULL on error). */
+int cov_init(const cov_cosmology* cosmo, const cov_nz* nz, const cov_bins* bins,
+             const cov_opts* opts, cov_handle** out);
+
+/* Rebuild every cosmology-dependent table (and the counts) for a new
+ * cosmology without reallocation; stream-ordered. */
+int cov_update(cov_handle* h, const cov_cosmology* cosmo, void* stream);
+
+/* Sizes of the joint data vector D = {P, B} (Eq. eq:SN2): M = n_P + n_B,
+ * and the number of closed bin triples.  row_desc, if not NULL, receives
+ * M x 8 int32 host values: type (0 = P, 1 = B), three ell bins, three
+ * tomographic bins (the P rows repeat the first bin and leave the third
+ * tomographic slot -1), triple index (or the ell bin for P rows). */
+int cov_layout(const cov_handle* h, int64_t* M, int64_t* n_P, int64_t* n_B, int64_t* n_tri,
+               int32_t* row_desc);
+
+/* Copy the exact integer counts to host memory: N(l^b) for the n_ell bins
+ * (Eq. PSest) and N_tri for the n_tri closed triples (App. B, first
+ * equality of the N_tri definition).  Synchronises the stream. */
+int cov_counts(cov_handle* h, int64_t* N_ell, int64_t* N_tri, void* stream);
+
+/* Predict the data vector: d_D[M] (device) receives P_ij(l) (Eqs.
+ * nProjection, PspHMtot2) and B_ijk(l1,l2,l3) (Eq. BspHMtot) in the layout
+ * order, without shot noise.  Also prepares the projected spectra the
+ * covariance needs. */
+int cov_spectra(cov_handle* h, double* d_D, void* stream);
+
+/* Assemble the lower triangle of the joint covariance into d_C (device,
+ * M x M, leading dimension ldc) as the sum of the selected terms.
+ * precision selects the arithmetic of the 1-halo (chi, M) contraction
+ * (COV_FP64 or COV_SPLIT_BF16); every other term is FP64.  Requires a
+ * preceding cov_spectra on the same handle. */
+int cov_assemble(cov_handle* h, double* d_C, int64_t ldc, unsigned terms, int precision, void* stream);
+
+/* Cumulative signal-to-noise (Eqs. SNprim, eq:SN): h_snr[c] (host, n_ell
+ * values) = sqrt(D^T C^-1 D) over the selected entries whose largest ell bin
+ * is <= c, via a Jacobi-scaled FP64 Cholesky of a workspace copy (d_C is not
+ * modified).  Returns COV_ERR_NOT_PD on a non-positive pivot.  Synchronises
+ * the stream. */
+int cov_snr(cov_handle* h, const double* d_C, int64_t ldc, const double* d_D, int which,
+            double* h_snr, void* stream);
+
+/* Copy an internal FP64 table to host memory for inspection (tests).  name is
+ * one of "chi", "wchi", "z", "growth", "mass", "f", "b1", "b2", "U", "Plin",
+ * "dPlin", "W", "sigw2", "P3", "RP3", "B3", "RB3", "B1h3", "Ps", "B1h";
+ * *count receives the number of doubles (pass host = NULL to query). */
+int cov_table(cov_handle* h, const char* name, double* host, int64_t* count, void* stream);
+
+const char* cov_last_error(const cov_handle* h);
+void cov_free(cov_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WLCOV_H */

@@ -1,0 +1,346 @@
+// C ABI of libwlcov: host-side planning (binning, data-vector layout of the
+// paper's Sec. 5, lattice thresholds), device allocation and stage dispatch.
+// All arithmetic of the method runs in the device kernels of the other
+// translation units.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+
+#include "common.cuh"
+
+int wl_fail(cov_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+int wl_cuda(cov_handle* h, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();
+  if (e == cudaErrorMemoryAllocation) return wl_fail(h, COV_ERR_NOMEM, m);
+  return wl_fail(h, COV_ERR_CUDA, m);
+}
+
+static thread_local std::string g_init_err;
+
+static int dalloc(cov_handle* h, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 8;
+  if (h->budget && h->allocated + bytes > h->budget) return wl_fail(h, COV_ERR_NOMEM, "hbm_budget exceeded");
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return wl_cuda(h, e, "cudaMalloc");
+  }
+  h->allocated += bytes;
+  return COV_OK;
+}
+
+static void tomo_triples(int a, int b, int c, int nt, std::vector<int>& out) {
+  out.clear();
+  for (int i = 0; i < nt; ++i)
+    for (int j = 0; j < nt; ++j)
+      for (int k = 0; k < nt; ++k) {
+        bool ok;
+        if (a == b && b == c)
+          ok = i <= j && j <= k;
+        else if (a == b)
+          ok = i <= j;
+        else if (b == c)
+          ok = j <= k;
+        else
+          ok = true;
+        if (ok) {
+          out.push_back(i);
+          out.push_back(j);
+          out.push_back(k);
+        }
+      }
+}
+
+static int plan(cov_handle* h) {
+  const cov_bins& b = h->bins;
+  const cov_nz& nz = h->nz;
+  h->nl = b.n_ell;
+  h->nt = nz.n_tomo;
+  h->nchi = b.n_chi;
+  h->nm = b.n_mass;
+  h->K = b.n_chi * b.n_mass;
+  // ell bins: log-spaced edges, centre = (lo + hi)/2, width = hi - lo
+  double r = b.ell_max / b.ell_min;
+  h->ell_edges.resize(h->nl + 1);
+  for (int i = 0; i <= h->nl; ++i) h->ell_edges[i] = b.ell_min * pow(r, (double)i / h->nl);
+  h->ell.resize(h->nl);
+  h->dell.resize(h->nl);
+  for (int i = 0; i < h->nl; ++i) {
+    h->ell[i] = 0.5 * (h->ell_edges[i] + h->ell_edges[i + 1]);
+    h->dell[i] = h->ell_edges[i + 1] - h->ell_edges[i];
+  }
+  // closed triples, l_c <= l_a + l_b on bin centres; c slowest, b fastest
+  h->tris.clear();
+  for (int c = 0; c < h->nl; ++c)
+    for (int a = 0; a <= c; ++a)
+      for (int bb = a; bb <= c; ++bb)
+        if (h->ell[c] <= h->ell[a] + h->ell[bb]) {
+          h->tris.push_back(a);
+          h->tris.push_back(bb);
+          h->tris.push_back(c);
+        }
+  h->ntri = (int)(h->tris.size() / 3);
+  // data-vector rows
+  h->rowdesc.clear();
+  for (int bb = 0; bb < h->nl; ++bb)
+    for (int i = 0; i < h->nt; ++i)
+      for (int j = i; j < h->nt; ++j) {
+        int32_t d[8] = {0, bb, bb, bb, i, j, -1, bb};
+        h->rowdesc.insert(h->rowdesc.end(), d, d + 8);
+      }
+  h->nP = (int64_t)h->rowdesc.size() / 8;
+  std::vector<int> tt;
+  for (int t = 0; t < h->ntri; ++t) {
+    int a = h->tris[3 * t], bb = h->tris[3 * t + 1], c = h->tris[3 * t + 2];
+    tomo_triples(a, bb, c, h->nt, tt);
+    for (size_t k = 0; k < tt.size(); k += 3) {
+      int32_t d[8] = {1, a, bb, c, tt[k], tt[k + 1], tt[k + 2], t};
+      h->rowdesc.insert(h->rowdesc.end(), d, d + 8);
+    }
+  }
+  h->M = (int64_t)h->rowdesc.size() / 8;
+  h->nB = h->M - h->nP;
+  // sky and lattice: l_f = 2 pi / sqrt(Omega), Omega = 4 pi f_sky
+  h->omega = 4.0 * WL_PI * b.f_sky;
+  h->theta = acos(1.0 - 2.0 * b.f_sky);
+  h->ell_f = 2.0 * WL_PI / sqrt(h->omega);
+  h->s_lo.resize(h->nl);
+  h->s_hi.resize(h->nl);
+  for (int i = 0; i < h->nl; ++i) {
+    double x = h->ell_edges[i] / h->ell_f;
+    h->s_lo[i] = (int64_t)ceil(x * x);
+  }
+  double xt = h->ell_edges[h->nl] / h->ell_f;
+  for (int i = 0; i + 1 < h->nl; ++i) h->s_hi[i] = h->s_lo[i + 1];
+  h->s_hi[h->nl - 1] = (int64_t)floor(xt * xt) + 1;
+  int64_t smax = *std::max_element(h->s_hi.begin(), h->s_hi.end()) - 1;
+  int64_t rm = (int64_t)sqrt((double)smax);
+  while (rm * rm > smax) --rm;
+  while ((rm + 1) * (rm + 1) <= smax) ++rm;
+  h->rmax = (int)rm;
+  h->nleg = h->nl * h->nt;
+  h->ntrow = (int64_t)h->nleg * (h->nleg + 1) / 2;
+  return COV_OK;
+}
+
+static int validate(const cov_cosmology* c, const cov_nz* nz, const cov_bins* b) {
+  if (!c || !nz || !b) return COV_ERR_INVALID;
+  if (nz->n_tomo < 1 || nz->n_tomo > 32) return COV_ERR_INVALID;
+  if (nz->alpha != 1.5 || !(nz->z0 > 0) || !(nz->zmin >= 0) || !(nz->zmax > nz->zmin)) return COV_ERR_INVALID;
+  if (!(nz->photoz_sigma0 >= 0) || !(nz->n_gal_arcmin2 > 0) || !(nz->sigma_e >= 0)) return COV_ERR_INVALID;
+  if (b->n_ell < 1 || b->n_ell > 64 || !(b->ell_min > 0) || !(b->ell_max > b->ell_min)) return COV_ERR_INVALID;
+  if (!(b->f_sky > 0 && b->f_sky < 1)) return COV_ERR_INVALID;
+  if (b->n_chi < 2 || b->n_chi > 4096 || b->n_mass < 2 || b->n_mass > 4096) return COV_ERR_INVALID;
+  if (!(b->m_min > 0) || !(b->m_max > b->m_min) || !(b->k_max > 0)) return COV_ERR_INVALID;
+  if (!(c->Om > 0 && c->Om <= 1) || !(c->Ob > 0 && c->Ob < c->Om) || !(c->h > 0) || !(c->sigma8 > 0) ||
+      !(c->Tcmb > 0))
+    return COV_ERR_INVALID;
+  return COV_OK;
+}
+
+static void free_all(cov_handle* h) {
+  void* ptrs[] = {h->gl64x, h->gl64w, h->glkx, h->glkw, h->glcx, h->glcw, h->scal, h->chi, h->wchi, h->z, h->D,
+                  h->ell_d, h->m, h->om, h->sig0, h->dlns, h->f, h->b1, h->b2, h->U, h->Pl, h->dPl, h->zedges,
+                  h->norms, h->W, h->sigw2, h->slo_d, h->shi_d, h->Nmodes, h->Ntri, h->rowtab, h->tris_d,
+                  h->rowdesc_d, h->P3, h->RP3, h->B3, h->RB3, h->B1h3, h->Ps, h->B1hp, h->Bp, h->A, h->Ahi,
+                  h->Alo, h->Ascale, h->Trows, h->Tmat, h->Srows, h->work, h->perm};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+extern "C" int cov_init(const cov_cosmology* cosmo, const cov_nz* nz, const cov_bins* bins, const cov_opts* opts,
+                        cov_handle** out) {
+  if (!out) return COV_ERR_INVALID;
+  *out = nullptr;
+  if (validate(cosmo, nz, bins) != COV_OK) {
+    g_init_err = "invalid cosmology, n(z) or binning parameters";
+    return COV_ERR_INVALID;
+  }
+  cov_handle* h = new cov_handle();
+  h->cosmo = *cosmo;
+  h->nz = *nz;
+  h->bins = *bins;
+  h->device = opts ? opts->device : 0;
+  h->budget = opts ? opts->hbm_budget : 0;
+  int rc;
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) {
+    g_init_err = std::string("cudaSetDevice: ") + cudaGetErrorString(e);
+    delete h;
+    return COV_ERR_CUDA;
+  }
+  plan(h);
+  const size_t d = sizeof(double);
+  int nl = h->nl, nt = h->nt, nchi = h->nchi, nm = h->nm, ntri = std::max(h->ntri, 1);
+  struct {
+    void** p;
+    size_t n;
+  } al[] = {
+      {(void**)&h->gl64x, d * WL_N_GL_CHI}, {(void**)&h->gl64w, d * WL_N_GL_CHI},
+      {(void**)&h->glkx, d * WL_N_K},       {(void**)&h->glkw, d * WL_N_K},
+      {(void**)&h->glcx, d * nchi},         {(void**)&h->glcw, d * nchi},
+      {(void**)&h->scal, d * SC_N},         {(void**)&h->chi, d * nchi},
+      {(void**)&h->wchi, d * nchi},         {(void**)&h->z, d * nchi},
+      {(void**)&h->D, d * nchi},            {(void**)&h->ell_d, d * nl},
+      {(void**)&h->m, d * nm},              {(void**)&h->om, d * nm},
+      {(void**)&h->sig0, d * nm},           {(void**)&h->dlns, d * nm},
+      {(void**)&h->f, d * nchi * nm},       {(void**)&h->b1, d * nchi * nm},
+      {(void**)&h->b2, d * nchi * nm},      {(void**)&h->U, d * (size_t)nl * nchi * nm},
+      {(void**)&h->Pl, d * nl * nchi},      {(void**)&h->dPl, d * nl * nchi},
+      {(void**)&h->zedges, d * (nt + 1)},   {(void**)&h->norms, d * nt},
+      {(void**)&h->W, d * nt * nchi},       {(void**)&h->sigw2, d * nchi},
+      {(void**)&h->slo_d, 8ul * nl},          {(void**)&h->shi_d, 8ul * nl},
+      {(void**)&h->Nmodes, 8ul * nl},         {(void**)&h->Ntri, 8 * (size_t)ntri},
+      {(void**)&h->rowtab, 4 * (size_t)nl * 2 * (h->rmax + 1)},
+      {(void**)&h->tris_d, 4 * 3 * (size_t)ntri},
+      {(void**)&h->rowdesc_d, 4 * 8 * (size_t)h->M},
+      {(void**)&h->P3, d * nl * nchi},      {(void**)&h->RP3, d * nl * nchi},
+      {(void**)&h->B3, d * (size_t)ntri * nchi}, {(void**)&h->RB3, d * (size_t)ntri * nchi},
+      {(void**)&h->B1h3, d * (size_t)ntri * nchi}, {(void**)&h->Ps, d * nl * nt * nt},
+      {(void**)&h->B1hp, d * (size_t)ntri * nt * nt * nt},
+  };
+  for (auto& a : al) {
+    if ((rc = dalloc(h, a.p, a.n)) != COV_OK) {
+      g_init_err = h->err;
+      free_all(h);
+      delete h;
+      return rc;
+    }
+  }
+  cudaStream_t s = 0;
+  cudaMemcpy(h->ell_d, h->ell.data(), d * nl, cudaMemcpyHostToDevice);
+  cudaMemcpy(h->slo_d, h->s_lo.data(), 8 * nl, cudaMemcpyHostToDevice);
+  cudaMemcpy(h->shi_d, h->s_hi.data(), 8 * nl, cudaMemcpyHostToDevice);
+  if (h->ntri) cudaMemcpy(h->tris_d, h->tris.data(), 4 * h->tris.size(), cudaMemcpyHostToDevice);
+  e = cudaMemcpy(h->rowdesc_d, h->rowdesc.data(), 4 * h->rowdesc.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(h->scal, 0, d * SC_N);
+  if (e != cudaSuccess) {
+    g_init_err = std::string("upload: ") + cudaGetErrorString(e);
+    free_all(h);
+    delete h;
+    return COV_ERR_CUDA;
+  }
+  if ((rc = wl_tables(h, s)) == COV_OK) rc = wl_counts(h, s);
+  if (rc == COV_OK) {
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = wl_cuda(h, e, "cov_init tables");
+  }
+  if (rc != COV_OK) {
+    g_init_err = h->err;
+    free_all(h);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return COV_OK;
+}
+
+extern "C" int cov_update(cov_handle* h, const cov_cosmology* cosmo, void* stream) {
+  if (!h || !cosmo) return COV_ERR_INVALID;
+  if (validate(cosmo, &h->nz, &h->bins) != COV_OK) return wl_fail(h, COV_ERR_INVALID, "invalid cosmology");
+  h->cosmo = *cosmo;
+  h->spectra_ready = false;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = wl_tables(h, s);
+  if (rc == COV_OK) rc = wl_counts(h, s);
+  return rc;
+}
+
+extern "C" int cov_layout(const cov_handle* h, int64_t* M, int64_t* n_P, int64_t* n_B, int64_t* n_tri,
+                          int32_t* row_desc) {
+  if (!h) return COV_ERR_INVALID;
+  if (M) *M = h->M;
+  if (n_P) *n_P = h->nP;
+  if (n_B) *n_B = h->nB;
+  if (n_tri) *n_tri = h->ntri;
+  if (row_desc) memcpy(row_desc, h->rowdesc.data(), sizeof(int32_t) * h->rowdesc.size());
+  return COV_OK;
+}
+
+extern "C" int cov_counts(cov_handle* h, int64_t* N_ell, int64_t* N_tri, void* stream) {
+  if (!h) return COV_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (N_ell) WL_CHECK(h, cudaMemcpyAsync(N_ell, h->Nmodes, 8 * h->nl, cudaMemcpyDeviceToHost, s));
+  if (N_tri && h->ntri) WL_CHECK(h, cudaMemcpyAsync(N_tri, h->Ntri, 8 * (size_t)h->ntri, cudaMemcpyDeviceToHost, s));
+  WL_CHECK(h, cudaStreamSynchronize(s));
+  return COV_OK;
+}
+
+extern "C" int cov_spectra(cov_handle* h, double* d_D, void* stream) {
+  if (!h) return COV_ERR_INVALID;
+  return wl_spectra(h, d_D, (cudaStream_t)stream);
+}
+
+extern "C" int cov_assemble(cov_handle* h, double* d_C, int64_t ldc, unsigned terms, int precision, void* stream) {
+  if (!h || !d_C || ldc < h->M || (terms & ~COV_TERMS_ALL)) return wl_fail(h, COV_ERR_INVALID, "bad cov_assemble args");
+  if (precision != COV_FP64 && precision != COV_SPLIT_BF16) return wl_fail(h, COV_ERR_INVALID, "bad precision");
+  if (!h->spectra_ready) return wl_fail(h, COV_ERR_INVALID, "cov_spectra must run before cov_assemble");
+  return wl_assemble(h, d_C, ldc, terms, precision, (cudaStream_t)stream);
+}
+
+extern "C" int cov_snr(cov_handle* h, const double* d_C, int64_t ldc, const double* d_D, int which, double* h_snr,
+                       void* stream) {
+  if (!h || !d_C || !d_D || !h_snr || ldc < h->M) return wl_fail(h, COV_ERR_INVALID, "bad cov_snr args");
+  if (which < COV_WHICH_P || which > COV_WHICH_JOINT) return wl_fail(h, COV_ERR_INVALID, "bad selection");
+  return wl_snr(h, d_C, ldc, d_D, which, h_snr, (cudaStream_t)stream);
+}
+
+extern "C" int cov_table(cov_handle* h, const char* name, double* host, int64_t* count, void* stream) {
+  if (!h || !name || !count) return COV_ERR_INVALID;
+  struct {
+    const char* n;
+    const double* p;
+    int64_t c;
+  } tab[] = {
+      {"chi", h->chi, h->nchi},
+      {"wchi", h->wchi, h->nchi},
+      {"z", h->z, h->nchi},
+      {"growth", h->D, h->nchi},
+      {"mass", h->m, h->nm},
+      {"f", h->f, (int64_t)h->nchi * h->nm},
+      {"b1", h->b1, (int64_t)h->nchi * h->nm},
+      {"b2", h->b2, (int64_t)h->nchi * h->nm},
+      {"U", h->U, (int64_t)h->nl * h->nchi * h->nm},
+      {"Plin", h->Pl, (int64_t)h->nl * h->nchi},
+      {"dPlin", h->dPl, (int64_t)h->nl * h->nchi},
+      {"W", h->W, (int64_t)h->nt * h->nchi},
+      {"sigw2", h->sigw2, h->nchi},
+      {"P3", h->P3, (int64_t)h->nl * h->nchi},
+      {"RP3", h->RP3, (int64_t)h->nl * h->nchi},
+      {"B3", h->B3, (int64_t)h->ntri * h->nchi},
+      {"RB3", h->RB3, (int64_t)h->ntri * h->nchi},
+      {"B1h3", h->B1h3, (int64_t)h->ntri * h->nchi},
+      {"Ps", h->Ps, (int64_t)h->nl * h->nt * h->nt},
+      {"B1h", h->B1hp, (int64_t)h->ntri * h->nt * h->nt * h->nt},
+      {"zedges", h->zedges, h->nt + 1},
+  };
+  for (auto& t : tab) {
+    if (strcmp(t.n, name) == 0) {
+      *count = t.c;
+      if (host && t.c > 0) {
+        cudaStream_t s = (cudaStream_t)stream;
+        WL_CHECK(h, cudaMemcpyAsync(host, t.p, sizeof(double) * t.c, cudaMemcpyDeviceToHost, s));
+        WL_CHECK(h, cudaStreamSynchronize(s));
+      }
+      return COV_OK;
+    }
+  }
+  return wl_fail(h, COV_ERR_INVALID, std::string("unknown table ") + name);
+}
+
+extern "C" const char* cov_last_error(const cov_handle* h) {
+  return h ? h->err.c_str() : g_init_err.c_str();
+}
+
+extern "C" void cov_free(cov_handle* h) {
+  if (!h) return;
+  free_all(h);
+  delete h;
+}

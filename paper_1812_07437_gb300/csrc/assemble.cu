@@ -1,0 +1,250 @@
+// Covariance assembly (paper Sec. 3.2 and Appendix B):
+//  * k_gather   Gaussian PP/BB, BB+PT and PB product terms, element by
+//               element over the lower triangle (it initialises every lower
+//               element of C, so no separate clear pass is needed);
+//  * k_gemm_lower  C = alpha A B^T + beta C on the lower triangle in FP64:
+//               the 1-halo (chi, M) contraction (FP64 form), the 1-halo
+//               trispectrum table of the PT term and the rank-N_chi
+//               super-sample term.
+#include "common.cuh"
+
+int wl_rows_a(cov_handle* h, cudaStream_t s);
+int wl_rows_t(cov_handle* h, cudaStream_t s);
+int wl_rows_s(cov_handle* h, cudaStream_t s);
+int wl_rows_split(cov_handle* h, cudaStream_t s);
+
+__device__ __forceinline__ int64_t leg_pair(int L1, int L2, int nleg) {
+  if (L1 > L2) {
+    int t = L1;
+    L1 = L2;
+    L2 = t;
+  }
+  return (int64_t)L1 * (2 * nleg - L1 + 1) / 2 + (L2 - L1);
+}
+
+struct GatherArgs {
+  int nt, nleg;
+  unsigned terms;
+  double omega;
+  const int32_t* rd;
+  const double* Ps;      // [nl][nt][nt]
+  const double* B1hp;    // [ntri][nt][nt][nt]
+  const double* Tmat;    // [ntrow][ntrow] lower
+  int64_t ntrow;
+  const int64_t* Nm;     // N(l^b)
+  const int64_t* Ntri;   // N_tri(t)
+};
+
+__device__ __forceinline__ double ps(const GatherArgs& g, int b, int i, int j) {
+  return g.Ps[((size_t)b * g.nt + i) * g.nt + j];
+}
+__device__ __forceinline__ double b1h(const GatherArgs& g, int t, int i, int j, int k) {
+  return g.B1hp[(((size_t)t * g.nt + i) * g.nt + j) * g.nt + k];
+}
+
+__device__ double gather_element(const GatherArgs& g, const int32_t* ra, const int32_t* rb) {
+  double v = 0.0;
+  if (ra[0] == 0 && rb[0] == 0) {
+    if ((g.terms & COV_TERM_G) && ra[1] == rb[1]) {
+      int b = ra[1], i = ra[4], j = ra[5], k = rb[4], l = rb[5];
+      v += (ps(g, b, i, k) * ps(g, b, j, l) + ps(g, b, i, l) * ps(g, b, j, k)) / (double)g.Nm[b];
+    }
+    return v;
+  }
+  if (ra[0] == 1 && rb[0] == 1) {
+    const int* ba = ra + 1; const int* ta = ra + 4;
+    const int* bb = rb + 1; const int* tb = rb + 4;
+    if ((g.terms & COV_TERM_G) && ra[7] == rb[7]) {
+      const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+      double tot = 0.0;
+      for (int p = 0; p < 6; ++p) {
+        const int* s = perm[p];
+        if (ba[0] == ba[s[0]] && ba[1] == ba[s[1]] && ba[2] == ba[s[2]])
+          tot += ps(g, ba[0], ta[0], tb[s[0]]) * ps(g, ba[1], ta[1], tb[s[1]]) * ps(g, ba[2], ta[2], tb[s[2]]);
+      }
+      v += g.omega / (double)g.Ntri[ra[7]] * tot;
+    }
+    if (g.terms & COV_TERM_BBPT) {
+      for (int x = 0; x < 3; ++x)
+        for (int y = 0; y < 3; ++y) {
+          if (ba[x] != bb[y]) continue;
+          int x1 = (x + 1) % 3, x2 = (x + 2) % 3, y1 = (y + 1) % 3, y2 = (y + 2) % 3;
+          double nN = (double)g.Nm[ba[x]];
+          double bbv = b1h(g, ra[7], tb[y], ta[x1], ta[x2]) * b1h(g, rb[7], ta[x], tb[y1], tb[y2]);
+          int64_t r1 = leg_pair(ba[x1] * g.nt + ta[x1], ba[x2] * g.nt + ta[x2], g.nleg);
+          int64_t r2 = leg_pair(bb[y1] * g.nt + tb[y1], bb[y2] * g.nt + tb[y2], g.nleg);
+          int64_t hi = r1 > r2 ? r1 : r2, lo = r1 > r2 ? r2 : r1;
+          double tv = g.Tmat[hi * g.ntrow + lo];
+          v += (bbv + ps(g, ba[x], ta[x], tb[y]) * tv) / nN;
+        }
+    }
+    return v;
+  }
+  if (g.terms & COV_TERM_PB) {
+    const int32_t* rp = ra[0] == 0 ? ra : rb;
+    const int32_t* rq = ra[0] == 0 ? rb : ra;
+    int b = rp[1], i = rp[4], j = rp[5];
+    for (int y = 0; y < 3; ++y) {
+      if (rq[1 + y] != b) continue;
+      int y1 = (y + 1) % 3, y2 = (y + 2) % 3;
+      int t = rq[7];
+      v += (ps(g, b, i, rq[4 + y]) * b1h(g, t, j, rq[4 + y1], rq[4 + y2]) +
+            ps(g, b, j, rq[4 + y]) * b1h(g, t, i, rq[4 + y1], rq[4 + y2])) /
+           (double)g.Nm[b];
+    }
+  }
+  return v;
+}
+
+// lower-triangle tile index -> (ti, tj), ti >= tj
+__device__ __forceinline__ void tri_tile(int64_t id, int64_t* ti, int64_t* tj) {
+  int64_t i = (int64_t)((sqrt(8.0 * (double)id + 1.0) - 1.0) * 0.5);
+  while (i * (i + 1) / 2 > id) --i;
+  while ((i + 1) * (i + 2) / 2 <= id) ++i;
+  *ti = i;
+  *tj = id - i * (i + 1) / 2;
+}
+
+__global__ void k_gather(GatherArgs g, int64_t M, double* C, int64_t ldc) {
+  __shared__ int32_t rdA[32 * 8], rdB[32 * 8];
+  int64_t ti, tj;
+  tri_tile(blockIdx.x, &ti, &tj);
+  int64_t a0 = ti * 32, b0 = tj * 32;
+  int tid = threadIdx.y * 32 + threadIdx.x;
+  for (int e = tid; e < 256; e += 256) {
+    int r = e / 8, c = e % 8;
+    rdA[e] = (a0 + r < M) ? g.rd[(a0 + r) * 8 + c] : 0;
+    rdB[e] = (b0 + r < M) ? g.rd[(b0 + r) * 8 + c] : 0;
+  }
+  __syncthreads();
+  int64_t b = b0 + threadIdx.x;
+  for (int rr = threadIdx.y; rr < 32; rr += 8) {
+    int64_t a = a0 + rr;
+    if (a >= M || b >= M || b > a) continue;
+    C[a * ldc + b] = gather_element(g, rdA + rr * 8, rdB + threadIdx.x * 8);
+  }
+}
+
+// ---- FP64 tiled product on the lower triangle ------------------------------
+// 64 x 64 tile per block, 256 threads (4 x 4 outputs each), K slabs of 16.
+#define GT 64
+#define GK 16
+__global__ void __launch_bounds__(256) k_gemm_lower(const double* __restrict__ A, int64_t lda,
+                                                    const double* __restrict__ B, int64_t ldb, double* C,
+                                                    int64_t ldc, int64_t n, int64_t k, double alpha, double beta,
+                                                    int lower_only, int64_t ntiles_1d) {
+  __shared__ double As[GK][GT + 1];
+  __shared__ double Bs[GK][GT + 1];
+  int64_t ti, tj;
+  if (lower_only) {
+    tri_tile(blockIdx.x, &ti, &tj);
+  } else {
+    ti = blockIdx.x / ntiles_1d;
+    tj = blockIdx.x % ntiles_1d;
+  }
+  int64_t i0 = ti * GT, j0 = tj * GT;
+  int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+  for (int64_t k0 = 0; k0 < k; k0 += GK) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      int idx = threadIdx.x + 256 * l;
+      int row = idx / GK, col = idx % GK;
+      int64_t gi = i0 + row, gj = j0 + row, gk = k0 + col;
+      As[col][row] = (gi < n && gk < k) ? A[gi * lda + gk] : 0.0;
+      Bs[col][row] = (gj < n && gk < k) ? B[gj * ldb + gk] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) av[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) bv[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      int64_t gi = i0 + ty + 16 * r, gj = j0 + tx + 16 * c;
+      if (gi < n && gj < n && (!lower_only || gj <= gi)) {
+        double* p = C + gi * ldc + gj;
+        *p = alpha * acc[r][c] + (beta == 0.0 ? 0.0 : beta * *p);
+      }
+    }
+}
+
+int wl_gemm_lower_fp64(cov_handle* h, const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
+                       int64_t ldc, int64_t n, int64_t k, double alpha, double beta, bool lower_only,
+                       cudaStream_t s) {
+  if (n <= 0) return COV_OK;
+  int64_t nt1 = (n + GT - 1) / GT;
+  int64_t nblk = lower_only ? nt1 * (nt1 + 1) / 2 : nt1 * nt1;
+  k_gemm_lower<<<(unsigned)nblk, 256, 0, s>>>(A, lda, B, ldb, C, ldc, n, k, alpha, beta, lower_only ? 1 : 0, nt1);
+  WL_LAUNCH(h, "k_gemm_lower");
+  return COV_OK;
+}
+
+static int ensure(cov_handle* h, void** p, size_t bytes, const char* what) {
+  if (*p) return COV_OK;
+  if (h->budget && h->allocated + bytes > h->budget)
+    return wl_fail(h, COV_ERR_NOMEM, std::string("hbm_budget exceeded allocating ") + what);
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return wl_fail(h, COV_ERR_NOMEM, std::string("cudaMalloc failed for ") + what);
+  }
+  h->allocated += bytes;
+  return COV_OK;
+}
+
+int wl_assemble(cov_handle* h, double* C, int64_t ldc, unsigned terms, int precision, cudaStream_t s) {
+  int rc;
+  const int64_t M = h->M, K = h->K;
+  // 1. per-element product terms; initialises the lower triangle
+  if (terms & COV_TERM_BBPT) {
+    if ((rc = ensure(h, (void**)&h->Trows, sizeof(double) * h->ntrow * K, "trispectrum rows"))) return rc;
+    if ((rc = ensure(h, (void**)&h->Tmat, sizeof(double) * h->ntrow * h->ntrow, "trispectrum table"))) return rc;
+    if ((rc = wl_rows_t(h, s))) return rc;
+    if ((rc = wl_gemm_lower_fp64(h, h->Trows, K, h->Trows, K, h->Tmat, h->ntrow, h->ntrow, K, 1.0, 0.0, true, s)))
+      return rc;
+  }
+  GatherArgs g{h->nt, h->nleg, terms, h->omega, h->rowdesc_d, h->Ps, h->B1hp, h->Tmat, h->ntrow, h->Nmodes, h->Ntri};
+  int64_t nt32 = (M + 31) / 32;
+  k_gather<<<(unsigned)(nt32 * (nt32 + 1) / 2), dim3(32, 8), 0, s>>>(g, M, C, ldc);
+  WL_LAUNCH(h, "k_gather");
+  // 2. 1-halo (chi, M) contraction
+  if (terms & COV_TERM_1H) {
+    if (precision == COV_FP64) {
+      if ((rc = ensure(h, (void**)&h->A, sizeof(double) * M * K, "FP64 factor rows"))) return rc;
+      if ((rc = wl_rows_a(h, s))) return rc;
+      if ((rc = wl_gemm_lower_fp64(h, h->A, K, h->A, K, C, ldc, M, K, 1.0, 1.0, true, s))) return rc;
+    } else {
+      if ((rc = ensure(h, (void**)&h->Ahi, sizeof(uint16_t) * M * K, "BF16 hi rows"))) return rc;
+      if ((rc = ensure(h, (void**)&h->Alo, sizeof(uint16_t) * M * K, "BF16 lo rows"))) return rc;
+      if ((rc = ensure(h, (void**)&h->Ascale, sizeof(float) * M, "row scales"))) return rc;
+      if ((rc = wl_rows_split(h, s))) return rc;
+      if ((rc = wl_syrk_tc(h, C, ldc, s))) return rc;
+    }
+  }
+  // 3. super-sample term, rank N_chi
+  if (terms & COV_TERM_SSC) {
+    if ((rc = ensure(h, (void**)&h->Srows, sizeof(double) * M * h->nchi, "SSC rows"))) return rc;
+    if ((rc = wl_rows_s(h, s))) return rc;
+    if ((rc = wl_gemm_lower_fp64(h, h->Srows, h->nchi, h->Srows, h->nchi, C, ldc, M, h->nchi, 1.0, 1.0, true, s)))
+      return rc;
+  }
+  return COV_OK;
+}

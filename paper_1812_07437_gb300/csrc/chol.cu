@@ -1,0 +1,176 @@
+// Cumulative signal-to-noise (paper Sec. 5, Eqs. SNprim and eq:SN).
+//
+// The selected entries (P, B or the joint vector) are reordered by their
+// largest ell bin (stable), Jacobi-scaled, C' = d^-1/2 C d^-1/2 and
+// D' = d^-1/2 D, and written with D' as one extra last row into an FP64
+// workspace.  A blocked right-looking Cholesky factorisation of the leading
+// M_s x M_s block carries the extra row along, so that row ends up holding
+// y = L^-1 D'.  Because the leading principal block of a Cholesky factor is
+// the factor of the leading principal block, (S/N)^2 for every cumulative
+// ell_max is a prefix sum of y^2 over the reordered entries.
+#include <algorithm>
+
+#include "common.cuh"
+
+#define NB 64
+
+__global__ void k_snr_pack(int64_t Ms, const int* perm, const double* C, int64_t ldc, const double* D, double* Wk,
+                           int64_t ldw) {
+  int64_t i = blockIdx.x;  // row of the workspace (0..Ms)
+  int64_t j = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+  if (i > Ms || j > i) return;
+  if (i == Ms) {
+    if (j < Ms) {
+      int64_t pj = perm[j];
+      Wk[i * ldw + j] = D[pj] / sqrt(C[pj * ldc + pj]);
+    } else {
+      Wk[i * ldw + j] = 0.0;
+    }
+    return;
+  }
+  int64_t pi = perm[i], pj = perm[j];
+  int64_t hi = pi > pj ? pi : pj, lo = pi > pj ? pj : pi;
+  Wk[i * ldw + j] = C[hi * ldc + lo] / sqrt(C[pi * ldc + pi] * C[pj * ldc + pj]);
+}
+
+// in-place Cholesky of the kb x kb diagonal block at (k0, k0); one block
+__global__ void k_potrf_diag(double* Wk, int64_t ldw, int64_t k0, int kb, int* status) {
+  __shared__ double L[NB][NB + 1];
+  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+    int i = e / kb, j = e % kb;
+    L[i][j] = (j <= i) ? Wk[(k0 + i) * ldw + k0 + j] : 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    if (threadIdx.x == 0) {
+      double d = L[j][j];
+      if (!(d > 0.0)) {
+        atomicExch(status, 1);
+        d = 1.0;
+      }
+      L[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    double djj = L[j][j];
+    for (int i = j + 1 + threadIdx.x; i < kb; i += blockDim.x) L[i][j] /= djj;
+    __syncthreads();
+    for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+      int i = e / kb, l = e % kb;
+      if (l > j && l <= i) L[i][l] -= L[i][j] * L[l][j];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+    int i = e / kb, j = e % kb;
+    if (j <= i) Wk[(k0 + i) * ldw + k0 + j] = L[i][j];
+  }
+}
+
+// rows r in [r0, r1): x L11^T = a, one warp per row (column-oriented solve)
+__global__ void k_trsm_rows(double* Wk, int64_t ldw, int64_t k0, int kb, int64_t r0, int64_t r1) {
+  __shared__ double L[NB][NB + 1];
+  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+    int i = e / kb, j = e % kb;
+    L[i][j] = (j <= i) ? Wk[(k0 + i) * ldw + k0 + j] : 0.0;
+  }
+  __syncthreads();
+  int lane = threadIdx.x & 31;
+  int64_t r = r0 + (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (r >= r1) return;
+  double* row = Wk + r * ldw + k0;
+  double a0 = lane < kb ? row[lane] : 0.0;
+  double a1 = lane + 32 < kb ? row[lane + 32] : 0.0;
+  for (int j = 0; j < kb; ++j) {
+    double own = (j < 32) ? a0 : a1;
+    double xj = __shfl_sync(0xffffffffu, own, j & 31) / L[j][j];
+    if (lane == (j & 31)) {
+      if (j < 32) a0 = xj; else a1 = xj;
+    }
+    if (lane > j && lane < kb) a0 -= xj * L[lane][j];
+    if (lane + 32 > j && lane + 32 < kb) a1 -= xj * L[lane + 32][j];
+  }
+  if (lane < kb) row[lane] = a0;
+  if (lane + 32 < kb) row[lane + 32] = a1;
+}
+
+__global__ void k_snr_prefix(int64_t Ms, const double* Wk, int64_t ldw, const int64_t* cnt, int nl, double* out) {
+  __shared__ double sh[32];
+  int c = blockIdx.x;
+  int64_t n = cnt[c];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    double y = Wk[Ms * ldw + i];
+    s += y * y;
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) out[c] = (n > 0) ? sqrt(s) : nan("");
+}
+
+int wl_snr(cov_handle* h, const double* C, int64_t ldc, const double* D, int which, double* h_snr, cudaStream_t s) {
+  // host plan: selection ordered by largest ell bin (stable)
+  std::vector<int> sel;
+  for (int64_t a = 0; a < h->M; ++a) {
+    int type = h->rowdesc[8 * a];
+    if (which == COV_WHICH_P && type != 0) continue;
+    if (which == COV_WHICH_B && type != 1) continue;
+    sel.push_back((int)a);
+  }
+  auto maxbin = [&](int a) { return h->rowdesc[8 * a] == 0 ? h->rowdesc[8 * a + 1] : h->rowdesc[8 * a + 3]; };
+  std::stable_sort(sel.begin(), sel.end(), [&](int x, int y) { return maxbin(x) < maxbin(y); });
+  int64_t Ms = (int64_t)sel.size();
+  std::vector<int64_t> cnt(h->nl, 0);
+  for (int c = 0; c < h->nl; ++c)
+    for (int64_t i = 0; i < Ms; ++i)
+      if (maxbin(sel[i]) <= c) cnt[c] = i + 1;
+  if (Ms == 0) {
+    for (int c = 0; c < h->nl; ++c) h_snr[c] = nan("");
+    return COV_OK;
+  }
+  int64_t ldw = Ms + 1;
+  int64_t need = ldw * ldw;
+  if (need > h->work_n) {
+    if (h->work) cudaFree(h->work);
+    h->work = nullptr;
+    if (h->budget && h->allocated + sizeof(double) * need > h->budget)
+      return wl_fail(h, COV_ERR_NOMEM, "hbm_budget exceeded allocating the Cholesky workspace");
+    WL_CHECK(h, cudaMalloc(&h->work, sizeof(double) * need));
+    h->work_n = need;
+  }
+  if (!h->perm) WL_CHECK(h, cudaMalloc(&h->perm, sizeof(int) * h->M));
+  int* st = nullptr;
+  int64_t* cnt_d = nullptr;
+  double* out_d = nullptr;
+  WL_CHECK(h, cudaMallocAsync(&st, sizeof(int), s));
+  WL_CHECK(h, cudaMallocAsync(&cnt_d, sizeof(int64_t) * h->nl, s));
+  WL_CHECK(h, cudaMallocAsync(&out_d, sizeof(double) * h->nl, s));
+  WL_CHECK(h, cudaMemsetAsync(st, 0, sizeof(int), s));
+  WL_CHECK(h, cudaMemcpyAsync(h->perm, sel.data(), sizeof(int) * Ms, cudaMemcpyHostToDevice, s));
+  WL_CHECK(h, cudaMemcpyAsync(cnt_d, cnt.data(), sizeof(int64_t) * h->nl, cudaMemcpyHostToDevice, s));
+  dim3 gp((unsigned)(Ms + 1), (unsigned)((Ms + 1 + 255) / 256));
+  k_snr_pack<<<gp, 256, 0, s>>>(Ms, h->perm, C, ldc, D, h->work, ldw);
+  WL_LAUNCH(h, "k_snr_pack");
+  for (int64_t k0 = 0; k0 < Ms; k0 += NB) {
+    int kb = (int)std::min<int64_t>(NB, Ms - k0);
+    k_potrf_diag<<<1, 256, 0, s>>>(h->work, ldw, k0, kb, st);
+    int64_t r0 = k0 + kb, r1 = Ms + 1;
+    if (r1 > r0) {
+      k_trsm_rows<<<(unsigned)((r1 - r0 + 7) / 8), 256, 0, s>>>(h->work, ldw, k0, kb, r0, r1);
+      int64_t n = r1 - r0;
+      double* P = h->work + r0 * ldw + k0;
+      double* Csub = h->work + r0 * ldw + r0;
+      int rc = wl_gemm_lower_fp64(h, P, ldw, P, ldw, Csub, ldw, n, kb, -1.0, 1.0, true, s);
+      if (rc) return rc;
+    }
+  }
+  WL_LAUNCH(h, "Cholesky kernels");
+  k_snr_prefix<<<h->nl, 256, 0, s>>>(Ms, h->work, ldw, cnt_d, h->nl, out_d);
+  int status = 0;
+  WL_CHECK(h, cudaMemcpyAsync(h_snr, out_d, sizeof(double) * h->nl, cudaMemcpyDeviceToHost, s));
+  WL_CHECK(h, cudaMemcpyAsync(&status, st, sizeof(int), cudaMemcpyDeviceToHost, s));
+  WL_CHECK(h, cudaFreeAsync(st, s));
+  WL_CHECK(h, cudaFreeAsync(cnt_d, s));
+  WL_CHECK(h, cudaFreeAsync(out_d, s));
+  WL_CHECK(h, cudaStreamSynchronize(s));
+  if (status) return wl_fail(h, COV_ERR_NOT_PD, "Cholesky met a non-positive pivot");
+  return COV_OK;
+}

@@ -1,0 +1,83 @@
+"""Thin PyTorch-facing wrapper around the libwlcov C ABI (marshalling only).
+
+Device buffers are torch tensors on the handle's device; streams are torch
+CUDA streams.  Every computation happens inside libwlcov's kernels.
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import native as N
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Handle:
+    def __init__(self, wl, device=0, hbm_budget=0):
+        self.L = N.lib()
+        cs, ns, bs = N.structs_from_workload(wl)
+        opts = N.cov_opts(int(device), int(hbm_budget))
+        h = C.c_void_p()
+        N.check(self.L.cov_init(C.byref(cs), C.byref(ns), C.byref(bs), C.byref(opts), C.byref(h)))
+        self.h = h
+        self.wl = wl
+        self.device = device
+        M, nP, nB, nT = (C.c_int64() for _ in range(4))
+        N.check(self.L.cov_layout(h, C.byref(M), C.byref(nP), C.byref(nB), C.byref(nT), None), h)
+        self.M, self.n_P, self.n_B, self.n_tri = M.value, nP.value, nB.value, nT.value
+        self.n_ell = int(wl["bins"]["n_ell"])
+
+    def close(self):
+        if self.h:
+            self.L.cov_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def row_desc(self):
+        out = np.zeros((self.M, 8), dtype=np.int32)
+        N.check(self.L.cov_layout(self.h, None, None, None, None, out.ctypes.data_as(C.c_void_p)), self.h)
+        return out
+
+    def counts(self, stream=None):
+        ne = np.zeros(self.n_ell, dtype=np.int64)
+        nt = np.zeros(max(self.n_tri, 1), dtype=np.int64)
+        N.check(self.L.cov_counts(self.h, ne.ctypes.data_as(C.c_void_p), nt.ctypes.data_as(C.c_void_p),
+                                  _stream_ptr(stream)), self.h)
+        return ne, nt[: self.n_tri]
+
+    def table(self, name, stream=None):
+        cnt = C.c_int64()
+        N.check(self.L.cov_table(self.h, name.encode(), None, C.byref(cnt), _stream_ptr(stream)), self.h)
+        out = np.zeros(cnt.value, dtype=np.float64)
+        N.check(self.L.cov_table(self.h, name.encode(), out.ctypes.data_as(C.c_void_p), C.byref(cnt),
+                                 _stream_ptr(stream)), self.h)
+        return out
+
+    def update(self, cosmology, stream=None):
+        cs = N.cov_cosmology(*(float(cosmology[k]) for k in ("Om", "Ob", "h", "ns", "sigma8", "w0", "Tcmb")))
+        N.check(self.L.cov_update(self.h, C.byref(cs), _stream_ptr(stream)), self.h)
+
+    def spectra(self, D=None, stream=None):
+        ptr = C.c_void_p(D.data_ptr()) if D is not None else None
+        N.check(self.L.cov_spectra(self.h, ptr, _stream_ptr(stream)), self.h)
+
+    def assemble(self, Cmat, terms=N.COV_TERMS_ALL, precision=N.COV_FP64, stream=None):
+        ldc = Cmat.stride(0)
+        N.check(self.L.cov_assemble(self.h, C.c_void_p(Cmat.data_ptr()), ldc, terms, precision,
+                                    _stream_ptr(stream)), self.h)
+
+    def snr(self, Cmat, D, which=N.COV_WHICH_JOINT, stream=None):
+        out = np.zeros(self.n_ell, dtype=np.float64)
+        N.check(self.L.cov_snr(self.h, C.c_void_p(Cmat.data_ptr()), Cmat.stride(0), C.c_void_p(D.data_ptr()),
+                               which, out.ctypes.data_as(C.c_void_p), _stream_ptr(stream)), self.h)
+        return out

@@ -1,0 +1,111 @@
+"""ctypes binding of libwlcov (argument marshalling only).
+
+Every function of ``include/wlcov.h`` is exposed under the same name; device
+memory and streams come from PyTorch tensors / streams and are passed as raw
+pointers.  There is no CPU fallback: importing this module on a machine
+without the built library raises.
+"""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libwlcov.so")
+
+COV_OK = 0
+COV_ERR_INVALID = -1
+COV_ERR_NOMEM = -2
+COV_ERR_NOT_PD = -3
+COV_ERR_TIMEOUT = -4
+COV_ERR_CUDA = -5
+
+COV_TERM_G = 1
+COV_TERM_1H = 2
+COV_TERM_BBPT = 4
+COV_TERM_PB = 8
+COV_TERM_SSC = 16
+COV_TERMS_ALL = 31
+
+COV_FP64 = 0
+COV_SPLIT_BF16 = 1
+
+COV_WHICH_P = 0
+COV_WHICH_B = 1
+COV_WHICH_JOINT = 2
+
+EXPORTED = ["cov_init", "cov_update", "cov_layout", "cov_counts", "cov_spectra", "cov_assemble", "cov_snr",
+            "cov_table", "cov_last_error", "cov_free"]
+
+
+class cov_cosmology(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("Om", "Ob", "h", "ns", "sigma8", "w0", "Tcmb")]
+
+
+class cov_nz(C.Structure):
+    _fields_ = [("n_tomo", C.c_int)] + [(n, C.c_double) for n in (
+        "z0", "alpha", "zmin", "zmax", "photoz_sigma0", "n_gal_arcmin2", "sigma_e")]
+
+
+class cov_bins(C.Structure):
+    _fields_ = [("n_ell", C.c_int), ("ell_min", C.c_double), ("ell_max", C.c_double), ("f_sky", C.c_double),
+                ("n_chi", C.c_int), ("n_mass", C.c_int), ("m_min", C.c_double), ("m_max", C.c_double),
+                ("k_max", C.c_double)]
+
+
+class cov_opts(C.Structure):
+    _fields_ = [("device", C.c_int), ("hbm_budget", C.c_size_t)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libwlcov.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        i64 = C.c_int64
+        L.cov_init.argtypes = [C.POINTER(cov_cosmology), C.POINTER(cov_nz), C.POINTER(cov_bins),
+                               C.POINTER(cov_opts), C.POINTER(P)]
+        L.cov_update.argtypes = [P, C.POINTER(cov_cosmology), P]
+        L.cov_layout.argtypes = [P, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), P]
+        L.cov_counts.argtypes = [P, P, P, P]
+        L.cov_spectra.argtypes = [P, P, P]
+        L.cov_assemble.argtypes = [P, P, i64, C.c_uint, C.c_int, P]
+        L.cov_snr.argtypes = [P, P, i64, P, C.c_int, P, P]
+        L.cov_table.argtypes = [P, C.c_char_p, P, C.POINTER(i64), P]
+        L.cov_last_error.argtypes = [P]
+        L.cov_last_error.restype = C.c_char_p
+        L.cov_free.argtypes = [P]
+        L.cov_free.restype = None
+        for n in EXPORTED:
+            if n not in ("cov_last_error", "cov_free"):
+                getattr(L, n).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+class CovError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libwlcov error {code}: {msg}")
+        self.code = code
+
+
+def check(rc, handle=None):
+    if rc != COV_OK:
+        raise CovError(rc, lib().cov_last_error(handle).decode())
+    return rc
+
+
+def structs_from_workload(wl):
+    c = wl["cosmology"]
+    nz = wl["nz"]
+    b = wl["bins"]
+    cs = cov_cosmology(*(float(c[k]) for k in ("Om", "Ob", "h", "ns", "sigma8", "w0", "Tcmb")))
+    ns = cov_nz(int(nz["n_tomo"]), *(float(nz[k]) for k in (
+        "z0", "alpha", "zmin", "zmax", "photoz_sigma0", "n_gal_arcmin2", "sigma_e")))
+    bs = cov_bins(int(b["n_ell"]), float(b["ell_min"]), float(b["ell_max"]), float(b["f_sky"]), int(b["n_chi"]),
+                  int(b["n_mass"]), float(b["m_min"]), float(b["m_max"]), float(b["k_max"]))
+    return cs, ns, bs
