@@ -139,6 +139,17 @@ int cov_snr(cov_handle* h, const double* d_C, int64_t ldc, const double* d_D, in
  * *count receives the number of doubles (pass host = NULL to query). */
 int cov_table(cov_handle* h, const char* name, double* host, int64_t* count, void* stream);
 
+/* Stage timing with CUDA events recorded on the caller's stream around each
+ * stage (tables, counts, spectra, row builders, each contraction, the
+ * gather pass, the S/N factorisation).  cov_profile(h, 1) starts recording;
+ * cov_stage_times synchronises on the recorded events, writes the summed
+ * milliseconds and the number of timed calls per stage into the first
+ * n_stages entries of ms / calls (host arrays, either may be NULL) and
+ * clears the record.  cov_stage_name(i) names stage i (NULL past the end). */
+int cov_profile(cov_handle* h, int enable);
+int cov_stage_times(cov_handle* h, double* ms, int64_t* calls, int n_stages);
+const char* cov_stage_name(int stage);
+
 const char* cov_last_error(const cov_handle* h);
 void cov_free(cov_handle* h);
 

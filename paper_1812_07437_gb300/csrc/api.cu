@@ -24,6 +24,34 @@ int wl_cuda(cov_handle* h, cudaError_t e, const char* what) {
 
 static thread_local std::string g_init_err;
 
+static const char* kStageNames[ST_COUNT] = {"tables", "counts", "spectra", "rows_T", "syrk_T", "gather",
+                                            "rows_A", "syrk_1h", "rows_S", "syrk_ssc", "snr_pack",
+                                            "snr_cholesky", "snr_prefix"};
+
+static cudaEvent_t ev_get(cov_handle* h) {
+  if (!h->pool.empty()) {
+    cudaEvent_t e = h->pool.back();
+    h->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+int wl_stage_begin(cov_handle* h, int stage, cudaStream_t s) {
+  if (!h->prof) return -1;
+  StageEvent se{stage, ev_get(h), ev_get(h)};
+  cudaEventRecord(se.a, s);
+  h->pending.push_back(se);
+  return (int)h->pending.size() - 1;
+}
+
+void wl_stage_end(cov_handle* h, int token, cudaStream_t s) {
+  if (token < 0 || token >= (int)h->pending.size()) return;
+  cudaEventRecord(h->pending[token].b, s);
+}
+
 static int dalloc(cov_handle* h, void** p, size_t bytes) {
   if (bytes == 0) bytes = 8;
   if (h->budget && h->allocated + bytes > h->budget) return wl_fail(h, COV_ERR_NOMEM, "hbm_budget exceeded");
@@ -146,11 +174,18 @@ static int validate(const cov_cosmology* c, const cov_nz* nz, const cov_bins* b)
 }
 
 static void free_all(cov_handle* h) {
+  for (auto& se : h->pending) {
+    cudaEventDestroy(se.a);
+    cudaEventDestroy(se.b);
+  }
+  for (auto e : h->pool) cudaEventDestroy(e);
+  h->pending.clear();
+  h->pool.clear();
   void* ptrs[] = {h->gl64x, h->gl64w, h->glkx, h->glkw, h->glcx, h->glcw, h->scal, h->chi, h->wchi, h->z, h->D,
                   h->ell_d, h->m, h->om, h->sig0, h->dlns, h->f, h->b1, h->b2, h->U, h->Pl, h->dPl, h->zedges,
                   h->norms, h->W, h->sigw2, h->slo_d, h->shi_d, h->Nmodes, h->Ntri, h->rowtab, h->tris_d,
                   h->rowdesc_d, h->P3, h->RP3, h->B3, h->RB3, h->B1h3, h->Ps, h->B1hp, h->Bp, h->A, h->Ahi,
-                  h->Alo, h->Ascale, h->Trows, h->Tmat, h->Srows, h->work, h->perm};
+                  h->Alo, h->Ascale, h->tc_status, h->Trows, h->Tmat, h->Srows, h->work, h->perm};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -248,8 +283,14 @@ extern "C" int cov_update(cov_handle* h, const cov_cosmology* cosmo, void* strea
   h->cosmo = *cosmo;
   h->spectra_ready = false;
   cudaStream_t s = (cudaStream_t)stream;
+  int tk = wl_stage_begin(h, ST_TABLES, s);
   int rc = wl_tables(h, s);
-  if (rc == COV_OK) rc = wl_counts(h, s);
+  wl_stage_end(h, tk, s);
+  if (rc == COV_OK) {
+    tk = wl_stage_begin(h, ST_COUNTS, s);
+    rc = wl_counts(h, s);
+    wl_stage_end(h, tk, s);
+  }
   return rc;
 }
 
@@ -275,7 +316,10 @@ extern "C" int cov_counts(cov_handle* h, int64_t* N_ell, int64_t* N_tri, void* s
 
 extern "C" int cov_spectra(cov_handle* h, double* d_D, void* stream) {
   if (!h) return COV_ERR_INVALID;
-  return wl_spectra(h, d_D, (cudaStream_t)stream);
+  int tk = wl_stage_begin(h, ST_SPECTRA, (cudaStream_t)stream);
+  int rc = wl_spectra(h, d_D, (cudaStream_t)stream);
+  wl_stage_end(h, tk, (cudaStream_t)stream);
+  return rc;
 }
 
 extern "C" int cov_assemble(cov_handle* h, double* d_C, int64_t ldc, unsigned terms, int precision, void* stream) {
@@ -334,6 +378,36 @@ extern "C" int cov_table(cov_handle* h, const char* name, double* host, int64_t*
   }
   return wl_fail(h, COV_ERR_INVALID, std::string("unknown table ") + name);
 }
+
+extern "C" int cov_profile(cov_handle* h, int enable) {
+  if (!h) return COV_ERR_INVALID;
+  h->prof = enable != 0;
+  return COV_OK;
+}
+
+extern "C" int cov_stage_times(cov_handle* h, double* ms, int64_t* calls, int n_stages) {
+  if (!h || n_stages < 0) return COV_ERR_INVALID;
+  for (auto& se : h->pending) {
+    cudaError_t e = cudaEventSynchronize(se.b);
+    if (e != cudaSuccess) return wl_cuda(h, e, "cudaEventSynchronize");
+    float t = 0.f;
+    cudaEventElapsedTime(&t, se.a, se.b);
+    h->stage_ms[se.stage] += t;
+    h->stage_calls[se.stage] += 1;
+    h->pool.push_back(se.a);
+    h->pool.push_back(se.b);
+  }
+  h->pending.clear();
+  for (int i = 0; i < n_stages && i < ST_COUNT; ++i) {
+    if (ms) ms[i] = h->stage_ms[i];
+    if (calls) calls[i] = h->stage_calls[i];
+    h->stage_ms[i] = 0.0;
+    h->stage_calls[i] = 0;
+  }
+  return COV_OK;
+}
+
+extern "C" const char* cov_stage_name(int stage) { return (stage >= 0 && stage < ST_COUNT) ? kStageNames[stage] : nullptr; }
 
 extern "C" const char* cov_last_error(const cov_handle* h) {
   return h ? h->err.c_str() : g_init_err.c_str();

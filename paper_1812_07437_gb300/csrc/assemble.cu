@@ -217,34 +217,55 @@ int wl_assemble(cov_handle* h, double* C, int64_t ldc, unsigned terms, int preci
   if (terms & COV_TERM_BBPT) {
     if ((rc = ensure(h, (void**)&h->Trows, sizeof(double) * h->ntrow * K, "trispectrum rows"))) return rc;
     if ((rc = ensure(h, (void**)&h->Tmat, sizeof(double) * h->ntrow * h->ntrow, "trispectrum table"))) return rc;
+    int tk = wl_stage_begin(h, ST_ROWS_T, s);
     if ((rc = wl_rows_t(h, s))) return rc;
+    wl_stage_end(h, tk, s);
+    tk = wl_stage_begin(h, ST_SYRK_T, s);
     if ((rc = wl_gemm_lower_fp64(h, h->Trows, K, h->Trows, K, h->Tmat, h->ntrow, h->ntrow, K, 1.0, 0.0, true, s)))
       return rc;
+    wl_stage_end(h, tk, s);
   }
   GatherArgs g{h->nt, h->nleg, terms, h->omega, h->rowdesc_d, h->Ps, h->B1hp, h->Tmat, h->ntrow, h->Nmodes, h->Ntri};
   int64_t nt32 = (M + 31) / 32;
+  int tg = wl_stage_begin(h, ST_GATHER, s);
   k_gather<<<(unsigned)(nt32 * (nt32 + 1) / 2), dim3(32, 8), 0, s>>>(g, M, C, ldc);
   WL_LAUNCH(h, "k_gather");
+  wl_stage_end(h, tg, s);
   // 2. 1-halo (chi, M) contraction
   if (terms & COV_TERM_1H) {
     if (precision == COV_FP64) {
       if ((rc = ensure(h, (void**)&h->A, sizeof(double) * M * K, "FP64 factor rows"))) return rc;
+      int tk = wl_stage_begin(h, ST_ROWS_A, s);
       if ((rc = wl_rows_a(h, s))) return rc;
+      wl_stage_end(h, tk, s);
+      tk = wl_stage_begin(h, ST_SYRK_1H, s);
       if ((rc = wl_gemm_lower_fp64(h, h->A, K, h->A, K, C, ldc, M, K, 1.0, 1.0, true, s))) return rc;
+      wl_stage_end(h, tk, s);
     } else {
-      if ((rc = ensure(h, (void**)&h->Ahi, sizeof(uint16_t) * M * K, "BF16 hi rows"))) return rc;
-      if ((rc = ensure(h, (void**)&h->Alo, sizeof(uint16_t) * M * K, "BF16 lo rows"))) return rc;
-      if ((rc = ensure(h, (void**)&h->Ascale, sizeof(float) * M, "row scales"))) return rc;
+      size_t sb = 0;
+      wl_split_bytes(M, (int)K, &sb);
+      if ((rc = ensure(h, (void**)&h->Ahi, sb, "BF16 hi rows"))) return rc;
+      if ((rc = ensure(h, (void**)&h->Alo, sb, "BF16 lo rows"))) return rc;
+      if ((rc = ensure(h, (void**)&h->Ascale, sizeof(double) * M, "row scales"))) return rc;
+      if ((rc = ensure(h, (void**)&h->tc_status, sizeof(int), "status word"))) return rc;
+      int tk = wl_stage_begin(h, ST_ROWS_A, s);
       if ((rc = wl_rows_split(h, s))) return rc;
+      wl_stage_end(h, tk, s);
+      tk = wl_stage_begin(h, ST_SYRK_1H, s);
       if ((rc = wl_syrk_tc(h, C, ldc, s))) return rc;
+      wl_stage_end(h, tk, s);
     }
   }
   // 3. super-sample term, rank N_chi
   if (terms & COV_TERM_SSC) {
     if ((rc = ensure(h, (void**)&h->Srows, sizeof(double) * M * h->nchi, "SSC rows"))) return rc;
+    int tk = wl_stage_begin(h, ST_ROWS_S, s);
     if ((rc = wl_rows_s(h, s))) return rc;
+    wl_stage_end(h, tk, s);
+    tk = wl_stage_begin(h, ST_SYRK_SSC, s);
     if ((rc = wl_gemm_lower_fp64(h, h->Srows, h->nchi, h->Srows, h->nchi, C, ldc, M, h->nchi, 1.0, 1.0, true, s)))
       return rc;
+    wl_stage_end(h, tk, s);
   }
   return COV_OK;
 }

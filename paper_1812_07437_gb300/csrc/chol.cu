@@ -147,8 +147,11 @@ int wl_snr(cov_handle* h, const double* C, int64_t ldc, const double* D, int whi
   WL_CHECK(h, cudaMemcpyAsync(h->perm, sel.data(), sizeof(int) * Ms, cudaMemcpyHostToDevice, s));
   WL_CHECK(h, cudaMemcpyAsync(cnt_d, cnt.data(), sizeof(int64_t) * h->nl, cudaMemcpyHostToDevice, s));
   dim3 gp((unsigned)(Ms + 1), (unsigned)((Ms + 1 + 255) / 256));
+  int tk = wl_stage_begin(h, ST_SNR_PACK, s);
   k_snr_pack<<<gp, 256, 0, s>>>(Ms, h->perm, C, ldc, D, h->work, ldw);
   WL_LAUNCH(h, "k_snr_pack");
+  wl_stage_end(h, tk, s);
+  tk = wl_stage_begin(h, ST_SNR_CHOL, s);
   for (int64_t k0 = 0; k0 < Ms; k0 += NB) {
     int kb = (int)std::min<int64_t>(NB, Ms - k0);
     k_potrf_diag<<<1, 256, 0, s>>>(h->work, ldw, k0, kb, st);
@@ -163,7 +166,10 @@ int wl_snr(cov_handle* h, const double* C, int64_t ldc, const double* D, int whi
     }
   }
   WL_LAUNCH(h, "Cholesky kernels");
+  wl_stage_end(h, tk, s);
+  tk = wl_stage_begin(h, ST_SNR_PREFIX, s);
   k_snr_prefix<<<h->nl, 256, 0, s>>>(Ms, h->work, ldw, cnt_d, h->nl, out_d);
+  wl_stage_end(h, tk, s);
   int status = 0;
   WL_CHECK(h, cudaMemcpyAsync(h_snr, out_d, sizeof(double) * h->nl, cudaMemcpyDeviceToHost, s));
   WL_CHECK(h, cudaMemcpyAsync(&status, st, sizeof(int), cudaMemcpyDeviceToHost, s));

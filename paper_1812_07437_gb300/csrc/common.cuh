@@ -38,6 +38,17 @@ struct DevCosmo {
   double Om, Ob, h, ns, sigma8, w0, Tcmb;
 };
 
+// timed stages (cov_stage_times)
+enum {
+  ST_TABLES = 0, ST_COUNTS, ST_SPECTRA, ST_ROWS_T, ST_SYRK_T, ST_GATHER, ST_ROWS_A, ST_SYRK_1H, ST_ROWS_S,
+  ST_SYRK_SSC, ST_SNR_PACK, ST_SNR_CHOL, ST_SNR_PREFIX, ST_COUNT
+};
+
+struct StageEvent {
+  int stage;
+  cudaEvent_t a, b;
+};
+
 struct cov_handle {
   int device = 0;
   size_t budget = 0, allocated = 0;
@@ -72,7 +83,8 @@ struct cov_handle {
   // device: contraction operands and workspaces
   double* A = nullptr;      // [M][K] FP64 1-halo factor rows
   uint16_t *Ahi = nullptr, *Alo = nullptr;  // [M][K] BF16 split rows (tensor-core form)
-  float* Ascale = nullptr;  // per-row power-of-two scales of the split rows
+  double* Ascale = nullptr; // per-row power-of-two scales of the split rows
+  int* tc_status = nullptr; // status word of the tensor-core contraction
   double* Trows = nullptr;  // [ntrow][K]
   double* Tmat = nullptr;   // [ntrow][ntrow] lower
   double* Srows = nullptr;  // [M][nchi]
@@ -80,6 +92,11 @@ struct cov_handle {
   int64_t work_n = 0;
   int* perm = nullptr;      // [M] reorder for the cumulative S/N
   bool spectra_ready = false;
+  bool prof = false;
+  std::vector<StageEvent> pending;
+  std::vector<cudaEvent_t> pool;
+  double stage_ms[ST_COUNT] = {0};
+  int64_t stage_calls[ST_COUNT] = {0};
   std::string err;
 };
 
@@ -97,6 +114,10 @@ int wl_cuda(cov_handle* h, cudaError_t e, const char* what);
     if (e_ != cudaSuccess) return wl_cuda((h), e_, (what)); \
   } while (0)
 
+// stage timing: the returned index pairs a begin with its end (-1 = off)
+int wl_stage_begin(cov_handle* h, int stage, cudaStream_t s);
+void wl_stage_end(cov_handle* h, int token, cudaStream_t s);
+
 // ---- stage entry points (one per translation unit) -------------------------
 int wl_tables(cov_handle* h, cudaStream_t s);   // tables.cu
 int wl_counts(cov_handle* h, cudaStream_t s);   // counts.cu
@@ -108,6 +129,7 @@ int wl_gemm_lower_fp64(cov_handle* h, const double* A, int64_t lda, const double
                        int64_t ldc, int64_t n, int64_t k, double alpha, double beta, bool lower_only,
                        cudaStream_t s);  // assemble.cu
 int wl_syrk_tc(cov_handle* h, double* d_C, int64_t ldc, cudaStream_t s);  // syrk_tc.cu
+int wl_split_bytes(int64_t M, int K, size_t* bytes);                      // syrk_tc.cu
 
 // ---- device helpers ------------------------------------------------------------
 __device__ __forceinline__ DevCosmo dev_cosmo(const cov_cosmology& c) {

@@ -76,6 +76,17 @@ class Handle:
         N.check(self.L.cov_assemble(self.h, C.c_void_p(Cmat.data_ptr()), ldc, terms, precision,
                                     _stream_ptr(stream)), self.h)
 
+    def profile(self, enable=True):
+        N.check(self.L.cov_profile(self.h, 1 if enable else 0), self.h)
+
+    def stage_times(self):
+        """{stage name: (summed ms, calls)} since the last query."""
+        ms = np.zeros(N.N_STAGES)
+        calls = np.zeros(N.N_STAGES, dtype=np.int64)
+        N.check(self.L.cov_stage_times(self.h, ms.ctypes.data_as(C.c_void_p), calls.ctypes.data_as(C.c_void_p),
+                                       N.N_STAGES), self.h)
+        return {self.L.cov_stage_name(i).decode(): (float(ms[i]), int(calls[i])) for i in range(N.N_STAGES)}
+
     def snr(self, Cmat, D, which=N.COV_WHICH_JOINT, stream=None):
         out = np.zeros(self.n_ell, dtype=np.float64)
         N.check(self.L.cov_snr(self.h, C.c_void_p(Cmat.data_ptr()), Cmat.stride(0), C.c_void_p(D.data_ptr()),

@@ -33,7 +33,9 @@ COV_WHICH_B = 1
 COV_WHICH_JOINT = 2
 
 EXPORTED = ["cov_init", "cov_update", "cov_layout", "cov_counts", "cov_spectra", "cov_assemble", "cov_snr",
-            "cov_table", "cov_last_error", "cov_free"]
+            "cov_table", "cov_profile", "cov_stage_times", "cov_stage_name", "cov_last_error", "cov_free"]
+N_STAGES = 13
+HAS_SPLIT_BF16 = True
 
 
 class cov_cosmology(C.Structure):
@@ -76,12 +78,16 @@ def lib():
         L.cov_assemble.argtypes = [P, P, i64, C.c_uint, C.c_int, P]
         L.cov_snr.argtypes = [P, P, i64, P, C.c_int, P, P]
         L.cov_table.argtypes = [P, C.c_char_p, P, C.POINTER(i64), P]
+        L.cov_profile.argtypes = [P, C.c_int]
+        L.cov_stage_times.argtypes = [P, P, P, C.c_int]
+        L.cov_stage_name.argtypes = [C.c_int]
+        L.cov_stage_name.restype = C.c_char_p
         L.cov_last_error.argtypes = [P]
         L.cov_last_error.restype = C.c_char_p
         L.cov_free.argtypes = [P]
         L.cov_free.restype = None
         for n in EXPORTED:
-            if n not in ("cov_last_error", "cov_free"):
+            if n not in ("cov_last_error", "cov_free", "cov_stage_name"):
                 getattr(L, n).restype = C.c_int
         _lib = L
     return _lib
