@@ -150,6 +150,35 @@ int cov_profile(cov_handle* h, int enable);
 int cov_stage_times(cov_handle* h, double* ms, int64_t* calls, int n_stages);
 const char* cov_stage_name(int stage);
 
+/* Allocation-free cumulative S/N, for callers that cannot allocate device
+ * memory: a host application that owns all device memory through its own
+ * pool and forbids further cudaMalloc calls (a plugin inside a larger
+ * framework, an embedded serving runtime with a fixed budget), or a loop that
+ * must never stall on an allocation.  The paper has no counterpart; this is a
+ * deployment variant of cov_snr.
+ *
+ * It runs the same Jacobi-scaled FP64 Cholesky as cov_snr on d_C (device,
+ * M x M lower triangle, row-major, leading dimension ldc >= M) and d_D
+ * (device, M values), both already in cumulative order, and writes
+ * d_snr[c] = sqrt(D^T C^-1 D) over the first prefix[c] entries, for
+ * c < n_prefix (1 <= n_prefix <= 64; prefix: host array, non-decreasing,
+ * each <= M; an empty prefix gives NaN).  *d_status (device int) is set to 0,
+ * or to 1 when a pivot was not positive.  Nothing is allocated and nothing
+ * is synchronised: the call is ordered on stream and the caller reads
+ * d_snr / d_status after it.
+ *
+ * The workspace is one static device array of (COV_NOALLOC_MAX_M + 1)^2
+ * doubles (32 MiB) that every GPU loading the library holds until the process
+ * exits; M > COV_NOALLOC_MAX_M is rejected with COV_ERR_INVALID (message in
+ * cov_last_error(NULL)).  The first call on each device looks up the array's
+ * device address with that device current; make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's
+ * contents, so calls that overlap on the GPU race and must be serialised by
+ * the caller. */
+#define COV_NOALLOC_MAX_M 2047
+int cov_snr_noalloc(const double* d_C, int64_t ldc, const double* d_D, int64_t M, const int64_t* prefix,
+                    int n_prefix, double* d_snr, int* d_status, void* stream);
+
 const char* cov_last_error(const cov_handle* h);
 void cov_free(cov_handle* h);
 

@@ -24,6 +24,8 @@ int wl_cuda(cov_handle* h, cudaError_t e, const char* what) {
 
 static thread_local std::string g_init_err;
 
+void wl_set_global_error(const std::string& msg) { g_init_err = msg; }
+
 static const char* kStageNames[ST_COUNT] = {"tables", "counts", "spectra", "rows_T", "syrk_T", "gather",
                                             "rows_A", "syrk_1h", "rows_S", "syrk_ssc", "snr_pack",
                                             "snr_cholesky", "snr_prefix"};

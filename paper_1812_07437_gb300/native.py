@@ -33,7 +33,9 @@ COV_WHICH_B = 1
 COV_WHICH_JOINT = 2
 
 EXPORTED = ["cov_init", "cov_update", "cov_layout", "cov_counts", "cov_spectra", "cov_assemble", "cov_snr",
-            "cov_table", "cov_profile", "cov_stage_times", "cov_stage_name", "cov_last_error", "cov_free"]
+            "cov_table", "cov_profile", "cov_stage_times", "cov_stage_name", "cov_snr_noalloc", "cov_last_error",
+            "cov_free"]
+COV_NOALLOC_MAX_M = 2047
 N_STAGES = 13
 HAS_SPLIT_BF16 = True
 
@@ -82,6 +84,7 @@ def lib():
         L.cov_stage_times.argtypes = [P, P, P, C.c_int]
         L.cov_stage_name.argtypes = [C.c_int]
         L.cov_stage_name.restype = C.c_char_p
+        L.cov_snr_noalloc.argtypes = [P, i64, P, i64, P, C.c_int, P, P, P]
         L.cov_last_error.argtypes = [P]
         L.cov_last_error.restype = C.c_char_p
         L.cov_free.argtypes = [P]
