@@ -221,8 +221,21 @@ int wl_assemble(cov_handle* h, double* C, int64_t ldc, unsigned terms, int preci
     if ((rc = wl_rows_t(h, s))) return rc;
     wl_stage_end(h, tk, s);
     tk = wl_stage_begin(h, ST_SYRK_T, s);
-    if ((rc = wl_gemm_lower_fp64(h, h->Trows, K, h->Trows, K, h->Tmat, h->ntrow, h->ntrow, K, 1.0, 0.0, true, s)))
-      return rc;
+    if (precision == COV_FP64) {
+      if ((rc = wl_gemm_lower_fp64(h, h->Trows, K, h->Trows, K, h->Tmat, h->ntrow, h->ntrow, K, 1.0, 0.0, true, s)))
+        return rc;
+    } else {
+      size_t sb = 0;
+      wl_split_bytes(h->ntrow, (int)K, &sb);
+      if ((rc = ensure(h, (void**)&h->Thi, sb, "BF16 hi trispectrum rows"))) return rc;
+      if ((rc = ensure(h, (void**)&h->Tlo, sb, "BF16 lo trispectrum rows"))) return rc;
+      if ((rc = ensure(h, (void**)&h->Tscale, sizeof(double) * h->ntrow, "trispectrum row scales"))) return rc;
+      if ((rc = wl_split_rows(h, h->Trows, h->ntrow, (int)K, h->Thi, h->Tlo, h->Tscale, s))) return rc;
+      WL_CHECK(h, cudaMemsetAsync(h->Tmat, 0, sizeof(double) * h->ntrow * h->ntrow, s));
+      if ((rc = wl_syrk_tc_rows(h, h->Thi, h->Tlo, h->Tscale, h->ntrow, (int)(sb / 2 / h->ntrow), h->Tmat, h->ntrow,
+                                s)))
+        return rc;
+    }
     wl_stage_end(h, tk, s);
   }
   GatherArgs g{h->nt, h->nleg, terms, h->omega, h->rowdesc_d, h->Ps, h->B1hp, h->Tmat, h->ntrow, h->Nmodes, h->Ntri};

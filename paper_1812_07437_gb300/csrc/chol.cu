@@ -33,13 +33,18 @@ __global__ void k_snr_pack(int64_t Ms, const int* perm, const double* C, int64_t
   Wk[i * ldw + j] = C[hi * ldc + lo] / sqrt(C[pi * ldc + pi] * C[pj * ldc + pj]);
 }
 
-// in-place Cholesky of the kb x kb diagonal block at (k0, k0); one block
+// in-place Cholesky of the kb x kb diagonal block at (k0, k0); one block of
+// 256 threads, thread (tx, ty) owns rows ty + 16 r and columns tx + 16 c
 __global__ void k_potrf_diag(double* Wk, int64_t ldw, int64_t k0, int kb, int* status) {
   __shared__ double L[NB][NB + 1];
-  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
-    int i = e / kb, j = e % kb;
-    L[i][j] = (j <= i) ? Wk[(k0 + i) * ldw + k0 + j] : 0.0;
-  }
+  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      int i = ty + 16 * r, l = tx + 16 * c;
+      L[i][l] = (i < kb && l <= i) ? Wk[(k0 + i) * ldw + k0 + l] : 0.0;
+    }
   __syncthreads();
   for (int j = 0; j < kb; ++j) {
     if (threadIdx.x == 0) {
@@ -51,46 +56,69 @@ __global__ void k_potrf_diag(double* Wk, int64_t ldw, int64_t k0, int kb, int* s
       L[j][j] = sqrt(d);
     }
     __syncthreads();
-    double djj = L[j][j];
-    for (int i = j + 1 + threadIdx.x; i < kb; i += blockDim.x) L[i][j] /= djj;
-    __syncthreads();
-    for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
-      int i = e / kb, l = e % kb;
-      if (l > j && l <= i) L[i][l] -= L[i][j] * L[l][j];
+    double inv = 1.0 / L[j][j];
+    if (tx == (j & 15)) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        int i = ty + 16 * r;
+        if (i > j && i < kb) L[i][j] *= inv;
+      }
     }
     __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        int i = ty + 16 * r, l = tx + 16 * c;
+        if (l > j && l <= i && i < kb) L[i][l] -= L[i][j] * L[l][j];
+      }
+    __syncthreads();
   }
-  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
-    int i = e / kb, j = e % kb;
-    if (j <= i) Wk[(k0 + i) * ldw + k0 + j] = L[i][j];
-  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      int i = ty + 16 * r, l = tx + 16 * c;
+      if (i < kb && l <= i) Wk[(k0 + i) * ldw + k0 + l] = L[i][l];
+    }
 }
 
-// rows r in [r0, r1): x L11^T = a, one warp per row (column-oriented solve)
+#define TRSM_ROWS 64
+// rows r in [r0, r1): x L11^T = a; 8 warps per block, 8 rows per warp, one
+// warp per row at a time (column-oriented solve with a shuffle broadcast)
 __global__ void k_trsm_rows(double* Wk, int64_t ldw, int64_t k0, int kb, int64_t r0, int64_t r1) {
   __shared__ double L[NB][NB + 1];
-  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
-    int i = e / kb, j = e % kb;
-    L[i][j] = (j <= i) ? Wk[(k0 + i) * ldw + k0 + j] : 0.0;
-  }
-  __syncthreads();
-  int lane = threadIdx.x & 31;
-  int64_t r = r0 + (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  if (r >= r1) return;
-  double* row = Wk + r * ldw + k0;
-  double a0 = lane < kb ? row[lane] : 0.0;
-  double a1 = lane + 32 < kb ? row[lane + 32] : 0.0;
-  for (int j = 0; j < kb; ++j) {
-    double own = (j < 32) ? a0 : a1;
-    double xj = __shfl_sync(0xffffffffu, own, j & 31) / L[j][j];
-    if (lane == (j & 31)) {
-      if (j < 32) a0 = xj; else a1 = xj;
+  __shared__ double invd[NB];
+  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      int i = ty + 16 * r, l = tx + 16 * c;
+      L[i][l] = (i < kb && l <= i) ? Wk[(k0 + i) * ldw + k0 + l] : 0.0;
     }
-    if (lane > j && lane < kb) a0 -= xj * L[lane][j];
-    if (lane + 32 > j && lane + 32 < kb) a1 -= xj * L[lane + 32][j];
+  __syncthreads();
+  if (threadIdx.x < kb) invd[threadIdx.x] = 1.0 / L[threadIdx.x][threadIdx.x];
+  __syncthreads();
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int t = 0; t < TRSM_ROWS / 8; ++t) {
+    int64_t r = r0 + (int64_t)blockIdx.x * TRSM_ROWS + warp + 8 * t;
+    if (r >= r1) break;
+    double* row = Wk + r * ldw + k0;
+    double a0 = lane < kb ? row[lane] : 0.0;
+    double a1 = lane + 32 < kb ? row[lane + 32] : 0.0;
+    for (int j = 0; j < kb; ++j) {
+      double own = (j < 32) ? a0 : a1;
+      double xj = __shfl_sync(0xffffffffu, own, j & 31) * invd[j];
+      if (lane == (j & 31)) {
+        if (j < 32) a0 = xj; else a1 = xj;
+      }
+      if (lane > j && lane < kb) a0 -= xj * L[lane][j];
+      if (lane + 32 > j && lane + 32 < kb) a1 -= xj * L[lane + 32][j];
+    }
+    if (lane < kb) row[lane] = a0;
+    if (lane + 32 < kb) row[lane + 32] = a1;
   }
-  if (lane < kb) row[lane] = a0;
-  if (lane + 32 < kb) row[lane + 32] = a1;
 }
 
 __global__ void k_snr_prefix(int64_t Ms, const double* Wk, int64_t ldw, const int64_t* cnt, int nl, double* out) {
@@ -157,7 +185,7 @@ int wl_snr(cov_handle* h, const double* C, int64_t ldc, const double* D, int whi
     k_potrf_diag<<<1, 256, 0, s>>>(h->work, ldw, k0, kb, st);
     int64_t r0 = k0 + kb, r1 = Ms + 1;
     if (r1 > r0) {
-      k_trsm_rows<<<(unsigned)((r1 - r0 + 7) / 8), 256, 0, s>>>(h->work, ldw, k0, kb, r0, r1);
+      k_trsm_rows<<<(unsigned)((r1 - r0 + TRSM_ROWS - 1) / TRSM_ROWS), 256, 0, s>>>(h->work, ldw, k0, kb, r0, r1);
       int64_t n = r1 - r0;
       double* P = h->work + r0 * ldw + k0;
       double* Csub = h->work + r0 * ldw + r0;

@@ -32,7 +32,7 @@
 #define WL_FD_H 1.0e-3     // ln k step of the 4th-order differences
 
 // scalars kept on the device (index into h->scal)
-enum { SC_CHIMAX = 0, SC_AMP = 1, SC_NOISE = 2, SC_STATUS = 7, SC_N = 8 };
+enum { SC_CHIMAX = 0, SC_AMP = 1, SC_NOISE = 2, SC_D1 = 3, SC_STATUS = 7, SC_N = 8 };
 
 struct DevCosmo {
   double Om, Ob, h, ns, sigma8, w0, Tcmb;
@@ -87,6 +87,8 @@ struct cov_handle {
   int* tc_status = nullptr; // status word of the tensor-core contraction
   double* Trows = nullptr;  // [ntrow][K]
   double* Tmat = nullptr;   // [ntrow][ntrow] lower
+  uint16_t *Thi = nullptr, *Tlo = nullptr;  // split trispectrum rows (tensor-core form)
+  double* Tscale = nullptr;
   double* Srows = nullptr;  // [M][nchi]
   double* work = nullptr;   // Cholesky workspace (M+1)^2
   int64_t work_n = 0;
@@ -119,6 +121,7 @@ int wl_stage_begin(cov_handle* h, int stage, cudaStream_t s);
 void wl_stage_end(cov_handle* h, int token, cudaStream_t s);
 
 // ---- stage entry points (one per translation unit) -------------------------
+int wl_quadrature(cov_handle* h, cudaStream_t s);  // tables.cu
 int wl_tables(cov_handle* h, cudaStream_t s);   // tables.cu
 int wl_counts(cov_handle* h, cudaStream_t s);   // counts.cu
 int wl_spectra(cov_handle* h, double* d_D, cudaStream_t s);  // spectra.cu
@@ -130,6 +133,10 @@ int wl_gemm_lower_fp64(cov_handle* h, const double* A, int64_t lda, const double
                        cudaStream_t s);  // assemble.cu
 int wl_syrk_tc(cov_handle* h, double* d_C, int64_t ldc, cudaStream_t s);  // syrk_tc.cu
 int wl_split_bytes(int64_t M, int K, size_t* bytes);                      // syrk_tc.cu
+int wl_syrk_tc_rows(cov_handle* h, const void* hi, const void* lo, const double* rscale, int64_t rows, int Kp,
+                    double* C, int64_t ldc, cudaStream_t s);
+int wl_split_rows(cov_handle* h, const double* X, int64_t rows, int K, void* hi, void* lo, double* rscale,
+                  cudaStream_t s);
 
 // ---- device helpers ------------------------------------------------------------
 __device__ __forceinline__ DevCosmo dev_cosmo(const cov_cosmology& c) {

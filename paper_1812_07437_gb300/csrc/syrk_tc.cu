@@ -80,6 +80,38 @@ __global__ void k_rows_split(int64_t M, int nchi, int nm, int Kp, double inv_ome
   if (threadIdx.x == 0) rscale[a] = ldexp(1.0, ex);
 }
 
+// split already-built FP64 rows X[rows][K] into scaled BF16 hi/lo rows [rows][Kp]
+__global__ void k_split_rows(const double* X, int64_t rows, int K, int Kp, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                             double* rscale) {
+  __shared__ double sh[32];
+  int64_t a = blockIdx.x;
+  if (a >= rows) return;
+  const double* x = X + a * K;
+  double mx = 0.0;
+  for (int kk = threadIdx.x; kk < K; kk += blockDim.x) mx = fmax(mx, fabs(x[kk]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+    if (threadIdx.x == 0) sh[0] = t;
+  }
+  __syncthreads();
+  mx = sh[0];
+  int ex = 0;
+  if (mx > 0.0) frexp(mx, &ex);
+  double inv = ldexp(1.0, -ex);
+  for (int kk = threadIdx.x; kk < Kp; kk += blockDim.x) {
+    double v = (kk < K) ? x[kk] * inv : 0.0;
+    __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+    __nv_bfloat16 l = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
+    hi[a * Kp + kk] = h;
+    lo[a * Kp + kk] = l;
+  }
+  if (threadIdx.x == 0) rscale[a] = ldexp(1.0, ex);
+}
+
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -336,26 +368,38 @@ int wl_rows_split(cov_handle* h, cudaStream_t s) {
   return COV_OK;
 }
 
-int wl_syrk_tc(cov_handle* h, double* C, int64_t ldc, cudaStream_t s) {
-  int Kp = kpad(h->K);
+// C (lower, FP64) += (hi + lo)(hi + lo)^T scaled, without the lo lo^T term
+int wl_syrk_tc_rows(cov_handle* h, const void* hi, const void* lo, const double* rscale, int64_t rows, int Kp,
+                    double* C, int64_t ldc, cudaStream_t s) {
   CUtensorMap mhi, mlo;
   int rc;
-  if ((rc = make_map(h, &mhi, h->Ahi, h->M, Kp))) return rc;
-  if ((rc = make_map(h, &mlo, h->Alo, h->M, Kp))) return rc;
+  if ((rc = make_map(h, &mhi, (void*)hi, rows, Kp))) return rc;
+  if ((rc = make_map(h, &mlo, (void*)lo, rows, Kp))) return rc;
   static bool attr = false;
   if (!attr) {
     WL_CHECK(h, cudaFuncSetAttribute(k_syrk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
     attr = true;
   }
-  int64_t nt = (h->M + TC_BM - 1) / TC_BM;
+  if (!h->tc_status) WL_CHECK(h, cudaMalloc(&h->tc_status, sizeof(int)));
+  int64_t nt = (rows + TC_BM - 1) / TC_BM;
   int64_t nblk = nt * (nt + 1) / 2;
   WL_CHECK(h, cudaMemsetAsync(h->tc_status, 0, sizeof(int), s));
-  k_syrk_tc<<<(unsigned)nblk, 128, TC_SMEM, s>>>(mhi, mlo, h->M, Kp / TC_BK, (const double*)h->Ascale, C, ldc,
-                                                 h->tc_status);
+  k_syrk_tc<<<(unsigned)nblk, 128, TC_SMEM, s>>>(mhi, mlo, rows, Kp / TC_BK, rscale, C, ldc, h->tc_status);
   WL_LAUNCH(h, "k_syrk_tc");
   int st = 0;
   WL_CHECK(h, cudaMemcpyAsync(&st, h->tc_status, sizeof(int), cudaMemcpyDeviceToHost, s));
   WL_CHECK(h, cudaStreamSynchronize(s));
   if (st) return wl_fail(h, COV_ERR_TIMEOUT, "tensor-core contraction: a bounded mbarrier wait expired");
+  return COV_OK;
+}
+
+int wl_syrk_tc(cov_handle* h, double* C, int64_t ldc, cudaStream_t s) {
+  return wl_syrk_tc_rows(h, h->Ahi, h->Alo, h->Ascale, h->M, kpad(h->K), C, ldc, s);
+}
+
+int wl_split_rows(cov_handle* h, const double* X, int64_t rows, int K, void* hi, void* lo, double* rscale,
+                  cudaStream_t s) {
+  k_split_rows<<<(unsigned)rows, 256, 0, s>>>(X, rows, K, kpad(K), (__nv_bfloat16*)hi, (__nv_bfloat16*)lo, rscale);
+  WL_LAUNCH(h, "k_split_rows");
   return COV_OK;
 }

@@ -12,7 +12,9 @@ __global__ void k_gauss_legendre(int n, double* x, double* w) {
   if (i >= n) return;
   double zz = cos(WL_PI * (i + 0.75) / (n + 0.5));
   double pp = 1.0;
-  for (int it = 0; it < 100; ++it) {
+  // Newton from the cosine guess: quadratic convergence reaches double
+  // precision in a handful of steps; stop at 5e-16 or after 10 steps
+  for (int it = 0; it < 10; ++it) {
     double p1 = 1.0, p2 = 0.0;
     for (int j = 1; j <= n; ++j) {
       double p3 = p2;
@@ -22,7 +24,7 @@ __global__ void k_gauss_legendre(int n, double* x, double* w) {
     pp = n * (zz * p1 - p2) / (zz * zz - 1.0);
     double z1 = zz;
     zz = z1 - p1 / pp;
-    if (fabs(zz - z1) < 1e-16) break;
+    if (fabs(zz - z1) <= 5e-16) break;
   }
   double p1 = 1.0, p2 = 0.0;
   for (int j = 1; j <= n; ++j) {
@@ -35,9 +37,7 @@ __global__ void k_gauss_legendre(int n, double* x, double* w) {
   w[i] = 2.0 / ((1.0 - zz * zz) * pp * pp);
 }
 
-__global__ void k_chimax(cov_cosmology c, double zmax, const double* glx, const double* glw, double* scal) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) scal[SC_CHIMAX] = dev_chi_of_z(zmax, c, glx, glw);
-}
+__global__ void k_chimax(cov_cosmology c, double zmax, const double* glx, const double* glw, double* scal);
 
 // RK4 integration of the linear growth ODE in ln a from a = 1e-3 to a_t
 __device__ double dev_growth_raw(double at, const cov_cosmology& c) {
@@ -46,9 +46,8 @@ __device__ double dev_growth_raw(double at, const cov_cosmology& c) {
   double d = WL_A_INIT, dp = WL_A_INIT;
   double om = c.Om, ode = 1.0 - c.Om, w = c.w0;
   auto rhs = [&](double lna, double yd, double yp, double* fd, double* fp) {
-    double a = exp(lna);
-    double em = om / (a * a * a);
-    double ed = ode * pow(a, -3.0 * (1.0 + w));
+    double em = om * exp(-3.0 * lna);
+    double ed = ode * exp(-3.0 * (1.0 + w) * lna);
     double e2 = em + ed;
     double dlnh = 0.5 * (-3.0 * em - 3.0 * (1.0 + w) * ed) / e2;
     *fd = yp;
@@ -67,24 +66,33 @@ __device__ double dev_growth_raw(double at, const cov_cosmology& c) {
   return d;
 }
 
-// line-of-sight nodes: chi_n (GL on [0, chi_max]), weights, z(chi_n), D(z_n)
+// chi(z_max) and the growth integration carried to a = 1 (shared by all nodes)
+__global__ void k_chimax(cov_cosmology c, double zmax, const double* glx, const double* glw, double* scal) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    scal[SC_CHIMAX] = dev_chi_of_z(zmax, c, glx, glw);
+    scal[SC_D1] = dev_growth_raw(1.0, c);
+  }
+}
+
+// line-of-sight nodes: chi_n (GL on [0, chi_max]), weights, z(chi_n), D(z_n);
+// one node per block so that the sequential RK4 runs spread over the SMs
 __global__ void k_los(cov_cosmology c, int nchi, const double* glcx, const double* glcw, const double* gl64x,
                       const double* gl64w, const double* scal, double* chi, double* wchi, double* z, double* D) {
-  int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= nchi) return;
+  int n = blockIdx.x;
+  if (n >= nchi || threadIdx.x != 0) return;
   double cm = scal[SC_CHIMAX];
   double ch = 0.5 * cm * (glcx[n] + 1.0);
   chi[n] = ch;
   wchi[n] = 0.5 * cm * glcw[n];
   double zz = ch / WL_C_OVER_H0;
-  for (int it = 0; it < 100; ++it) {
+  for (int it = 0; it < 40; ++it) {
     double f = dev_chi_of_z(zz, c, gl64x, gl64w) - ch;
     double step = f / WL_C_OVER_H0 * dev_E(zz, c);
     zz -= step;
     if (fabs(step) < 1e-15 * (1.0 + zz)) break;
   }
   z[n] = zz;
-  D[n] = dev_growth_raw(1.0 / (1.0 + zz), c) / dev_growth_raw(1.0, c);
+  D[n] = dev_growth_raw(1.0 / (1.0 + zz), c) / scal[SC_D1];
 }
 
 // sigma_8 normalisation: amplitude A of P_lin(k,0) = A k^ns T^2
@@ -312,15 +320,21 @@ __global__ void k_sigw2(cov_cosmology c, double theta, const double* chi, const 
   if (threadIdx.x == 0) out[n] = 4.0 / (2.0 * WL_PI) * s * D[n] * D[n];
 }
 
+// quadrature nodes depend on no cosmology: built once per handle
+int wl_quadrature(cov_handle* h, cudaStream_t s) {
+  k_gauss_legendre<<<1, 64, 0, s>>>(WL_N_GL_CHI, h->gl64x, h->gl64w);
+  k_gauss_legendre<<<(WL_N_K + 127) / 128, 128, 0, s>>>(WL_N_K, h->glkx, h->glkw);
+  k_gauss_legendre<<<(h->nchi + 127) / 128, 128, 0, s>>>(h->nchi, h->glcx, h->glcw);
+  WL_LAUNCH(h, "k_gauss_legendre");
+  return COV_OK;
+}
+
 int wl_tables(cov_handle* h, cudaStream_t s) {
   const cov_cosmology c = h->cosmo;
   const cov_bins b = h->bins;
   const cov_nz nz = h->nz;
-  k_gauss_legendre<<<1, 64, 0, s>>>(WL_N_GL_CHI, h->gl64x, h->gl64w);
-  k_gauss_legendre<<<(WL_N_K + 127) / 128, 128, 0, s>>>(WL_N_K, h->glkx, h->glkw);
-  k_gauss_legendre<<<(h->nchi + 127) / 128, 128, 0, s>>>(h->nchi, h->glcx, h->glcw);
   k_chimax<<<1, 1, 0, s>>>(c, nz.zmax, h->gl64x, h->gl64w, h->scal);
-  k_los<<<(h->nchi + 63) / 64, 64, 0, s>>>(c, h->nchi, h->glcx, h->glcw, h->gl64x, h->gl64w, h->scal, h->chi,
+  k_los<<<h->nchi, 32, 0, s>>>(c, h->nchi, h->glcx, h->glcw, h->gl64x, h->gl64w, h->scal, h->chi,
                                             h->wchi, h->z, h->D);
   k_amplitude<<<1, 256, 0, s>>>(c, h->glkx, h->glkw, h->scal);
   k_sigma<<<h->nm, 256, 0, s>>>(c, b, h->glkx, h->glkw, h->scal, h->m, h->om, h->sig0, h->dlns);
