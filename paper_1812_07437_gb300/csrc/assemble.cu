@@ -1,7 +1,8 @@
 // Covariance assembly (paper Sec. 3.2 and Appendix B):
+//  * the 1-halo contraction stores the lower triangle first (no clear pass);
 //  * k_gather   Gaussian PP/BB, BB+PT and PB product terms, element by
-//               element over the lower triangle (it initialises every lower
-//               element of C, so no separate clear pass is needed);
+//               element over the lower triangle, added on top (or stored when
+//               the 1-halo term is not requested);
 //  * k_gemm_lower  C = alpha A B^T + beta C on the lower triangle in FP64:
 //               the 1-halo (chi, M) contraction (FP64 form), the 1-halo
 //               trispectrum table of the PT term and the rank-N_chi
@@ -105,7 +106,7 @@ __device__ __forceinline__ void tri_tile(int64_t id, int64_t* ti, int64_t* tj) {
   *tj = id - i * (i + 1) / 2;
 }
 
-__global__ void k_gather(GatherArgs g, int64_t M, double* C, int64_t ldc) {
+__global__ void k_gather(GatherArgs g, int64_t M, double* C, int64_t ldc, int accumulate) {
   __shared__ int32_t rdA[32 * 8], rdB[32 * 8];
   int64_t ti, tj;
   tri_tile(blockIdx.x, &ti, &tj);
@@ -121,7 +122,8 @@ __global__ void k_gather(GatherArgs g, int64_t M, double* C, int64_t ldc) {
   for (int rr = threadIdx.y; rr < 32; rr += 8) {
     int64_t a = a0 + rr;
     if (a >= M || b >= M || b > a) continue;
-    C[a * ldc + b] = gather_element(g, rdA + rr * 8, rdB + threadIdx.x * 8);
+    double v = gather_element(g, rdA + rr * 8, rdB + threadIdx.x * 8);
+    C[a * ldc + b] = accumulate ? C[a * ldc + b] + v : v;
   }
 }
 
@@ -213,7 +215,7 @@ static int ensure(cov_handle* h, void** p, size_t bytes, const char* what) {
 int wl_assemble(cov_handle* h, double* C, int64_t ldc, unsigned terms, int precision, cudaStream_t s) {
   int rc;
   const int64_t M = h->M, K = h->K;
-  // 1. per-element product terms; initialises the lower triangle
+  // 1. the 1-halo trispectrum table of the PT term
   if (terms & COV_TERM_BBPT) {
     if ((rc = ensure(h, (void**)&h->Trows, sizeof(double) * h->ntrow * K, "trispectrum rows"))) return rc;
     if ((rc = ensure(h, (void**)&h->Tmat, sizeof(double) * h->ntrow * h->ntrow, "trispectrum table"))) return rc;
@@ -231,20 +233,12 @@ int wl_assemble(cov_handle* h, double* C, int64_t ldc, unsigned terms, int preci
       if ((rc = ensure(h, (void**)&h->Tlo, sb, "BF16 lo trispectrum rows"))) return rc;
       if ((rc = ensure(h, (void**)&h->Tscale, sizeof(double) * h->ntrow, "trispectrum row scales"))) return rc;
       if ((rc = wl_split_rows(h, h->Trows, h->ntrow, (int)K, h->Thi, h->Tlo, h->Tscale, s))) return rc;
-      WL_CHECK(h, cudaMemsetAsync(h->Tmat, 0, sizeof(double) * h->ntrow * h->ntrow, s));
-      if ((rc = wl_syrk_tc_rows(h, h->Thi, h->Tlo, h->Tscale, h->ntrow, (int)(sb / 2 / h->ntrow), h->Tmat, h->ntrow,
-                                s)))
+      if ((rc = wl_syrk_tc_rows(h, h->Thi, h->Tlo, h->Tscale, h->ntrow, wl_kpad((int)K), h->Tmat, h->ntrow, s)))
         return rc;
     }
     wl_stage_end(h, tk, s);
   }
-  GatherArgs g{h->nt, h->nleg, terms, h->omega, h->rowdesc_d, h->Ps, h->B1hp, h->Tmat, h->ntrow, h->Nmodes, h->Ntri};
-  int64_t nt32 = (M + 31) / 32;
-  int tg = wl_stage_begin(h, ST_GATHER, s);
-  k_gather<<<(unsigned)(nt32 * (nt32 + 1) / 2), dim3(32, 8), 0, s>>>(g, M, C, ldc);
-  WL_LAUNCH(h, "k_gather");
-  wl_stage_end(h, tg, s);
-  // 2. 1-halo (chi, M) contraction
+  // 2. 1-halo (chi, M) contraction: the first writer of the lower triangle
   if (terms & COV_TERM_1H) {
     if (precision == COV_FP64) {
       if ((rc = ensure(h, (void**)&h->A, sizeof(double) * M * K, "FP64 factor rows"))) return rc;
@@ -252,7 +246,7 @@ int wl_assemble(cov_handle* h, double* C, int64_t ldc, unsigned terms, int preci
       if ((rc = wl_rows_a(h, s))) return rc;
       wl_stage_end(h, tk, s);
       tk = wl_stage_begin(h, ST_SYRK_1H, s);
-      if ((rc = wl_gemm_lower_fp64(h, h->A, K, h->A, K, C, ldc, M, K, 1.0, 1.0, true, s))) return rc;
+      if ((rc = wl_gemm_lower_fp64(h, h->A, K, h->A, K, C, ldc, M, K, 1.0, 0.0, true, s))) return rc;
       wl_stage_end(h, tk, s);
     } else {
       size_t sb = 0;
@@ -269,6 +263,14 @@ int wl_assemble(cov_handle* h, double* C, int64_t ldc, unsigned terms, int preci
       wl_stage_end(h, tk, s);
     }
   }
+  // per-element product terms: initialise C when no 1-halo term ran
+  GatherArgs g{h->nt, h->nleg, terms, h->omega, h->rowdesc_d, h->Ps, h->B1hp, h->Tmat, h->ntrow, h->Nmodes, h->Ntri};
+  int64_t nt32 = (M + 31) / 32;
+  int tg = wl_stage_begin(h, ST_GATHER, s);
+  k_gather<<<(unsigned)(nt32 * (nt32 + 1) / 2), dim3(32, 8), 0, s>>>(g, M, C, ldc,
+                                                                  (terms & COV_TERM_1H) ? 1 : 0);
+  WL_LAUNCH(h, "k_gather");
+  wl_stage_end(h, tg, s);
   // 3. super-sample term, rank N_chi
   if (terms & COV_TERM_SSC) {
     if ((rc = ensure(h, (void**)&h->Srows, sizeof(double) * M * h->nchi, "SSC rows"))) return rc;

@@ -133,6 +133,7 @@ int wl_gemm_lower_fp64(cov_handle* h, const double* A, int64_t lda, const double
                        cudaStream_t s);  // assemble.cu
 int wl_syrk_tc(cov_handle* h, double* d_C, int64_t ldc, cudaStream_t s);  // syrk_tc.cu
 int wl_split_bytes(int64_t M, int K, size_t* bytes);                      // syrk_tc.cu
+int wl_kpad(int K);  // K padded to the contraction's K granularity
 int wl_syrk_tc_rows(cov_handle* h, const void* hi, const void* lo, const double* rscale, int64_t rows, int Kp,
                     double* C, int64_t ldc, cudaStream_t s);
 int wl_split_rows(cov_handle* h, const double* X, int64_t rows, int K, void* hi, void* lo, double* rscale,

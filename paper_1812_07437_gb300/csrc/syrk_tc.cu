@@ -4,33 +4,37 @@
 //   * k_rows_split builds each factor row in FP64, scales it by an exact power
 //     of two s_a so that its largest entry lies in [0.5, 1), and splits it into
 //     two BF16 rows, hi = bf16(a / s_a), lo = bf16(a / s_a - hi).
-//   * k_syrk_tc computes, per 128 x 128 lower-triangle tile, the FP32 sum
+//   * k_syrk_tc256 computes, per 256 x 256 lower-triangle tile, the FP32 sum
 //     hi_i hi_j + hi_i lo_j + lo_i hi_j over K on the tcgen05 tensor cores
-//     (kind::f16, BF16 operands, FP32 accumulator in TMEM) and adds
-//     acc * s_i * s_j into the FP64 covariance.
+//     (kind::f16, BF16 operands, FP32 accumulators in TMEM) and stores
+//     acc * s_i * s_j into the FP64 lower triangle (first writer of C).
 //
-// Per CTA (128 threads): warp 0 / lane 0 issues TMA loads of the four
-// 128 x 64 operand tiles of a K block (hi/lo rows of tile I and of tile J,
-// 128B-swizzled) into a 3-stage shared-memory ring; warp 1 / lane 0 issues the
-// 12 MMAs of 128 x 128 x 16 per K block and releases each stage with
-// tcgen05.commit; after the last block all four warps read the accumulator
-// from TMEM (tcgen05.ld 32x32b) and write the tile.  Every wait on an mbarrier
-// is bounded: on expiry the kernel raises a status word, stops issuing work,
-// waits (bounded) for its own copies, frees its TMEM and returns.
+// The split rows are stored tile-blocked (256 rows x 32 K contiguous) so that
+// every TMA box is one contiguous 16 KB block of HBM.  Per CTA (128 threads):
+// warp 0 / lane 0 issues the TMA loads of a K block (hi/lo of the 256 I rows
+// and of the 256 J rows, 64-byte swizzle) into a 3-stage shared-memory ring;
+// warp 1 / lane 0 issues the 12 MMAs of 128 x 256 x 16 per K block into two
+// TMEM accumulators (row halves) and releases each stage with tcgen05.commit;
+// after the last block all four warps read the accumulators (tcgen05.ld
+// 32x32b) and write the tile.  Every wait on an mbarrier is bounded: on expiry
+// the kernel raises a status word, stops issuing work, waits (bounded) for its
+// own copies, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include "common.cuh"
 
-#define TC_BM 128
-#define TC_BN 128
-#define TC_BK 64
-#define TC_STAGES 3
-#define TC_TILE_BYTES (TC_BM * TC_BK * 2)           // 16 KB per operand tile
-#define TC_STAGE_BYTES (4 * TC_TILE_BYTES)          // hi_I, lo_I, hi_J, lo_J
-#define TC_SMEM (TC_STAGES * TC_STAGE_BYTES + 1024) // + alignment slack
 #define TC_SPIN_LIMIT (1u << 22)
+#define TW_BM 256
+#define TW_BK 32
+
+// Tile-blocked operand layout: entry (r, k) of a split row array lives at
+// ((r / 256) * nk + k / 32) * 8192 + (r % 256) * 32 + k % 32, with nk = Kp / 32,
+// so that each 256 x 32 TMA box is one contiguous 16 KB block in HBM.
+__device__ __forceinline__ int64_t blk_off(int64_t r, int k, int nk) {
+  return (((r >> 8) * nk + (k >> 5)) << 13) + ((r & 255) << 5) + (k & 31);
+}
 
 // ---------------------------------------------------------------- row split
 __global__ void k_rows_split(int64_t M, int nchi, int nm, int Kp, double inv_omega, double rho, const int32_t* rd,
@@ -70,12 +74,13 @@ __global__ void k_rows_split(int64_t M, int nchi, int nm, int Kp, double inv_ome
   int ex = 0;
   if (mx > 0.0) frexp(mx, &ex);
   double inv = ldexp(1.0, -ex);
+  int nk = Kp / TW_BK;
   for (int kk = threadIdx.x; kk < Kp; kk += blockDim.x) {
     double x = (kk < K) ? value(kk) * inv : 0.0;
     __nv_bfloat16 h = __float2bfloat16_rn((float)x);
     __nv_bfloat16 l = __float2bfloat16_rn((float)(x - (double)__bfloat162float(h)));
-    hi[a * Kp + kk] = h;
-    lo[a * Kp + kk] = l;
+    hi[blk_off(a, kk, nk)] = h;
+    lo[blk_off(a, kk, nk)] = l;
   }
   if (threadIdx.x == 0) rscale[a] = ldexp(1.0, ex);
 }
@@ -102,12 +107,13 @@ __global__ void k_split_rows(const double* X, int64_t rows, int K, int Kp, __nv_
   int ex = 0;
   if (mx > 0.0) frexp(mx, &ex);
   double inv = ldexp(1.0, -ex);
+  int nk = Kp / TW_BK;
   for (int kk = threadIdx.x; kk < Kp; kk += blockDim.x) {
     double v = (kk < K) ? x[kk] * inv : 0.0;
     __nv_bfloat16 h = __float2bfloat16_rn((float)v);
     __nv_bfloat16 l = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
-    hi[a * Kp + kk] = h;
-    lo[a * Kp + kk] = l;
+    hi[blk_off(a, kk, nk)] = h;
+    lo[blk_off(a, kk, nk)] = l;
   }
   if (threadIdx.x == 0) rscale[a] = ldexp(1.0, ex);
 }
@@ -153,16 +159,6 @@ __device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* ba
       : "memory");
 }
 
-__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);        // start address
-  d |= (uint64_t)1 << 16;                        // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;              // stride byte offset: 8 rows x 128 B
-  d |= (uint64_t)1 << 46;                        // descriptor version (sm_100 family)
-  d |= (uint64_t)2 << 61;                        // SWIZZLE_128B
-  return d;
-}
-
 __device__ __forceinline__ void umma_bf16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
@@ -191,17 +187,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// instruction descriptor: kind::f16, BF16 x BF16 -> FP32, both K-major, M = 128, N = 128
-__device__ __forceinline__ uint32_t idesc_bf16_128x128() {
-  uint32_t d = 0;
-  d |= 1u << 4;                 // D format FP32
-  d |= 1u << 7;                 // A format BF16
-  d |= 1u << 10;                // B format BF16
-  d |= (uint32_t)(TC_BN >> 3) << 17;
-  d |= (uint32_t)(TC_BM >> 4) << 24;
-  return d;
-}
-
 __device__ __forceinline__ void tri_tile_tc(int64_t id, int64_t* ti, int64_t* tj) {
   int64_t i = (int64_t)((sqrt(8.0 * (double)id + 1.0) - 1.0) * 0.5);
   while (i * (i + 1) / 2 > id) --i;
@@ -210,12 +195,53 @@ __device__ __forceinline__ void tri_tile_tc(int64_t id, int64_t* ti, int64_t* tj
   *tj = id - i * (i + 1) / 2;
 }
 
+// ---------------------------------------------------------------- 256 x 256 tiles
+// One CTA per 256 x 256 lower tile: rows I0..I0+255 against rows J0..J0+255.
+// Two TMEM accumulators of 128 x 256 FP32 (all 512 columns), D_h for the row
+// half h.  K blocks of 32 BF16 (64-byte rows, SWIZZLE_64B); a stage holds
+// hi/lo of the 256 I rows and hi/lo of the 256 J rows (4 x 16 KB) and feeds
+// 12 MMAs of 128 x 256 x 16 (2 halves x 2 K steps x 3 products).
+#define TW_STAGES 3
+#define TW_OP_BYTES (TW_BM * TW_BK * 2)              // 16 KB per operand panel
+#define TW_STAGE_BYTES (4 * TW_OP_BYTES)             // 64 KB
+#define TW_SMEM (TW_STAGES * TW_STAGE_BYTES + 1024)
+
+#define TW_PREFETCH 16
+
+// TMA prefetch of one box into L2 (no shared memory, no completion signal)
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int c0, int c1) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"((uint64_t)map), "r"(c0),
+               "r"(c1)
+               : "memory");
+}
+
+__device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);        // start address
+  d |= (uint64_t)1 << 16;                        // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;               // stride byte offset: 8 rows x 64 B
+  d |= (uint64_t)1 << 46;                        // descriptor version (sm_100 family)
+  d |= (uint64_t)4 << 61;                        // SWIZZLE_64B
+  return d;
+}
+
+// kind::f16, BF16 x BF16 -> FP32, K-major, M = 128, N = 256
+__device__ __forceinline__ uint32_t idesc_bf16_128x256() {
+  uint32_t d = 0;
+  d |= 1u << 4;
+  d |= 1u << 7;
+  d |= 1u << 10;
+  d |= (uint32_t)(256 >> 3) << 17;
+  d |= (uint32_t)(128 >> 4) << 24;
+  return d;
+}
+
 __global__ void __launch_bounds__(128, 1)
-    k_syrk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, int64_t M,
-              int nk, const double* __restrict__ rscale, double* C, int64_t ldc, int* status) {
+    k_syrk_tc256(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, int64_t M,
+                 int nk, const double* __restrict__ rscale, double* C, int64_t ldc, int* status) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar[TC_STAGES];
-  __shared__ __align__(8) uint64_t empty_bar[TC_STAGES];
+  __shared__ __align__(8) uint64_t full_bar[TW_STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[TW_STAGES];
   __shared__ __align__(8) uint64_t acc_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_flag;
@@ -224,11 +250,11 @@ __global__ void __launch_bounds__(128, 1)
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t ti, tj;
   tri_tile_tc(blockIdx.x, &ti, &tj);
-  int row_i = (int)(ti * TC_BM), row_j = (int)(tj * TC_BN);
+  int row_i = (int)(ti * TW_BM), row_j = (int)(tj * TW_BM);
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
-    for (int s = 0; s < TC_STAGES; ++s) {
+    for (int s = 0; s < TW_STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
@@ -238,7 +264,7 @@ __global__ void __launch_bounds__(128, 1)
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
-                 "r"(TC_BN));
+                 "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -246,81 +272,107 @@ __global__ void __launch_bounds__(128, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   uint32_t tmem = tmem_base_sh;
 
+  // All CTAs sweep K in the same order so that the ~M/256 CTAs sharing an
+  // operand panel read it from L2 at about the same time; the producer also
+  // prefetches the K block TW_PREFETCH steps ahead into L2, so the HBM latency
+  // is hidden in L2 instead of in the shared-memory ring.
   if (warp == 0 && lane == 0) {
-    // TMA producer
     int issued = 0;
+    for (int kb = 0; kb < TW_PREFETCH && kb < nk; ++kb) {
+      tma_prefetch_2d(&map_hi, 0, (int)((ti * nk + kb) * TW_BM));
+      tma_prefetch_2d(&map_lo, 0, (int)((ti * nk + kb) * TW_BM));
+      tma_prefetch_2d(&map_hi, 0, (int)((tj * nk + kb) * TW_BM));
+      tma_prefetch_2d(&map_lo, 0, (int)((tj * nk + kb) * TW_BM));
+    }
     for (int kb = 0; kb < nk; ++kb) {
-      int s = kb % TC_STAGES;
-      uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
+      int s = kb % TW_STAGES;
+      uint32_t ph = (uint32_t)(kb / TW_STAGES) & 1u;
       if (!mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag, status)) break;
       issued = kb + 1;
-      uint8_t* st = smem + (size_t)s * TC_STAGE_BYTES;
-      mbar_expect_tx(&full_bar[s], TC_STAGE_BYTES);
-      int kc = kb * TC_BK;
-      tma_load_2d(&map_hi, &full_bar[s], st + 0 * TC_TILE_BYTES, kc, row_i);
-      tma_load_2d(&map_lo, &full_bar[s], st + 1 * TC_TILE_BYTES, kc, row_i);
-      tma_load_2d(&map_hi, &full_bar[s], st + 2 * TC_TILE_BYTES, kc, row_j);
-      tma_load_2d(&map_lo, &full_bar[s], st + 3 * TC_TILE_BYTES, kc, row_j);
+      uint8_t* st = smem + (size_t)s * TW_STAGE_BYTES;
+      mbar_expect_tx(&full_bar[s], TW_STAGE_BYTES);
+      int yi = (int)((ti * nk + kb) * TW_BM), yj = (int)((tj * nk + kb) * TW_BM);
+      if (kb + TW_PREFETCH < nk) {
+        int pi = yi + TW_PREFETCH * TW_BM, pj = yj + TW_PREFETCH * TW_BM;
+        tma_prefetch_2d(&map_hi, 0, pi);
+        tma_prefetch_2d(&map_lo, 0, pi);
+        tma_prefetch_2d(&map_hi, 0, pj);
+        tma_prefetch_2d(&map_lo, 0, pj);
+      }
+      tma_load_2d(&map_hi, &full_bar[s], st + 0 * TW_OP_BYTES, 0, yi);
+      tma_load_2d(&map_lo, &full_bar[s], st + 1 * TW_OP_BYTES, 0, yi);
+      tma_load_2d(&map_hi, &full_bar[s], st + 2 * TW_OP_BYTES, 0, yj);
+      tma_load_2d(&map_lo, &full_bar[s], st + 3 * TW_OP_BYTES, 0, yj);
     }
     if (abort_flag) {
-      // drain: wait (bounded) until the copies of the last ring of stages have landed
-      for (int kb = issued - TC_STAGES < 0 ? 0 : issued - TC_STAGES; kb < issued; ++kb) {
-        uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
-        for (uint32_t i = 0; i < TC_SPIN_LIMIT && !mbar_try(&full_bar[kb % TC_STAGES], ph); ++i) {
+      for (int kb = issued - TW_STAGES < 0 ? 0 : issued - TW_STAGES; kb < issued; ++kb) {
+        uint32_t ph = (uint32_t)(kb / TW_STAGES) & 1u;
+        for (uint32_t i = 0; i < TC_SPIN_LIMIT && !mbar_try(&full_bar[kb % TW_STAGES], ph); ++i) {
         }
       }
     }
   } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    const uint32_t idesc = idesc_bf16_128x128();
-    bool ok = true;
-    for (int kb = 0; kb < nk && ok; ++kb) {
-      int s = kb % TC_STAGES;
-      uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
-      if (!mbar_wait(&full_bar[s], ph, &abort_flag, status)) {
-        ok = false;
-        break;
-      }
+    const uint32_t idesc = idesc_bf16_128x256();
+    for (int kb = 0; kb < nk; ++kb) {
+      int s = kb % TW_STAGES;
+      uint32_t ph = (uint32_t)(kb / TW_STAGES) & 1u;
+      if (!mbar_wait(&full_bar[s], ph, &abort_flag, status)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      uint32_t st = smem_u32(smem + (size_t)s * TC_STAGE_BYTES);
-      uint32_t a_hi = st, a_lo = st + TC_TILE_BYTES, b_hi = st + 2 * TC_TILE_BYTES, b_lo = st + 3 * TC_TILE_BYTES;
+      uint32_t st = smem_u32(smem + (size_t)s * TW_STAGE_BYTES);
+      uint32_t a_hi = st, a_lo = st + TW_OP_BYTES, b_hi = st + 2 * TW_OP_BYTES, b_lo = st + 3 * TW_OP_BYTES;
 #pragma unroll
-      for (int k = 0; k < TC_BK / 16; ++k) {
-        uint32_t off = k * 32;  // 16 BF16 along K inside the 128-byte swizzle row
-        uint32_t first = (kb == 0 && k == 0) ? 0u : 1u;
-        umma_bf16(tmem, umma_desc_sw128(a_hi + off), umma_desc_sw128(b_hi + off), idesc, first);
-        umma_bf16(tmem, umma_desc_sw128(a_hi + off), umma_desc_sw128(b_lo + off), idesc, 1u);
-        umma_bf16(tmem, umma_desc_sw128(a_lo + off), umma_desc_sw128(b_hi + off), idesc, 1u);
+      for (int h = 0; h < 2; ++h) {
+        uint32_t dt = tmem + (uint32_t)(256 * h);
+        uint32_t aoff = (uint32_t)(h * 128 * 64);  // 128 rows x 64 B into the A panel
+#pragma unroll
+        for (int k = 0; k < TW_BK / 16; ++k) {
+          uint32_t off = k * 32;
+          uint32_t first = (kb == 0 && k == 0) ? 0u : 1u;
+          umma_bf16(dt, umma_desc_sw64(a_hi + aoff + off), umma_desc_sw64(b_hi + off), idesc, first);
+          umma_bf16(dt, umma_desc_sw64(a_hi + aoff + off), umma_desc_sw64(b_lo + off), idesc, 1u);
+          umma_bf16(dt, umma_desc_sw64(a_lo + aoff + off), umma_desc_sw64(b_hi + off), idesc, 1u);
+        }
       }
       umma_commit(&empty_bar[s]);
     }
     umma_commit(&acc_bar);
   }
   __syncwarp();
-  // epilogue: all four warps (warp w owns TMEM lanes 32w .. 32w+31)
   bool have = mbar_wait(&acc_bar, 0u, &abort_flag, status);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (have && !abort_flag) {
-    int64_t gi = (int64_t)row_i + warp * 32 + lane;
-    double si = (gi < M) ? rscale[gi] : 0.0;
+    // Epilogue: C = s_i s_j acc (plain stores; this contraction is the first
+    // writer of the tile).  Each warp stages a 32 x 32 block through the idle
+    // shared-memory ring (transpose) so that every store instruction writes 32
+    // consecutive doubles of one row.
+    double* stg = (double*)smem + warp * (32 * 33);
 #pragma unroll 1
-    for (int c = 0; c < TC_BN / 32; ++c) {
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
-      if (gi < M) {
-        double* crow = C + gi * ldc;
+    for (int h = 0; h < 2; ++h) {
+      int64_t r0 = (int64_t)row_i + 128 * h + warp * 32;
+      int64_t gi = r0 + lane;
+      double si = (gi < M) ? rscale[gi] : 0.0;
+#pragma unroll 1
+      for (int c = 0; c < 8; ++c) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(256 * h + c * 32), v);
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) {
-          int64_t gj = (int64_t)row_j + c * 32 + jj;
-          if (gj < M && gj <= gi) crow[gj] += (double)v[jj] * si * rscale[gj];
+        for (int jj = 0; jj < 32; ++jj) stg[lane * 33 + jj] = (double)v[jj] * si;
+        __syncwarp();
+        int64_t gj = (int64_t)row_j + c * 32 + lane;
+        double sj = (gj < M) ? rscale[gj] : 0.0;
+#pragma unroll 4
+        for (int rr = 0; rr < 32; ++rr) {
+          int64_t gr = r0 + rr;
+          if (gr < M && gj < M && gj <= gr) C[gr * ldc + gj] = stg[rr * 33 + lane] * sj;
         }
+        __syncwarp();
       }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
   }
 }
 
@@ -338,29 +390,45 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
+// 2D view of the blocked array: inner dimension 32 (64 B rows), outer
+// dimension ntiles * nk * 256 block rows; box 32 x 256 = one 16 KB block
 static int make_map(cov_handle* h, CUtensorMap* map, void* base, int64_t rows, int64_t kp) {
   auto fn = encode_fn();
   if (!fn) return wl_fail(h, COV_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
-  cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
-  cuuint32_t box[2] = {TC_BK, TC_BM};
+  int64_t ntiles = (rows + TW_BM - 1) / TW_BM;
+  cuuint64_t dims[2] = {(cuuint64_t)TW_BK, (cuuint64_t)(ntiles * (kp / TW_BK) * TW_BM)};
+  cuuint64_t strides[1] = {(cuuint64_t)TW_BK * 2};
+  cuuint32_t box[2] = {(cuuint32_t)TW_BK, (cuuint32_t)TW_BM};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return wl_fail(h, COV_ERR_CUDA, "cuTensorMapEncodeTiled failed");
   return COV_OK;
 }
 
-static inline int kpad(int K) { return (K + TC_BK - 1) / TC_BK * TC_BK; }
+static inline int kpad(int K) { return (K + 63) / 64 * 64; }
+int wl_kpad(int K) { return kpad(K); }
 
+// bytes of one split array: rows padded to whole 256-row tiles (zero rows)
 int wl_split_bytes(int64_t M, int K, size_t* bytes) {
-  *bytes = (size_t)M * kpad(K) * 2;
+  *bytes = (size_t)((M + TW_BM - 1) / TW_BM) * TW_BM * kpad(K) * 2;
+  return COV_OK;
+}
+
+// the rows past M in the last 256-row tile must read as zero
+static int zero_last_tile(cov_handle* h, void* base, int64_t rows, int K, cudaStream_t s) {
+  if (rows % TW_BM == 0) return COV_OK;
+  int64_t nk = kpad(K) / TW_BK;
+  int64_t first = ((rows / TW_BM) * nk) * (int64_t)TW_BM * TW_BK;
+  WL_CHECK(h, cudaMemsetAsync((uint16_t*)base + first, 0, (size_t)nk * TW_BM * TW_BK * 2, s));
   return COV_OK;
 }
 
 int wl_rows_split(cov_handle* h, cudaStream_t s) {
   double rho = WL_RHO_CRIT0 * h->cosmo.Om;
+  if (int rc = zero_last_tile(h, h->Ahi, h->M, h->K, s)) return rc;
+  if (int rc = zero_last_tile(h, h->Alo, h->M, h->K, s)) return rc;
   k_rows_split<<<(unsigned)h->M, 256, 0, s>>>(h->M, h->nchi, h->nm, kpad(h->K), 1.0 / h->omega, rho, h->rowdesc_d,
                                                h->chi, h->wchi, h->W, h->m, h->om, h->f, h->U,
                                                (__nv_bfloat16*)h->Ahi, (__nv_bfloat16*)h->Alo, (double*)h->Ascale);
@@ -368,7 +436,7 @@ int wl_rows_split(cov_handle* h, cudaStream_t s) {
   return COV_OK;
 }
 
-// C (lower, FP64) += (hi + lo)(hi + lo)^T scaled, without the lo lo^T term
+// C (lower, FP64) = (hi + lo)(hi + lo)^T scaled, without the lo lo^T term
 int wl_syrk_tc_rows(cov_handle* h, const void* hi, const void* lo, const double* rscale, int64_t rows, int Kp,
                     double* C, int64_t ldc, cudaStream_t s) {
   CUtensorMap mhi, mlo;
@@ -377,15 +445,15 @@ int wl_syrk_tc_rows(cov_handle* h, const void* hi, const void* lo, const double*
   if ((rc = make_map(h, &mlo, (void*)lo, rows, Kp))) return rc;
   static bool attr = false;
   if (!attr) {
-    WL_CHECK(h, cudaFuncSetAttribute(k_syrk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    WL_CHECK(h, cudaFuncSetAttribute(k_syrk_tc256, cudaFuncAttributeMaxDynamicSharedMemorySize, TW_SMEM));
     attr = true;
   }
   if (!h->tc_status) WL_CHECK(h, cudaMalloc(&h->tc_status, sizeof(int)));
-  int64_t nt = (rows + TC_BM - 1) / TC_BM;
-  int64_t nblk = nt * (nt + 1) / 2;
   WL_CHECK(h, cudaMemsetAsync(h->tc_status, 0, sizeof(int), s));
-  k_syrk_tc<<<(unsigned)nblk, 128, TC_SMEM, s>>>(mhi, mlo, rows, Kp / TC_BK, rscale, C, ldc, h->tc_status);
-  WL_LAUNCH(h, "k_syrk_tc");
+  int64_t nt = (rows + TW_BM - 1) / TW_BM;
+  int64_t nblk = nt * (nt + 1) / 2;
+  k_syrk_tc256<<<(unsigned)nblk, 128, TW_SMEM, s>>>(mhi, mlo, rows, Kp / TW_BK, rscale, C, ldc, h->tc_status);
+  WL_LAUNCH(h, "k_syrk_tc256");
   int st = 0;
   WL_CHECK(h, cudaMemcpyAsync(&st, h->tc_status, sizeof(int), cudaMemcpyDeviceToHost, s));
   WL_CHECK(h, cudaStreamSynchronize(s));
@@ -399,6 +467,8 @@ int wl_syrk_tc(cov_handle* h, double* C, int64_t ldc, cudaStream_t s) {
 
 int wl_split_rows(cov_handle* h, const double* X, int64_t rows, int K, void* hi, void* lo, double* rscale,
                   cudaStream_t s) {
+  if (int rc = zero_last_tile(h, hi, rows, K, s)) return rc;
+  if (int rc = zero_last_tile(h, lo, rows, K, s)) return rc;
   k_split_rows<<<(unsigned)rows, 256, 0, s>>>(X, rows, K, kpad(K), (__nv_bfloat16*)hi, (__nv_bfloat16*)lo, rscale);
   WL_LAUNCH(h, "k_split_rows");
   return COV_OK;
