@@ -12,7 +12,7 @@
 int wl_rows_a(cov_handle* h, cudaStream_t s);
 int wl_rows_t(cov_handle* h, cudaStream_t s);
 int wl_rows_s(cov_handle* h, cudaStream_t s);
-int wl_rows_split(cov_handle* h, cudaStream_t s);
+int wl_rows_split(cov_handle* h, int nssc, cudaStream_t s);
 
 __device__ __forceinline__ int64_t leg_pair(int L1, int L2, int nleg) {
   if (L1 > L2) {
@@ -215,6 +215,7 @@ static int ensure(cov_handle* h, void** p, size_t bytes, const char* what) {
 int wl_assemble(cov_handle* h, double* C, int64_t ldc, unsigned terms, int precision, cudaStream_t s) {
   int rc;
   const int64_t M = h->M, K = h->K;
+  bool ssc_merged = false;
   // 1. the 1-halo trispectrum table of the PT term
   if (terms & COV_TERM_BBPT) {
     if ((rc = ensure(h, (void**)&h->Trows, sizeof(double) * h->ntrow * K, "trispectrum rows"))) return rc;
@@ -249,17 +250,25 @@ int wl_assemble(cov_handle* h, double* C, int64_t ldc, unsigned terms, int preci
       if ((rc = wl_gemm_lower_fp64(h, h->A, K, h->A, K, C, ldc, M, K, 1.0, 0.0, true, s))) return rc;
       wl_stage_end(h, tk, s);
     } else {
+      // the super-sample rows ride along as N_chi extra columns: one
+      // contraction gives A A^T + S S^T
+      ssc_merged = (terms & COV_TERM_SSC) != 0;
+      int nssc = ssc_merged ? h->nchi : 0;
       size_t sb = 0;
-      wl_split_bytes(M, (int)K, &sb);
+      wl_split_bytes(M, (int)K + h->nchi, &sb);
       if ((rc = ensure(h, (void**)&h->Ahi, sb, "BF16 hi rows"))) return rc;
       if ((rc = ensure(h, (void**)&h->Alo, sb, "BF16 lo rows"))) return rc;
       if ((rc = ensure(h, (void**)&h->Ascale, sizeof(double) * M, "row scales"))) return rc;
       if ((rc = ensure(h, (void**)&h->tc_status, sizeof(int), "status word"))) return rc;
+      if ((rc = ensure(h, (void**)&h->G2, sizeof(double) * K, "row factor table"))) return rc;
+      if ((rc = ensure(h, (void**)&h->G3, sizeof(double) * K, "row factor table"))) return rc;
+      if ((rc = ensure(h, (void**)&h->C2, sizeof(double) * h->nchi, "row factor table"))) return rc;
+      if ((rc = ensure(h, (void**)&h->C3, sizeof(double) * h->nchi, "row factor table"))) return rc;
       int tk = wl_stage_begin(h, ST_ROWS_A, s);
-      if ((rc = wl_rows_split(h, s))) return rc;
+      if ((rc = wl_rows_split(h, nssc, s))) return rc;
       wl_stage_end(h, tk, s);
       tk = wl_stage_begin(h, ST_SYRK_1H, s);
-      if ((rc = wl_syrk_tc(h, C, ldc, s))) return rc;
+      if ((rc = wl_syrk_tc(h, nssc, C, ldc, s))) return rc;
       wl_stage_end(h, tk, s);
     }
   }
@@ -271,8 +280,8 @@ int wl_assemble(cov_handle* h, double* C, int64_t ldc, unsigned terms, int preci
                                                                   (terms & COV_TERM_1H) ? 1 : 0);
   WL_LAUNCH(h, "k_gather");
   wl_stage_end(h, tg, s);
-  // 3. super-sample term, rank N_chi
-  if (terms & COV_TERM_SSC) {
+  // 3. super-sample term, rank N_chi (already inside the split contraction)
+  if ((terms & COV_TERM_SSC) && !ssc_merged) {
     if ((rc = ensure(h, (void**)&h->Srows, sizeof(double) * M * h->nchi, "SSC rows"))) return rc;
     int tk = wl_stage_begin(h, ST_ROWS_S, s);
     if ((rc = wl_rows_s(h, s))) return rc;

@@ -84,6 +84,7 @@ struct cov_handle {
   double* A = nullptr;      // [M][K] FP64 1-halo factor rows
   uint16_t *Ahi = nullptr, *Alo = nullptr;  // [M][K] BF16 split rows (tensor-core form)
   double* Ascale = nullptr; // per-row power-of-two scales of the split rows
+  double *G2 = nullptr, *G3 = nullptr, *C2 = nullptr, *C3 = nullptr;  // row-builder factor tables
   int* tc_status = nullptr; // status word of the tensor-core contraction
   double* Trows = nullptr;  // [ntrow][K]
   double* Tmat = nullptr;   // [ntrow][ntrow] lower
@@ -131,7 +132,7 @@ int wl_snr(cov_handle* h, const double* d_C, int64_t ldc, const double* d_D, int
 int wl_gemm_lower_fp64(cov_handle* h, const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
                        int64_t ldc, int64_t n, int64_t k, double alpha, double beta, bool lower_only,
                        cudaStream_t s);  // assemble.cu
-int wl_syrk_tc(cov_handle* h, double* d_C, int64_t ldc, cudaStream_t s);  // syrk_tc.cu
+int wl_syrk_tc(cov_handle* h, int nssc, double* d_C, int64_t ldc, cudaStream_t s);  // syrk_tc.cu
 int wl_split_bytes(int64_t M, int K, size_t* bytes);                      // syrk_tc.cu
 int wl_kpad(int K);  // K padded to the contraction's K granularity
 int wl_syrk_tc_rows(cov_handle* h, const void* hi, const void* lo, const double* rscale, int64_t rows, int Kp,

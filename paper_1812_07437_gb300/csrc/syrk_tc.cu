@@ -37,30 +37,67 @@ __device__ __forceinline__ int64_t blk_off(int64_t r, int k, int nk) {
 }
 
 // ---------------------------------------------------------------- row split
-__global__ void k_rows_split(int64_t M, int nchi, int nm, int Kp, double inv_omega, double rho, const int32_t* rd,
-                             const double* chi, const double* wchi, const double* W, const double* m,
-                             const double* om, const double* f, const double* U, __nv_bfloat16* hi,
-                             __nv_bfloat16* lo, double* rscale) {
+// Per-(n, q) and per-n factors of the 1-halo rows, so that the row builder
+// needs only products: g_mu[n][q] = sqrt(w_n omega_q f_nq / Omega) (m_q/rho)^mu
+// and c_mu[n] = chi_n^(1 - 2 mu), for mu = 2 (P rows) and 3 (B rows).
+__global__ void k_rows_prep(int nchi, int nm, double inv_omega, double rho, const double* chi, const double* wchi,
+                            const double* m, const double* om, const double* f, double* g2, double* g3, double* c2,
+                            double* c3) {
+  int kk = blockIdx.x * blockDim.x + threadIdx.x;
+  if (kk >= nchi * nm) return;
+  int n = kk / nm, q = kk % nm;
+  double mr = m[q] / rho;
+  double base = sqrt(wchi[n] * om[q] * f[kk] * inv_omega);
+  g2[kk] = base * mr * mr;
+  g3[kk] = base * mr * mr * mr;
+  if (q == 0) {
+    double ch = chi[n];
+    c2[n] = 1.0 / (ch * ch * ch);
+    c3[n] = 1.0 / (ch * ch * ch * ch * ch);
+  }
+}
+
+// One block per row a: entries 0..K-1 are the 1-halo factor row; when
+// nssc > 0, entries K..K+nssc-1 are the super-sample row S[a][n] (so that one
+// contraction gives A A^T + S S^T); the rest of Kp is zero.  The row is scaled
+// by an exact power of two s_a (largest entry in [0.5, 1)) and split into
+// BF16 hi/lo.
+__global__ void k_rows_split(int64_t M, int nchi, int nm, int Kp, int nssc, const int32_t* rd, const double* W,
+                             const double* U, const double* g2, const double* g3, const double* c2,
+                             const double* c3, const double* wchi, const double* sigw2, const double* chi,
+                             const double* RP3, const double* RB3, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                             double* rscale) {
   __shared__ double sh[32];
   int64_t a = blockIdx.x;
   if (a >= M) return;
   const int32_t* r = rd + 8 * a;
   int K = nchi * nm;
-  int mu = (r[0] == 0) ? 2 : 3;
+  const bool isP = (r[0] == 0);
+  const double* g = isP ? g2 : g3;
+  const double* cp = isP ? c2 : c3;
+  const double* U1 = U + (size_t)r[1] * nchi * nm;
+  const double* U2 = U + (size_t)r[2] * nchi * nm;
+  const double* U3 = U + (size_t)r[3] * nchi * nm;
+  const double* W1 = W + r[4] * nchi;
+  const double* W2 = W + r[5] * nchi;
+  const double* W3 = W + (isP ? r[4] : r[6]) * nchi;
   auto value = [&](int kk) -> double {
-    int n = kk / nm, q = kk % nm;
-    double mr = m[q] / rho, ch = chi[n];
-    double v = sqrt(wchi[n] * om[q] * f[kk] * inv_omega);
-    v *= (mu == 2) ? 1.0 / (ch * ch * ch) : 1.0 / (ch * ch * ch * ch * ch);
-    v *= (mu == 2) ? mr * mr : mr * mr * mr;
-    v *= W[r[4] * nchi + n] * W[r[5] * nchi + n];
-    v *= U[((size_t)r[1] * nchi + n) * nm + q] * U[((size_t)r[2] * nchi + n) * nm + q];
-    if (mu == 3) v *= W[r[6] * nchi + n] * U[((size_t)r[3] * nchi + n) * nm + q];
-    return v;
+    if (kk < K) {
+      int n = kk / nm;
+      double v = g[kk] * cp[n] * W1[n] * W2[n] * U1[kk] * U2[kk];
+      if (!isP) v *= W3[n] * U3[kk];
+      return v;
+    }
+    int n = kk - K;
+    if (n >= nssc) return 0.0;
+    double ch = chi[n], v = sqrt(wchi[n] * sigw2[n]) * W1[n] * W2[n];
+    if (isP) return v / (ch * ch) * RP3[r[1] * nchi + n];
+    double c2_ = ch * ch;
+    return v * W3[n] / (c2_ * c2_) * RB3[r[7] * nchi + n];
   };
+  int Kt = K + nssc;
   double mx = 0.0;
-  for (int kk = threadIdx.x; kk < K; kk += blockDim.x) mx = fmax(mx, fabs(value(kk)));
-  // block max via the sum helper's layout
+  for (int kk = threadIdx.x; kk < Kt; kk += blockDim.x) mx = fmax(mx, fabs(value(kk)));
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
   __syncthreads();
@@ -76,7 +113,7 @@ __global__ void k_rows_split(int64_t M, int nchi, int nm, int Kp, double inv_ome
   double inv = ldexp(1.0, -ex);
   int nk = Kp / TW_BK;
   for (int kk = threadIdx.x; kk < Kp; kk += blockDim.x) {
-    double x = (kk < K) ? value(kk) * inv : 0.0;
+    double x = (kk < Kt) ? value(kk) * inv : 0.0;
     __nv_bfloat16 h = __float2bfloat16_rn((float)x);
     __nv_bfloat16 l = __float2bfloat16_rn((float)(x - (double)__bfloat162float(h)));
     hi[blk_off(a, kk, nk)] = h;
@@ -425,12 +462,15 @@ static int zero_last_tile(cov_handle* h, void* base, int64_t rows, int K, cudaSt
   return COV_OK;
 }
 
-int wl_rows_split(cov_handle* h, cudaStream_t s) {
+int wl_rows_split(cov_handle* h, int nssc, cudaStream_t s) {
   double rho = WL_RHO_CRIT0 * h->cosmo.Om;
-  if (int rc = zero_last_tile(h, h->Ahi, h->M, h->K, s)) return rc;
-  if (int rc = zero_last_tile(h, h->Alo, h->M, h->K, s)) return rc;
-  k_rows_split<<<(unsigned)h->M, 256, 0, s>>>(h->M, h->nchi, h->nm, kpad(h->K), 1.0 / h->omega, rho, h->rowdesc_d,
-                                               h->chi, h->wchi, h->W, h->m, h->om, h->f, h->U,
+  int Kt = h->K + nssc;
+  if (int rc = zero_last_tile(h, h->Ahi, h->M, Kt, s)) return rc;
+  if (int rc = zero_last_tile(h, h->Alo, h->M, Kt, s)) return rc;
+  k_rows_prep<<<(h->K + 255) / 256, 256, 0, s>>>(h->nchi, h->nm, 1.0 / h->omega, rho, h->chi, h->wchi, h->m, h->om,
+                                                   h->f, h->G2, h->G3, h->C2, h->C3);
+  k_rows_split<<<(unsigned)h->M, 256, 0, s>>>(h->M, h->nchi, h->nm, kpad(Kt), nssc, h->rowdesc_d, h->W, h->U, h->G2,
+                                               h->G3, h->C2, h->C3, h->wchi, h->sigw2, h->chi, h->RP3, h->RB3,
                                                (__nv_bfloat16*)h->Ahi, (__nv_bfloat16*)h->Alo, (double*)h->Ascale);
   WL_LAUNCH(h, "k_rows_split");
   return COV_OK;
@@ -461,8 +501,8 @@ int wl_syrk_tc_rows(cov_handle* h, const void* hi, const void* lo, const double*
   return COV_OK;
 }
 
-int wl_syrk_tc(cov_handle* h, double* C, int64_t ldc, cudaStream_t s) {
-  return wl_syrk_tc_rows(h, h->Ahi, h->Alo, h->Ascale, h->M, kpad(h->K), C, ldc, s);
+int wl_syrk_tc(cov_handle* h, int nssc, double* C, int64_t ldc, cudaStream_t s) {
+  return wl_syrk_tc_rows(h, h->Ahi, h->Alo, h->Ascale, h->M, kpad(h->K + nssc), C, ldc, s);
 }
 
 int wl_split_rows(cov_handle* h, const double* X, int64_t rows, int K, void* hi, void* lo, double* rscale,
