@@ -187,7 +187,7 @@ static void free_all(cov_handle* h) {
                   h->ell_d, h->m, h->om, h->sig0, h->dlns, h->f, h->b1, h->b2, h->U, h->Pl, h->dPl, h->zedges,
                   h->norms, h->W, h->sigw2, h->slo_d, h->shi_d, h->Nmodes, h->Ntri, h->rowtab, h->tris_d,
                   h->rowdesc_d, h->P3, h->RP3, h->B3, h->RB3, h->B1h3, h->Ps, h->B1hp, h->Bp, h->A, h->Ahi,
-                  h->Alo, h->Ascale, h->G2, h->G3, h->C2, h->C3, h->tc_status, h->Thi, h->Tlo, h->Tscale, h->Trows, h->Tmat, h->Srows, h->work, h->perm};
+                  h->Alo, h->Ascale, h->G2, h->G3, h->C2, h->C3, h->tc_status, h->Thi, h->Tlo, h->Tscale, h->Trows, h->Tmat, h->Srows, h->work, h->perm, h->chol_scratch, h->chol_status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }

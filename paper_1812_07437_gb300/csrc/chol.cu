@@ -5,7 +5,9 @@
 // D' = d^-1/2 D, and written with D' as one extra last row into an FP64
 // workspace.  A blocked right-looking Cholesky factorisation of the leading
 // M_s x M_s block carries the extra row along, so that row ends up holding
-// y = L^-1 D'.  Because the leading principal block of a Cholesky factor is
+// y = L^-1 D'.  Diagonal blocks and panel solves run in FP64 on the CUDA cores;
+// the trailing updates run on the tensor cores with exact integer slicing
+// (chol_tc.cu), accurate to ~2^-48 of each row's largest entry.  Because the leading principal block of a Cholesky factor is
 // the factor of the leading principal block, (S/N)^2 for every cumulative
 // ell_max is a prefix sum of y^2 over the reordered entries.
 #include <algorithm>
@@ -165,6 +167,16 @@ int wl_snr(cov_handle* h, const double* C, int64_t ldc, const double* D, int whi
     h->work_n = need;
   }
   if (!h->perm) WL_CHECK(h, cudaMalloc(&h->perm, sizeof(int) * h->M));
+  size_t need_sc = wl_chol_tc_bytes(Ms + 1);
+  if (need_sc > h->chol_scratch_n) {
+    if (h->chol_scratch) cudaFree(h->chol_scratch);
+    h->chol_scratch = nullptr;
+    h->chol_scratch_n = 0;
+    WL_CHECK(h, cudaMalloc(&h->chol_scratch, need_sc));
+    h->chol_scratch_n = need_sc;
+  }
+  if (!h->chol_status) WL_CHECK(h, cudaMalloc(&h->chol_status, sizeof(int)));
+  WL_CHECK(h, cudaMemsetAsync(h->chol_status, 0, sizeof(int), s));
   int* st = nullptr;
   int64_t* cnt_d = nullptr;
   double* out_d = nullptr;
@@ -186,10 +198,8 @@ int wl_snr(cov_handle* h, const double* C, int64_t ldc, const double* D, int whi
     int64_t r0 = k0 + kb, r1 = Ms + 1;
     if (r1 > r0) {
       k_trsm_rows<<<(unsigned)((r1 - r0 + TRSM_ROWS - 1) / TRSM_ROWS), 256, 0, s>>>(h->work, ldw, k0, kb, r0, r1);
-      int64_t n = r1 - r0;
-      double* P = h->work + r0 * ldw + k0;
-      double* Csub = h->work + r0 * ldw + r0;
-      int rc = wl_gemm_lower_fp64(h, P, ldw, P, ldw, Csub, ldw, n, kb, -1.0, 1.0, true, s);
+      // trailing update on the tensor cores, FP64-accurate by exact slicing
+      int rc = wl_chol_update_tc(h, h->work, ldw, k0, kb, r0, r1, h->chol_scratch, h->chol_status, s);
       if (rc) return rc;
     }
   }
@@ -198,13 +208,15 @@ int wl_snr(cov_handle* h, const double* C, int64_t ldc, const double* D, int whi
   tk = wl_stage_begin(h, ST_SNR_PREFIX, s);
   k_snr_prefix<<<h->nl, 256, 0, s>>>(Ms, h->work, ldw, cnt_d, h->nl, out_d);
   wl_stage_end(h, tk, s);
-  int status = 0;
+  int status = 0, tstatus = 0;
   WL_CHECK(h, cudaMemcpyAsync(h_snr, out_d, sizeof(double) * h->nl, cudaMemcpyDeviceToHost, s));
   WL_CHECK(h, cudaMemcpyAsync(&status, st, sizeof(int), cudaMemcpyDeviceToHost, s));
+  WL_CHECK(h, cudaMemcpyAsync(&tstatus, h->chol_status, sizeof(int), cudaMemcpyDeviceToHost, s));
   WL_CHECK(h, cudaFreeAsync(st, s));
   WL_CHECK(h, cudaFreeAsync(cnt_d, s));
   WL_CHECK(h, cudaFreeAsync(out_d, s));
   WL_CHECK(h, cudaStreamSynchronize(s));
+  if (tstatus) return wl_fail(h, COV_ERR_TIMEOUT, "Cholesky trailing update: a bounded mbarrier wait expired");
   if (status) return wl_fail(h, COV_ERR_NOT_PD, "Cholesky met a non-positive pivot");
   return COV_OK;
 }

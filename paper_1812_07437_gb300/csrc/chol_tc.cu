@@ -1,0 +1,311 @@
+// FP64-accurate trailing update of the blocked Cholesky on the tcgen05 tensor
+// cores (the S/N solve of the paper's Sec. 5, Eq. eq:SN), by exact integer
+// slicing in the manner of Ozaki, Ogita & Oishi (2012):
+//
+//   * k_chol_slice: every panel row x (kb <= 64 FP64 entries) is scaled by an
+//     exact power of two 2^-e (e from its largest entry) and cut into
+//     S = 6 fixed-point slices, x 2^-e = sum_t d_t 2^(-7-8t), d_t integers in
+//     [-128, 128] stored exactly as BF16; the residual is below 2^-48 of the row
+//     maximum.
+//   * k_chol_update: per 128 x 64 lower tile of the trailing matrix, the
+//     products d_t(i) . d_u(j) over the panel's K = 64 are exact in FP32
+//     (|d d| <= 2^14, 64 terms -> 2^20), and so are their sums over the pairs
+//     with equal t + u = g (at most 6 pairs -> < 2^23).  21 pairs (t + u <= 5) x
+//     4 K steps of tcgen05.mma (kind::f16, M = 128, N = 64) accumulate into six
+//     TMEM accumulators, one per g; the epilogue recombines them in FP64,
+//     v = 2^(e_i + e_j - 14) sum_g acc_g 2^-8g, and subtracts v from the FP64
+//     trailing matrix with coalesced read-modify-writes.
+//
+// One CTA (128 threads) per tile: warp 0 / lane 0 loads the 6 I-slices
+// (128 x 64) and 6 J-slices (64 x 64) with TMA (128B swizzle) in one stage,
+// warp 1 / lane 0 issues the MMAs, all four warps run the epilogue.  Waits are
+// bounded (status word, COV_ERR_TIMEOUT).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+
+#define CS_S 6                                   // slices per entry
+#define CS_BI 128                                // tile rows
+#define CS_BJ 64                                 // tile columns
+#define CS_K 64                                  // panel width
+#define CS_IBYTES (CS_BI * CS_K * 2)             // 16 KB per I slice tile
+#define CS_JBYTES (CS_BJ * CS_K * 2)             // 8 KB per J slice tile
+#define CS_STAGE (CS_S * (CS_IBYTES + CS_JBYTES))  // 144 KB
+#define CS_CTILE (CS_BI * CS_BJ * 8)             // 64 KB FP64 trailing tile
+#define CS_SMEM (CS_STAGE + CS_CTILE + 1024)
+#define CS_SPIN (1u << 22)
+
+// slices of the panel rows r0..r1-1 (columns k0..k0+kb-1 of the workspace);
+// rows up to the padded count are written (zeros past r1)
+__global__ void k_chol_slice(const double* Wk, int64_t ldw, int64_t k0, int kb, int64_t r0, int64_t nrows,
+                             int64_t nrows_pad, __nv_bfloat16* slices, int* rexp) {
+  int64_t r = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  int lane = threadIdx.x & 31;
+  if (r >= nrows_pad) return;
+  double x0 = 0.0, x1 = 0.0;
+  if (r < nrows) {
+    const double* row = Wk + (r0 + r) * ldw + k0;
+    if (lane < kb) x0 = row[lane];
+    if (lane + 32 < kb) x1 = row[lane + 32];
+  }
+  double mx = fmax(fabs(x0), fabs(x1));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  int e = 0;
+  if (mx > 0.0) frexp(mx, &e);
+  double s0 = ldexp(x0, 7 - e), s1 = ldexp(x1, 7 - e);  // |s| < 128
+  for (int t = 0; t < CS_S; ++t) {
+    double d0 = rint(s0), d1 = rint(s1);
+    s0 = (s0 - d0) * 256.0;
+    s1 = (s1 - d1) * 256.0;
+    __nv_bfloat16* out = slices + ((size_t)t * nrows_pad + r) * CS_K;
+    out[lane] = __float2bfloat16_rn((float)d0);
+    out[lane + 32] = __float2bfloat16_rn((float)d1);
+  }
+  if (lane == 0) rexp[r] = e;
+}
+
+__device__ __forceinline__ uint32_t cs_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t cs_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(cs_smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok;
+}
+
+__device__ __forceinline__ bool cs_wait(uint64_t* bar, uint32_t parity, int* status) {
+  for (uint32_t i = 0; i < CS_SPIN; ++i)
+    if (cs_try(bar, parity)) return true;
+  atomicExch(status, 1);
+  return false;
+}
+
+__device__ __forceinline__ uint64_t cs_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;  // 8 rows x 128 B
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;  // SWIZZLE_128B
+  return d;
+}
+
+__device__ __forceinline__ void cs_tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// grid.x = tile row (128 rows), grid.y = tile column (64 columns)
+__global__ void __launch_bounds__(128, 1)
+    k_chol_update(const __grid_constant__ CUtensorMap map_i, const __grid_constant__ CUtensorMap map_j,
+                  int64_t nrows, int64_t nrows_pad, const int* __restrict__ rexp, double* Csub, int64_t ldc,
+                  int* status) {
+  int ti = blockIdx.x, tj = blockIdx.y;
+  if ((int64_t)tj * CS_BJ > (int64_t)ti * CS_BI + CS_BI - 1) return;  // tile above the diagonal
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar;
+  __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ uint32_t tmem_sh;
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int row_i = ti * CS_BI, row_j = tj * CS_BJ;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(cs_smem_u32(&full_bar)), "r"(1) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(cs_smem_u32(&acc_bar)), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(cs_smem_u32(&tmem_sh)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  uint32_t tmem = tmem_sh;
+  bool loaded = false;
+  double* ctile = (double*)(smem + CS_STAGE);  // [128][64] FP64 copy of the trailing tile
+  if (warp >= 2) {
+    // warps 2-3 stream the FP64 tile into shared memory while the slices load
+    // and the MMAs run (8-byte cp.async, coalesced along each row)
+    int t = threadIdx.x - 64;
+    for (int e = t; e < CS_BI * CS_BJ; e += 64) {
+      int rr = e / CS_BJ, cc = e % CS_BJ;
+      int64_t gr = (int64_t)row_i + rr, gc = (int64_t)row_j + cc;
+      if (gr < nrows && gc < nrows && gc <= gr) {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(cs_smem_u32(ctile + e)),
+                     "l"(Csub + gr * ldc + gc)
+                     : "memory");
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  } else if (warp == 0 && lane == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cs_smem_u32(&full_bar)),
+                 "r"(CS_STAGE)
+                 : "memory");
+    for (int t = 0; t < CS_S; ++t) {
+      int yi = (int)(t * nrows_pad + row_i), yj = (int)(t * nrows_pad + row_j);
+      asm volatile(
+          "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+          "[%2];" ::"r"(cs_smem_u32(smem + t * CS_IBYTES)),
+          "l"((uint64_t)&map_i), "r"(cs_smem_u32(&full_bar)), "r"(0), "r"(yi)
+          : "memory");
+      asm volatile(
+          "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+          "[%2];" ::"r"(cs_smem_u32(smem + CS_S * CS_IBYTES + t * CS_JBYTES)),
+          "l"((uint64_t)&map_j), "r"(cs_smem_u32(&full_bar)), "r"(0), "r"(yj)
+          : "memory");
+    }
+  } else if (warp == 1 && lane == 0) {
+    loaded = cs_wait(&full_bar, 0u, status);
+    if (loaded) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // kind::f16, BF16 x BF16 -> FP32, K-major, M = 128, N = 64
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CS_BJ >> 3) << 17) |
+                             ((uint32_t)(CS_BI >> 4) << 24);
+      uint32_t base_i = cs_smem_u32(smem), base_j = cs_smem_u32(smem + CS_S * CS_IBYTES);
+      for (int g = 0; g < CS_S; ++g) {
+        uint32_t dt = tmem + (uint32_t)(g * CS_BJ);
+        int first = 1;
+        for (int t = 0; t <= g; ++t) {
+          int u = g - t;
+#pragma unroll
+          for (int k = 0; k < CS_K / 16; ++k) {
+            uint64_t ad = cs_desc_sw128(base_i + t * CS_IBYTES + k * 32);
+            uint64_t bd = cs_desc_sw128(base_j + u * CS_JBYTES + k * 32);
+            uint32_t acc = first ? 0u : 1u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, "
+                "p;\n}\n" ::"r"(dt),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                : "memory");
+            first = 0;
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     cs_smem_u32(&acc_bar))
+                 : "memory");
+  }
+  __syncwarp();
+  bool have = cs_wait(&acc_bar, 0u, status);
+  if (warp == 0 && lane == 0) {
+    // the copies must have landed before the CTA exits (bounded)
+    for (uint32_t i = 0; i < CS_SPIN && !cs_try(&full_bar, 0u); ++i) {
+    }
+  }
+  if (warp >= 2) asm volatile("cp.async.wait_all;" ::: "memory");
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (have && *(volatile int*)status == 0) {
+    double* stg = (double*)smem + warp * (32 * 33);
+    int64_t gi = (int64_t)row_i + warp * 32 + lane;
+    int ei = (gi < nrows) ? rexp[gi] : 0;
+#pragma unroll 1
+    for (int c = 0; c < CS_BJ / 32; ++c) {
+      double acc[32];
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) acc[jj] = 0.0;
+#pragma unroll 1
+      for (int g = CS_S - 1; g >= 0; --g) {
+        float v[32];
+        cs_tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * CS_BJ + c * 32), v);
+        double sc = ldexp(1.0, -8 * g);
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) acc[jj] += (double)v[jj] * sc;
+      }
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) stg[lane * 33 + jj] = ldexp(acc[jj], ei - 14);
+      __syncwarp();
+      int64_t gj = (int64_t)row_j + c * 32 + lane;
+      int ej = (gj < nrows) ? rexp[gj] : 0;
+#pragma unroll 4
+      for (int rr = 0; rr < 32; ++rr) {
+        int lr = warp * 32 + rr;
+        int64_t gr = (int64_t)row_i + lr;
+        if (gr < nrows && gj < nrows && gj <= gr)
+          Csub[gr * ldc + gj] = ctile[lr * CS_BJ + c * 32 + lane] - ldexp(stg[rr * 33 + lane], ej);
+      }
+      __syncwarp();
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 cs_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+static int cs_map(cov_handle* h, CUtensorMap* map, void* base, int64_t total_rows, int box_rows) {
+  auto fn = cs_encode();
+  if (!fn) return wl_fail(h, COV_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  cuuint64_t dims[2] = {(cuuint64_t)CS_K, (cuuint64_t)total_rows};
+  cuuint64_t strides[1] = {(cuuint64_t)CS_K * 2};
+  cuuint32_t box[2] = {(cuuint32_t)CS_K, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return wl_fail(h, COV_ERR_CUDA, "cuTensorMapEncodeTiled failed (Cholesky slices)");
+  return COV_OK;
+}
+
+// bytes of the slice workspace for up to n trailing rows
+size_t wl_chol_tc_bytes(int64_t n) {
+  int64_t pad = (n + CS_BI - 1) / CS_BI * CS_BI;
+  return (size_t)CS_S * pad * CS_K * 2 + (size_t)pad * sizeof(int);
+}
+
+// Csub (rows/cols r0..r1-1 of the workspace, leading dimension ldw) -=
+// L21 L21^T with L21 = rows r0..r1-1, columns k0..k0+kb-1, lower triangle only
+int wl_chol_update_tc(cov_handle* h, double* Wk, int64_t ldw, int64_t k0, int kb, int64_t r0, int64_t r1,
+                      void* scratch, int* status, cudaStream_t s) {
+  int64_t n = r1 - r0;
+  if (n <= 0) return COV_OK;
+  int64_t pad = (n + CS_BI - 1) / CS_BI * CS_BI;
+  __nv_bfloat16* slices = (__nv_bfloat16*)scratch;
+  int* rexp = (int*)((uint8_t*)scratch + (size_t)CS_S * pad * CS_K * 2);
+  k_chol_slice<<<(unsigned)((pad + 7) / 8), 256, 0, s>>>(Wk, ldw, k0, kb, r0, n, pad, slices, rexp);
+  WL_LAUNCH(h, "k_chol_slice");
+  CUtensorMap mi, mj;
+  int rc;
+  if ((rc = cs_map(h, &mi, slices, CS_S * pad, CS_BI))) return rc;
+  if ((rc = cs_map(h, &mj, slices, CS_S * pad, CS_BJ))) return rc;
+  static bool attr = false;
+  if (!attr) {
+    WL_CHECK(h, cudaFuncSetAttribute(k_chol_update, cudaFuncAttributeMaxDynamicSharedMemorySize, CS_SMEM));
+    attr = true;
+  }
+  dim3 grid((unsigned)(pad / CS_BI), (unsigned)((n + CS_BJ - 1) / CS_BJ));
+  k_chol_update<<<grid, 128, CS_SMEM, s>>>(mi, mj, n, pad, rexp, Wk + r0 * ldw + r0, ldw, status);
+  WL_LAUNCH(h, "k_chol_update");
+  return COV_OK;
+}

@@ -94,6 +94,9 @@ struct cov_handle {
   double* work = nullptr;   // Cholesky workspace (M+1)^2
   int64_t work_n = 0;
   int* perm = nullptr;      // [M] reorder for the cumulative S/N
+  void* chol_scratch = nullptr;  // slices of the tensor-core trailing update
+  size_t chol_scratch_n = 0;
+  int* chol_status = nullptr;
   bool spectra_ready = false;
   bool prof = false;
   std::vector<StageEvent> pending;
@@ -135,6 +138,9 @@ int wl_gemm_lower_fp64(cov_handle* h, const double* A, int64_t lda, const double
 int wl_syrk_tc(cov_handle* h, int nssc, double* d_C, int64_t ldc, cudaStream_t s);  // syrk_tc.cu
 int wl_split_bytes(int64_t M, int K, size_t* bytes);                      // syrk_tc.cu
 int wl_kpad(int K);  // K padded to the contraction's K granularity
+size_t wl_chol_tc_bytes(int64_t n);  // chol_tc.cu
+int wl_chol_update_tc(cov_handle* h, double* Wk, int64_t ldw, int64_t k0, int kb, int64_t r0, int64_t r1,
+                      void* scratch, int* status, cudaStream_t s);
 int wl_syrk_tc_rows(cov_handle* h, const void* hi, const void* lo, const double* rscale, int64_t rows, int Kp,
                     double* C, int64_t ldc, cudaStream_t s);
 int wl_split_rows(cov_handle* h, const double* X, int64_t rows, int K, void* hi, void* lo, double* rscale,
