@@ -12,9 +12,10 @@
 //     (|d d| <= 2^14, 64 terms -> 2^20), and so are their sums over the pairs
 //     with equal t + u = g (at most 6 pairs -> < 2^23).  21 pairs (t + u <= 5) x
 //     4 K steps of tcgen05.mma (kind::f16, M = 128, N = 64) accumulate into six
-//     TMEM accumulators, one per g; the epilogue recombines them in FP64,
-//     v = 2^(e_i + e_j - 14) sum_g acc_g 2^-8g, and subtracts v from the FP64
-//     trailing matrix with coalesced read-modify-writes.
+//     TMEM accumulators, one per g; the epilogue recombines them exactly in
+//     int64, v = 2^(e_i + e_j - 54) sum_g acc_g 2^(8 (5 - g)), converts once to
+//     FP64 and subtracts v from the FP64 trailing matrix (coalesced stores; the
+//     tile was copied to shared memory during the MMAs).
 //
 // One CTA (128 threads) per tile: warp 0 / lane 0 loads the 6 I-slices
 // (128 x 64) and 6 J-slices (64 x 64) with TMA (128B swizzle) in one stage,
@@ -121,9 +122,11 @@ __global__ void __launch_bounds__(128, 1)
   __shared__ __align__(8) uint64_t full_bar;
   __shared__ __align__(8) uint64_t acc_bar;
   __shared__ uint32_t tmem_sh;
+  __shared__ int rexp_sh[CS_BI];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int row_i = ti * CS_BI, row_j = tj * CS_BJ;
+  rexp_sh[threadIdx.x] = (row_i + (int)threadIdx.x < nrows) ? rexp[row_i + threadIdx.x] : 0;
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(cs_smem_u32(&full_bar)), "r"(1) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(cs_smem_u32(&acc_bar)), "r"(1) : "memory");
@@ -216,23 +219,23 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   if (have && *(volatile int*)status == 0) {
     double* stg = (double*)smem + warp * (32 * 33);
-    int64_t gi = (int64_t)row_i + warp * 32 + lane;
-    int ei = (gi < nrows) ? rexp[gi] : 0;
 #pragma unroll 1
     for (int c = 0; c < CS_BJ / 32; ++c) {
-      double acc[32];
+      // the six group sums are exact integers (< 2^23): combine them exactly
+      // in int64, v = sum_g acc_g 2^(8 (5 - g)), then one conversion to FP64
+      long long acc[32];
 #pragma unroll
-      for (int jj = 0; jj < 32; ++jj) acc[jj] = 0.0;
+      for (int jj = 0; jj < 32; ++jj) acc[jj] = 0;
 #pragma unroll 1
-      for (int g = CS_S - 1; g >= 0; --g) {
+      for (int g = 0; g < CS_S; ++g) {
         float v[32];
         cs_tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * CS_BJ + c * 32), v);
-        double sc = ldexp(1.0, -8 * g);
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) acc[jj] += (double)v[jj] * sc;
+        for (int jj = 0; jj < 32; ++jj) acc[jj] = (acc[jj] << 8) + (long long)__float2ll_rn(v[jj]);
       }
+      // value = acc 2^(e_i + e_j - 14 - 8 (S - 1)); the e_j part is applied per column below
 #pragma unroll
-      for (int jj = 0; jj < 32; ++jj) stg[lane * 33 + jj] = ldexp(acc[jj], ei - 14);
+      for (int jj = 0; jj < 32; ++jj) stg[lane * 33 + jj] = (double)acc[jj];
       __syncwarp();
       int64_t gj = (int64_t)row_j + c * 32 + lane;
       int ej = (gj < nrows) ? rexp[gj] : 0;
@@ -240,8 +243,13 @@ __global__ void __launch_bounds__(128, 1)
       for (int rr = 0; rr < 32; ++rr) {
         int lr = warp * 32 + rr;
         int64_t gr = (int64_t)row_i + lr;
-        if (gr < nrows && gj < nrows && gj <= gr)
-          Csub[gr * ldc + gj] = ctile[lr * CS_BJ + c * 32 + lane] - ldexp(stg[rr * 33 + lane], ej);
+        if (gr < nrows && gj < nrows && gj <= gr) {
+          int er = rexp_sh[lr];
+          // exact power of two 2^(e_r + e_j - 14 - 40) built from its exponent bits
+          int ex = er + ej - 54;
+          double sc = (ex > -1000 && ex < 1000) ? __longlong_as_double((long long)(ex + 1023) << 52) : ldexp(1.0, ex);
+          Csub[gr * ldc + gj] = ctile[lr * CS_BJ + c * 32 + lane] - stg[rr * 33 + lane] * sc;
+        }
       }
       __syncwarp();
     }

@@ -39,11 +39,7 @@ __global__ void k_rowtab(int nl, int rmax, const int64_t* slo, const int64_t* sh
   tab[((size_t)b * 2 + 1) * (rmax + 1) + y] = xi;
 }
 
-__device__ __forceinline__ int row_intervals(const int32_t* tab, int rmax, int b, int y, int* lo, int* hi) {
-  int ay = y < 0 ? -y : y;
-  if (ay > rmax) return 0;
-  int xo = tab[((size_t)b * 2 + 0) * (rmax + 1) + ay];
-  int xi = tab[((size_t)b * 2 + 1) * (rmax + 1) + ay];
+__device__ __forceinline__ int row_intervals_from(int xo, int xi, int* lo, int* hi) {
   if (xo < 0 || xi > xo) return 0;
   if (xi == 0) {
     lo[0] = -xo;
@@ -55,6 +51,14 @@ __device__ __forceinline__ int row_intervals(const int32_t* tab, int rmax, int b
   lo[1] = xi;
   hi[1] = xo;
   return 2;
+}
+
+__device__ __forceinline__ int row_intervals(const int32_t* tab, int rmax, int b, int y, int* lo, int* hi) {
+  int ay = y < 0 ? -y : y;
+  if (ay > rmax) return 0;
+  int xo = tab[((size_t)b * 2 + 0) * (rmax + 1) + ay];
+  int xi = tab[((size_t)b * 2 + 1) * (rmax + 1) + ay];
+  return row_intervals_from(xo, xi, lo, hi);
 }
 
 __global__ void k_nmodes(int rmax, const int32_t* tab, int64_t* N) {
@@ -80,13 +84,23 @@ __global__ void k_nmodes(int rmax, const int32_t* tab, int64_t* N) {
 __global__ void k_ntri(int rmax, const int32_t* tris, const int64_t* slo, const int64_t* shi, const int32_t* tab,
                        unsigned long long* out) {
   __shared__ unsigned long long sh[32];
+  extern __shared__ int2 rows_sh[];  // [2][rmax+1]: (x_outer, x_inner) of bins b and c
   int t = blockIdx.y;
   int x1 = blockIdx.x;
   int a = tris[3 * t], b = tris[3 * t + 1], c = tris[3 * t + 2];
   unsigned long long cnt = 0;
   int64_t x1s = (int64_t)x1 * x1;
   bool any = (x1s < shi[a]) && (2 * x1s >= slo[a]);  // the row can hold a point with y1 <= x1
-  if (any) {
+  if (!any) return;
+  for (int y = threadIdx.x; y <= rmax; y += blockDim.x) {
+    rows_sh[y] = make_int2(tab[((size_t)b * 2 + 0) * (rmax + 1) + y], tab[((size_t)b * 2 + 1) * (rmax + 1) + y]);
+    rows_sh[rmax + 1 + y] =
+        make_int2(tab[((size_t)c * 2 + 0) * (rmax + 1) + y], tab[((size_t)c * 2 + 1) * (rmax + 1) + y]);
+  }
+  __syncthreads();
+  const int2* rb_sh = rows_sh;
+  const int2* rc_sh = rows_sh + rmax + 1;
+  {
     for (int y1 = threadIdx.x; y1 <= x1; y1 += blockDim.x) {
       int64_t s1 = x1s + (int64_t)y1 * y1;
       if (s1 < slo[a] || s1 >= shi[a]) continue;
@@ -96,9 +110,14 @@ __global__ void k_ntri(int rmax, const int32_t* tris, const int64_t* slo, const 
       int ylo = max(-rb, -y1 - rc), yhi = min(rb, -y1 + rc);
       for (int y2 = ylo; y2 <= yhi; ++y2) {
         int blo[2], bhi[2], clo[2], chi_[2];
-        int nb = row_intervals(tab, rmax, b, y2, blo, bhi);
+        int2 pb = rb_sh[y2 < 0 ? -y2 : y2];
+        int nb = row_intervals_from(pb.x, pb.y, blo, bhi);
         if (nb == 0) continue;
-        int nc = row_intervals(tab, rmax, c, y1 + y2, clo, chi_);
+        int yc = y1 + y2;
+        int ayc = yc < 0 ? -yc : yc;
+        if (ayc > rmax) continue;
+        int2 pc = rc_sh[ayc];
+        int nc = row_intervals_from(pc.x, pc.y, clo, chi_);
         for (int i = 0; i < nb; ++i)
           for (int j = 0; j < nc; ++j) {
             int lo = max(blo[i], clo[j] - x1);
@@ -127,7 +146,9 @@ int wl_counts(cov_handle* h, cudaStream_t s) {
   WL_CHECK(h, cudaMemsetAsync(h->Ntri, 0, sizeof(int64_t) * h->ntri, s));
   if (h->ntri > 0) {
     dim3 g2(rmax + 1, h->ntri);
-    k_ntri<<<g2, 128, 0, s>>>(rmax, h->tris_d, h->slo_d, h->shi_d, h->rowtab, (unsigned long long*)h->Ntri);
+    size_t shb = sizeof(int2) * 2 * (size_t)(rmax + 1);
+    if (shb > 48 * 1024) WL_CHECK(h, cudaFuncSetAttribute(k_ntri, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
+    k_ntri<<<g2, 128, shb, s>>>(rmax, h->tris_d, h->slo_d, h->shi_d, h->rowtab, (unsigned long long*)h->Ntri);
   }
   WL_LAUNCH(h, "count kernels");
   return COV_OK;

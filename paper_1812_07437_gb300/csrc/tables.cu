@@ -45,9 +45,10 @@ __device__ double dev_growth_raw(double at, const cov_cosmology& c) {
   double h = (x1 - x) / WL_N_RK4;
   double d = WL_A_INIT, dp = WL_A_INIT;
   double om = c.Om, ode = 1.0 - c.Om, w = c.w0;
+  const bool lambda_cdm = (w == -1.0);
   auto rhs = [&](double lna, double yd, double yp, double* fd, double* fp) {
     double em = om * exp(-3.0 * lna);
-    double ed = ode * exp(-3.0 * (1.0 + w) * lna);
+    double ed = lambda_cdm ? ode : ode * exp(-3.0 * (1.0 + w) * lna);
     double e2 = em + ed;
     double dlnh = 0.5 * (-3.0 * em - 3.0 * (1.0 + w) * ed) / e2;
     *fd = yp;
@@ -289,17 +290,21 @@ __global__ void k_kernels(cov_cosmology c, cov_nz nz, int nchi, const double* ch
   double pref = 1.5 * c.Om / (WL_C_OVER_H0 * WL_C_OVER_H0) * (1.0 + zn) * ch;
   double pts[40];
   int np = (zn < nz.zmax) ? make_pieces(zn, nz.zmax, e, nt, pts) : 0;
-  for (int i = 0; i < nt; ++i) {
-    double s = 0.0;
-    for (int p = 0; p < np; ++p) {
-      double a = pts[p], b = pts[p + 1], half = 0.5 * (b - a);
-      for (int j = threadIdx.x; j < WL_N_ZS; j += blockDim.x) {
-        double zs = a + half * (gx[j] + 1.0);
-        double cs = dev_chi_of_z(zs, c, gx, gw);
-        s += half * gw[j] * nz_shape(zs, nz) * (cs - ch) / cs * bin_sel(zs, i, e, nt, nz.photoz_sigma0);
-      }
+  // each thread owns one source node per piece: chi(z_s) and the geometric
+  // weight are computed once and reused for every tomographic bin
+  double acc[32];
+  for (int i = 0; i < nt; ++i) acc[i] = 0.0;
+  for (int p = 0; p < np; ++p) {
+    double a = pts[p], b = pts[p + 1], half = 0.5 * (b - a);
+    for (int j = threadIdx.x; j < WL_N_ZS; j += blockDim.x) {
+      double zs = a + half * (gx[j] + 1.0);
+      double cs = dev_chi_of_z(zs, c, gx, gw);
+      double geo = half * gw[j] * nz_shape(zs, nz) * (cs - ch) / cs;
+      for (int i = 0; i < nt; ++i) acc[i] += geo * bin_sel(zs, i, e, nt, nz.photoz_sigma0);
     }
-    s = block_sum(s, sh);
+  }
+  for (int i = 0; i < nt; ++i) {
+    double s = block_sum(acc[i], sh);
     if (threadIdx.x == 0) W[i * nchi + n] = (np > 0) ? pref * s / norms[i] : 0.0;
   }
 }
