@@ -47,6 +47,7 @@ __global__ void k_potrf_diag(double* Wk, int64_t ldw, int64_t k0, int kb, int* s
       int i = ty + 16 * r, l = tx + 16 * c;
       L[i][l] = (i < kb && l <= i) ? Wk[(k0 + i) * ldw + k0 + l] : 0.0;
     }
+  __shared__ double inv_sh;
   __syncthreads();
   for (int j = 0; j < kb; ++j) {
     if (threadIdx.x == 0) {
@@ -55,10 +56,12 @@ __global__ void k_potrf_diag(double* Wk, int64_t ldw, int64_t k0, int kb, int* s
         atomicExch(status, 1);
         d = 1.0;
       }
-      L[j][j] = sqrt(d);
+      double r = sqrt(d);
+      L[j][j] = r;
+      inv_sh = 1.0 / r;  // one FP64 division per step, shared by all threads
     }
     __syncthreads();
-    double inv = 1.0 / L[j][j];
+    double inv = inv_sh;
     if (tx == (j & 15)) {
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
@@ -67,13 +70,18 @@ __global__ void k_potrf_diag(double* Wk, int64_t ldw, int64_t k0, int kb, int* s
       }
     }
     __syncthreads();
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        int i = ty + 16 * r, l = tx + 16 * c;
-        if (l > j && l <= i && i < kb) L[i][l] -= L[i][j] * L[l][j];
-      }
+    // rank-1 update of the trailing triangle j < l <= i < kb: only the active
+    // elements are enumerated, so no FP64 issue slot goes to masked lanes
+    int m = kb - j - 1;
+    int tot = m * (m + 1) / 2;
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+      int ii = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+      while (ii * (ii + 1) / 2 > e) --ii;
+      while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
+      int ll = e - ii * (ii + 1) / 2;
+      int i = j + 1 + ii, l = j + 1 + ll;
+      L[i][l] -= L[i][j] * L[l][j];
+    }
     __syncthreads();
   }
 #pragma unroll
@@ -85,42 +93,47 @@ __global__ void k_potrf_diag(double* Wk, int64_t ldw, int64_t k0, int kb, int* s
     }
 }
 
-#define TRSM_ROWS 64
-// rows r in [r0, r1): x L11^T = a; 8 warps per block, 8 rows per warp, one
-// warp per row at a time (column-oriented solve with a shuffle broadcast)
+#define TRSM_ROWS 32
+// rows r in [r0, r1): x L11^T = a by forward substitution, one row per lane
+// (32 rows per block): every lane runs the whole recurrence of its own row in
+// registers, reading L11 from shared memory by broadcast, so no FP64 issue slot
+// is spent on masked lanes
 __global__ void k_trsm_rows(double* Wk, int64_t ldw, int64_t k0, int kb, int64_t r0, int64_t r1) {
   __shared__ double L[NB][NB + 1];
   __shared__ double invd[NB];
-  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      int i = ty + 16 * r, l = tx + 16 * c;
-      L[i][l] = (i < kb && l <= i) ? Wk[(k0 + i) * ldw + k0 + l] : 0.0;
-    }
-  __syncthreads();
-  if (threadIdx.x < kb) invd[threadIdx.x] = 1.0 / L[threadIdx.x][threadIdx.x];
-  __syncthreads();
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int t = 0; t < TRSM_ROWS / 8; ++t) {
-    int64_t r = r0 + (int64_t)blockIdx.x * TRSM_ROWS + warp + 8 * t;
-    if (r >= r1) break;
-    double* row = Wk + r * ldw + k0;
-    double a0 = lane < kb ? row[lane] : 0.0;
-    double a1 = lane + 32 < kb ? row[lane + 32] : 0.0;
-    for (int j = 0; j < kb; ++j) {
-      double own = (j < 32) ? a0 : a1;
-      double xj = __shfl_sync(0xffffffffu, own, j & 31) * invd[j];
-      if (lane == (j & 31)) {
-        if (j < 32) a0 = xj; else a1 = xj;
-      }
-      if (lane > j && lane < kb) a0 -= xj * L[lane][j];
-      if (lane + 32 > j && lane + 32 < kb) a1 -= xj * L[lane + 32][j];
-    }
-    if (lane < kb) row[lane] = a0;
-    if (lane + 32 < kb) row[lane + 32] = a1;
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    int i = e >> 6, l = e & 63;
+    L[i][l] = (i < kb && l <= i) ? Wk[(k0 + i) * ldw + k0 + l] : 0.0;
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kb; i += blockDim.x) invd[i] = 1.0 / L[i][i];
+  __syncthreads();
+  int64_t r = r0 + (int64_t)blockIdx.x * TRSM_ROWS + threadIdx.x;
+  if (r >= r1) return;
+  double* row = Wk + r * ldw + k0;
+  double x[NB];
+#pragma unroll
+  for (int j = 0; j < NB; ++j) x[j] = (j < kb) ? row[j] : 0.0;
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    if (j < kb) {
+      // four independent partial sums break the FP64 dependency chain
+      double v0 = x[j], v1 = 0.0, v2 = 0.0, v3 = 0.0;
+#pragma unroll
+      for (int l = 0; l + 3 < j; l += 4) {
+        v0 -= x[l] * L[j][l];
+        v1 -= x[l + 1] * L[j][l + 1];
+        v2 -= x[l + 2] * L[j][l + 2];
+        v3 -= x[l + 3] * L[j][l + 3];
+      }
+#pragma unroll
+      for (int l = j & ~3; l < j; ++l) v0 -= x[l] * L[j][l];
+      x[j] = ((v0 + v1) + (v2 + v3)) * invd[j];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NB; ++j)
+    if (j < kb) row[j] = x[j];
 }
 
 __global__ void k_snr_prefix(int64_t Ms, const double* Wk, int64_t ldw, const int64_t* cnt, int nl, double* out) {
@@ -197,7 +210,8 @@ int wl_snr(cov_handle* h, const double* C, int64_t ldc, const double* D, int whi
     k_potrf_diag<<<1, 256, 0, s>>>(h->work, ldw, k0, kb, st);
     int64_t r0 = k0 + kb, r1 = Ms + 1;
     if (r1 > r0) {
-      k_trsm_rows<<<(unsigned)((r1 - r0 + TRSM_ROWS - 1) / TRSM_ROWS), 256, 0, s>>>(h->work, ldw, k0, kb, r0, r1);
+      k_trsm_rows<<<(unsigned)((r1 - r0 + TRSM_ROWS - 1) / TRSM_ROWS), TRSM_ROWS, 0, s>>>(h->work, ldw, k0, kb, r0,
+                                                                                           r1);
       // trailing update on the tensor cores, FP64-accurate by exact slicing
       int rc = wl_chol_update_tc(h, h->work, ldw, k0, kb, r0, r1, h->chol_scratch, h->chol_status, s);
       if (rc) return rc;

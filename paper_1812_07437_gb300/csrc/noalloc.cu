@@ -116,7 +116,7 @@ extern "C" int cov_snr_noalloc(const double* d_C, int64_t ldc, const double* d_D
     k_potrf_diag<<<1, 256, 0, s>>>(work, ldw, k0, kb, d_status);
     int64_t r0 = k0 + kb, r1 = M + 1;
     if (r1 > r0) {
-      k_trsm_rows<<<(unsigned)((r1 - r0 + 63) / 64), 256, 0, s>>>(work, ldw, k0, kb, r0, r1);
+      k_trsm_rows<<<(unsigned)((r1 - r0 + 31) / 32), 32, 0, s>>>(work, ldw, k0, kb, r0, r1);
       int64_t n = r1 - r0;
       int64_t nt1 = (n + 63) / 64;
       double* P = work + r0 * ldw + k0;
