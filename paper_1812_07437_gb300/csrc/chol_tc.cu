@@ -221,8 +221,9 @@ __global__ void __launch_bounds__(128, 1)
     double* stg = (double*)smem + warp * (32 * 33);
 #pragma unroll 1
     for (int c = 0; c < CS_BJ / 32; ++c) {
-      // the six group sums are exact integers (< 2^23): combine them exactly
-      // in int64, v = sum_g acc_g 2^(8 (5 - g)), then one conversion to FP64
+      // the six group sums are exact integers (< 2^23, so int32 conversions
+      // are exact and stay off the FP64 pipe): combine them exactly in int64,
+      // v = sum_g acc_g 2^(8 (5 - g)), then one conversion to FP64
       long long acc[32];
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) acc[jj] = 0;
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(128, 1)
         float v[32];
         cs_tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * CS_BJ + c * 32), v);
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) acc[jj] = (acc[jj] << 8) + (long long)__float2ll_rn(v[jj]);
+        for (int jj = 0; jj < 32; ++jj) acc[jj] = (acc[jj] << 8) + (long long)__float2int_rn(v[jj]);
       }
       // value = acc 2^(e_i + e_j - 14 - 8 (S - 1)); the e_j part is applied per column below
 #pragma unroll
