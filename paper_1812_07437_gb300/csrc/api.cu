@@ -184,7 +184,7 @@ static void free_all(cov_handle* h) {
   h->pending.clear();
   h->pool.clear();
   void* ptrs[] = {h->gl64x, h->gl64w, h->glkx, h->glkw, h->glcx, h->glcw, h->scal, h->chi, h->wchi, h->z, h->D,
-                  h->ell_d, h->m, h->om, h->sig0, h->dlns, h->f, h->b1, h->b2, h->U, h->Pl, h->dPl, h->zedges,
+                  h->ell_d, h->m, h->om, h->sig0, h->dlns, h->f, h->b1, h->b2, h->U, h->Pl, h->dPl, h->Psh, h->zedges,
                   h->norms, h->W, h->sigw2, h->slo_d, h->shi_d, h->Nmodes, h->Ntri, h->rowtab, h->tris_d,
                   h->rowdesc_d, h->P3, h->RP3, h->B3, h->RB3, h->B1h3, h->Ps, h->B1hp, h->Bp, h->A, h->Ahi,
                   h->Alo, h->Ascale, h->G2, h->G3, h->C2, h->C3, h->tc_status, h->Thi, h->Tlo, h->Tscale, h->Trows, h->Tmat, h->Srows, h->work, h->perm, h->chol_scratch, h->chol_status};
@@ -231,6 +231,7 @@ extern "C" int cov_init(const cov_cosmology* cosmo, const cov_nz* nz, const cov_
       {(void**)&h->f, d * nchi * nm},       {(void**)&h->b1, d * nchi * nm},
       {(void**)&h->b2, d * nchi * nm},      {(void**)&h->U, d * (size_t)nl * nchi * nm},
       {(void**)&h->Pl, d * nl * nchi},      {(void**)&h->dPl, d * nl * nchi},
+      {(void**)&h->Psh, d * 4 * nl * nchi},
       {(void**)&h->zedges, d * (nt + 1)},   {(void**)&h->norms, d * nt},
       {(void**)&h->W, d * nt * nchi},       {(void**)&h->sigw2, d * nchi},
       {(void**)&h->slo_d, 8ul * nl},          {(void**)&h->shi_d, 8ul * nl},

@@ -73,6 +73,7 @@ struct cov_handle {
   double *chi = nullptr, *wchi = nullptr, *z = nullptr, *D = nullptr;
   double *ell_d = nullptr, *m = nullptr, *om = nullptr, *sig0 = nullptr, *dlns = nullptr;
   double *f = nullptr, *b1 = nullptr, *b2 = nullptr, *U = nullptr, *Pl = nullptr, *dPl = nullptr;
+  double* Psh = nullptr;  // [n_ell][n_chi][4] P_lin at the shifted k of the ln k differences
   double *zedges = nullptr, *norms = nullptr, *W = nullptr, *sigw2 = nullptr;
   int64_t *slo_d = nullptr, *shi_d = nullptr, *Nmodes = nullptr, *Ntri = nullptr;
   int32_t* rowtab = nullptr;  // [nl][2][rmax+1]: x_outer, x_inner per row

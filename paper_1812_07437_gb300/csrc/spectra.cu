@@ -55,20 +55,22 @@ __device__ __forceinline__ double bpt3(double k1, double k2, double k3, double P
   return 2.0 * f2k(k1, k2, m12) * P1 * P2 + 2.0 * f2k(k2, k3, m23) * P2 * P3 + 2.0 * f2k(k3, k1, m31) * P3 * P1;
 }
 
-// B^PT with side i scaled by exp(s) (the other two fixed)
-__device__ __forceinline__ double bpt_shift(const double* k, int i, double s, double Dg, double amp,
-                                            const cov_cosmology& c) {
+// B^PT with side i scaled by exp(s) (the other two fixed); Pi_s is P_lin at
+// the shifted side, read from the table of shifted linear spectra
+__device__ __forceinline__ double bpt_shift(const double* k, const double* P, int i, double s, double Pi_s) {
   double kk[3] = {k[0], k[1], k[2]};
+  double pp[3] = {P[0], P[1], P[2]};
   kk[i] *= exp(s);
-  return bpt3(kk[0], kk[1], kk[2], dev_plin(kk[0], Dg, amp, c), dev_plin(kk[1], Dg, amp, c),
-              dev_plin(kk[2], Dg, amp, c));
+  pp[i] = Pi_s;
+  return bpt3(kk[0], kk[1], kk[2], pp[0], pp[1], pp[2]);
 }
 
 // One warp per (triple, node): B^HM, its response and the 1-halo B.
 __global__ void k_bspec(cov_cosmology c, int ntri, int nchi, int nm, double kmax, const int32_t* tris,
                         const double* ell, const double* chi, const double* D, const double* m, const double* om,
                         const double* f, const double* b1, const double* b2, const double* U, const double* Pl,
-                        const double* dPl, const double* scal, double* B3, double* RB3, double* B1h3) {
+                        const double* dPl, const double* Psh, const double* scal, double* B3, double* RB3,
+                        double* B1h3) {
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= ntri * nchi) return;
   int t = warp / nchi, n = warp % nchi;
@@ -137,15 +139,16 @@ __global__ void k_bspec(cov_cosmology c, int ntri, int nchi, int nm, double kmax
   B3[tn] = i30 + b2h + b3h;
   B1h3[tn] = i30;
   // response (Eqs. BispHMResp, RespB)
-  double amp = scal[SC_AMP], Dg = D[n];
   double bg2 = 2.0 * ((m12 * m12 - 1.0) * P[0] * P[1] + (m23 * m23 - 1.0) * P[1] * P[2] +
                       (m31 * m31 - 1.0) * P[2] * P[0]);
   const double h = WL_FD_H;
   double dsum = 0.0;
-  for (int i = 0; i < 3; ++i)
-    dsum += (-bpt_shift(k, i, 2 * h, Dg, amp, c) + 8.0 * bpt_shift(k, i, h, Dg, amp, c) -
-             8.0 * bpt_shift(k, i, -h, Dg, amp, c) + bpt_shift(k, i, -2 * h, Dg, amp, c)) /
+  for (int i = 0; i < 3; ++i) {
+    const double* ps = Psh + ((size_t)l[i] * nchi + n) * 4;  // s = -2h, -h, +h, +2h
+    dsum += (-bpt_shift(k, P, i, 2 * h, ps[3]) + 8.0 * bpt_shift(k, P, i, h, ps[2]) -
+             8.0 * bpt_shift(k, P, i, -h, ps[1]) + bpt_shift(k, P, i, -2 * h, ps[0])) /
             (12.0 * h);
+  }
   double rbpt = 433.0 / 126.0 * bpt + 5.0 / 126.0 * bg2 - dsum / 3.0;
   double r = i11[0] * i11[1] * i11[2] * rbpt;
   for (int x = 0; x < 3; ++x) r += i11[x] * i22[x] * P[x] + i11[x] * i21[x] * rl[x];
@@ -277,8 +280,8 @@ int wl_spectra(cov_handle* h, double* d_D, cudaStream_t s) {
   if (h->ntri > 0) {
     warps = h->ntri * nchi;
     k_bspec<<<(warps * 32 + 255) / 256, 256, 0, s>>>(c, h->ntri, nchi, nm, kmax, h->tris_d, h->ell_d, h->chi, h->D,
-                                                     h->m, h->om, h->f, h->b1, h->b2, h->U, h->Pl, h->dPl, h->scal,
-                                                     h->B3, h->RB3, h->B1h3);
+                                                     h->m, h->om, h->f, h->b1, h->b2, h->U, h->Pl, h->dPl, h->Psh,
+                                                     h->scal, h->B3, h->RB3, h->B1h3);
     int64_t nb = (int64_t)h->ntri * nt * nt * nt;
     k_proj_b<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(h->ntri, nt, nchi, h->chi, h->wchi, h->W, h->B1h3,
                                                           h->B1hp);

@@ -45,10 +45,13 @@ __device__ double dev_growth_raw(double at, const cov_cosmology& c) {
   double h = (x1 - x) / WL_N_RK4;
   double d = WL_A_INIT, dp = WL_A_INIT;
   double om = c.Om, ode = 1.0 - c.Om, w = c.w0;
-  const bool lambda_cdm = (w == -1.0);
-  auto rhs = [&](double lna, double yd, double yp, double* fd, double* fp) {
-    double em = om * exp(-3.0 * lna);
-    double ed = lambda_cdm ? ode : ode * exp(-3.0 * (1.0 + w) * lna);
+  // a^-3 and a^(-3(1+w)) at the RK4 stage points x, x + h/2, x + h advance
+  // by constant factors, so the loop needs no transcendental per stage
+  const double qm = exp(-1.5 * h), qd = exp(-1.5 * (1.0 + w) * h);
+  double am = exp(-3.0 * x), ad = exp(-3.0 * (1.0 + w) * x);
+  auto rhs = [&](double em_a, double ed_a, double yd, double yp, double* fd, double* fp) {
+    double em = om * em_a;
+    double ed = ode * ed_a;
     double e2 = em + ed;
     double dlnh = 0.5 * (-3.0 * em - 3.0 * (1.0 + w) * ed) / e2;
     *fd = yp;
@@ -56,10 +59,13 @@ __device__ double dev_growth_raw(double at, const cov_cosmology& c) {
   };
   for (int s = 0; s < WL_N_RK4; ++s) {
     double k1d, k1p, k2d, k2p, k3d, k3p, k4d, k4p;
-    rhs(x, d, dp, &k1d, &k1p);
-    rhs(x + 0.5 * h, d + 0.5 * h * k1d, dp + 0.5 * h * k1p, &k2d, &k2p);
-    rhs(x + 0.5 * h, d + 0.5 * h * k2d, dp + 0.5 * h * k2p, &k3d, &k3p);
-    rhs(x + h, d + h * k3d, dp + h * k3p, &k4d, &k4p);
+    double am_h = am * qm, ad_h = ad * qd, am_1 = am_h * qm, ad_1 = ad_h * qd;
+    rhs(am, ad, d, dp, &k1d, &k1p);
+    rhs(am_h, ad_h, d + 0.5 * h * k1d, dp + 0.5 * h * k1p, &k2d, &k2p);
+    rhs(am_h, ad_h, d + 0.5 * h * k2d, dp + 0.5 * h * k2p, &k3d, &k3p);
+    rhs(am_1, ad_1, d + h * k3d, dp + h * k3p, &k4d, &k4p);
+    am = am_1;
+    ad = ad_1;
     d = d + (h / 6.0) * (k1d + 2.0 * k2d + 2.0 * k3d + k4d);
     dp = dp + (h / 6.0) * (k1p + 2.0 * k2p + 2.0 * k3p + k4p);
     x = x + h;
@@ -191,7 +197,7 @@ __global__ void k_halo(cov_cosmology c, int nm, const double* D, const double* m
 // NFW profiles on the Limber grid and P_lin, dP_lin/dln k at k = l_b/chi_n
 __global__ void k_profiles(cov_cosmology c, cov_bins b, const double* ell, const double* chi, const double* z,
                            const double* D, const double* m, const double* scal, double* U, double* Pl,
-                           double* dPl) {
+                           double* dPl, double* Psh) {
   int bn = blockIdx.x;  // b * nchi + n
   int nchi = b.n_chi, nm = b.n_mass;
   int bb = bn / nchi, n = bn % nchi;
@@ -200,6 +206,12 @@ __global__ void k_profiles(cov_cosmology c, cov_bins b, const double* ell, const
   double rho = WL_RHO_CRIT0 * c.Om;
   for (int q = threadIdx.x; q < nm; q += blockDim.x)
     U[(size_t)bn * nm + q] = valid ? dev_nfw_u(k, m[q], z[n], rho) : 0.0;
+  if (threadIdx.x < 4) {
+    // P_lin at k exp(s), s = -2h, -h, +h, +2h (the 4th-order differences in ln k)
+    const double sh[4] = {-2.0 * WL_FD_H, -WL_FD_H, WL_FD_H, 2.0 * WL_FD_H};
+    double amp = scal[SC_AMP];
+    Psh[(size_t)bn * 4 + threadIdx.x] = valid ? dev_plin(k * exp(sh[threadIdx.x]), D[n], amp, c) : 0.0;
+  }
   if (threadIdx.x == 0) {
     double amp = scal[SC_AMP];
     Pl[bn] = valid ? dev_plin(k, D[n], amp, c) : 0.0;
@@ -345,7 +357,7 @@ int wl_tables(cov_handle* h, cudaStream_t s) {
   k_sigma<<<h->nm, 256, 0, s>>>(c, b, h->glkx, h->glkw, h->scal, h->m, h->om, h->sig0, h->dlns);
   k_halo<<<h->nchi, 128, 0, s>>>(c, h->nm, h->D, h->m, h->om, h->sig0, h->dlns, h->f, h->b1, h->b2);
   k_profiles<<<h->nl * h->nchi, 128, 0, s>>>(c, b, h->ell_d, h->chi, h->z, h->D, h->m, h->scal, h->U, h->Pl,
-                                             h->dPl);
+                                             h->dPl, h->Psh);
   k_edges<<<1, 64, 0, s>>>(nz, h->zedges, h->scal);
   k_norms<<<h->nt, 64, 0, s>>>(nz, h->zedges, h->gl64x, h->gl64w, h->norms);
   k_kernels<<<h->nchi, 64, 0, s>>>(c, nz, h->nchi, h->chi, h->z, h->zedges, h->norms, h->gl64x, h->gl64w, h->W);
