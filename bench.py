@@ -40,6 +40,7 @@ def parse():
     p.add_argument("--workload", default="cfg2_5bin")
     p.add_argument("--precision", default="auto", choices=["auto", "fp64", "split_bf16"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp64-form", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     return p.parse_args()
 
@@ -170,15 +171,16 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- GPU arm
-def launches_per_step(h, which_sizes, n_tri):
-    tables = 13
+def launches_per_step(which_sizes, n_tri, split):
+    """Kernels of libwlcov launched by one step (memsets not counted)."""
+    tables = 11          # chi_max, los, growth_norm, amplitude, sigma, halo, profiles, edges, norms, kernels, sigw2
     counts = 3 if n_tri > 0 else 2
     spectra = 5 if n_tri > 0 else 3
-    assemble = 7
-    snr = 0
+    assemble = 7         # split: rows_t, split(T), tc(T), rows_prep, rows_split, tc(1h+SSC), gather
+    snr = 0              # FP64: rows_t, gemm(T), rows_a, gemm(1h), gather, rows_s, gemm(SSC)
     for ms in which_sizes:
         nb = (ms + 63) // 64
-        snr += 2 + 3 * nb
+        snr += 2 + 4 * nb  # pack, prefix; per panel: diagonal block, panel solve, slice, tensor-core update
     return tables + counts + spectra + assemble + snr
 
 
@@ -265,15 +267,45 @@ def run_ours(args):
             stream.synchronize()
         e2e_s = (time.perf_counter() - t0) / args.steps
 
+        # the plain FP64 form of the same step (the comparison point of the
+        # reduced-precision form): a short timed run after the main one
+        fp64 = None
+        if prec != N.COV_FP64 and not args.no_fp64_form:
+            def step64():
+                h.update(cosmo, stream)
+                h.spectra(D, stream)
+                h.assemble(C, N.COV_TERMS_ALL, N.COV_FP64, stream)
+                return [h.snr(C, D, w, stream) for w in which]
+            step64()
+            torch.cuda.synchronize()
+            h.profile(True)
+            h.stage_times()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for _ in range(2):
+                step64()
+            f1.record(stream)
+            torch.cuda.synchronize()
+            st64 = h.stage_times()
+            h.profile(False)
+            ms64 = f0.elapsed_time(f1) / 2
+            s1h = st64["syrk_1h"][0] / max(st64["syrk_1h"][1], 1)
+            fp64 = {"ms_per_step": ms64, "value": elements / (ms64 / 1e3), "unit": UNIT,
+                    "syrk_1h_ms": s1h, "syrk_1h_tflops": 2.0 * elements * wl["bins"]["n_chi"]
+                    * wl["bins"]["n_mass"] / (s1h / 1e3) / 1e12}
+
     t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
     if world > 1:
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     ms_step = float(t.item()) / args.steps
     value = world * elements / (ms_step / 1e3)
 
-    # roofline of the dominant kernel: the 1-halo (chi, M) contraction
+    # roofline of the 1-halo (chi, M) contraction, the kernel the metric is built on
     syrk_ms, syrk_calls = stages["syrk_1h"]
     K = wl["bins"]["n_chi"] * wl["bins"]["n_mass"]
+    if prec != N.COV_FP64:
+        K += wl["bins"]["n_chi"]  # the super-sample rows ride along in the split contraction
     flops = 2.0 * elements * K
     avg_ms = syrk_ms / max(syrk_calls, 1)
     achieved = flops / (avg_ms / 1e3) / 1e12
@@ -292,6 +324,12 @@ def run_ours(args):
                 "algorithmic_tflops": achieved, "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}
 
     sizes = [h.n_P, h.n_B, M]
+    # the S/N factorisations hold most of the step: report their tensor-core
+    # trailing update too (FP64-equivalent work M^3/3 per factorisation)
+    chol_ms = stages["snr_cholesky"][0] / max(args.steps, 1)
+    chol_flops = sum(m ** 3 / 3.0 for m in sizes)
+    roof["cholesky"] = {"stage_ms_per_step": chol_ms, "fp64_equivalent_tflops": chol_flops / (chol_ms / 1e3) / 1e12,
+                        "note": "diagonal blocks and panel solves in FP64, trailing updates on tcgen05 by exact slicing"}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64" if prec == N.COV_FP64 else "bf16x3+f64",
@@ -305,7 +343,8 @@ def run_ours(args):
            "roofline": roof,
            "e2e": {"value": world * elements / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 56,
                    "d2h_bytes_per_step": M * M * 8 + M * 8 + 3 * wl["bins"]["n_ell"] * 8},
-           "gpu_launches": args.steps * launches_per_step(h, sizes, h.n_tri),
+           "gpu_launches": args.steps * launches_per_step(sizes, h.n_tri, prec != N.COV_FP64),
+           "fp64_form": fp64,
            "clocks": clocks,
            "stages_ms_per_step": {k: v[0] / max(args.steps, 1) for k, v in stages.items()},
            "snr_joint_max": float(np.nanmax(snr[2]))}

@@ -73,12 +73,15 @@ __device__ double dev_growth_raw(double at, const cov_cosmology& c) {
   return d;
 }
 
-// chi(z_max) and the growth integration carried to a = 1 (shared by all nodes)
+// chi(z_max)
 __global__ void k_chimax(cov_cosmology c, double zmax, const double* glx, const double* glw, double* scal) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    scal[SC_CHIMAX] = dev_chi_of_z(zmax, c, glx, glw);
-    scal[SC_D1] = dev_growth_raw(1.0, c);
-  }
+  if (threadIdx.x == 0 && blockIdx.x == 0) scal[SC_CHIMAX] = dev_chi_of_z(zmax, c, glx, glw);
+}
+
+// D(z_n) = D_raw(a_n) / D_raw(1)
+__global__ void k_growth_norm(int nchi, const double* scal, double* D) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < nchi) D[n] /= scal[SC_D1];
 }
 
 // line-of-sight nodes: chi_n (GL on [0, chi_max]), weights, z(chi_n), D(z_n);
@@ -86,7 +89,12 @@ __global__ void k_chimax(cov_cosmology c, double zmax, const double* glx, const 
 __global__ void k_los(cov_cosmology c, int nchi, const double* glcx, const double* glcw, const double* gl64x,
                       const double* gl64w, const double* scal, double* chi, double* wchi, double* z, double* D) {
   int n = blockIdx.x;
-  if (n >= nchi || threadIdx.x != 0) return;
+  if (threadIdx.x != 0 || n > nchi) return;
+  if (n == nchi) {  // one extra block: the growth integration carried to a = 1
+    double* sc = (double*)scal;
+    sc[SC_D1] = dev_growth_raw(1.0, c);
+    return;
+  }
   double cm = scal[SC_CHIMAX];
   double ch = 0.5 * cm * (glcx[n] + 1.0);
   chi[n] = ch;
@@ -99,7 +107,7 @@ __global__ void k_los(cov_cosmology c, int nchi, const double* glcx, const doubl
     if (fabs(step) < 1e-15 * (1.0 + zz)) break;
   }
   z[n] = zz;
-  D[n] = dev_growth_raw(1.0 / (1.0 + zz), c) / scal[SC_D1];
+  D[n] = dev_growth_raw(1.0 / (1.0 + zz), c);  // normalised by k_growth_norm
 }
 
 // sigma_8 normalisation: amplitude A of P_lin(k,0) = A k^ns T^2
@@ -351,8 +359,9 @@ int wl_tables(cov_handle* h, cudaStream_t s) {
   const cov_bins b = h->bins;
   const cov_nz nz = h->nz;
   k_chimax<<<1, 1, 0, s>>>(c, nz.zmax, h->gl64x, h->gl64w, h->scal);
-  k_los<<<h->nchi, 32, 0, s>>>(c, h->nchi, h->glcx, h->glcw, h->gl64x, h->gl64w, h->scal, h->chi,
+  k_los<<<h->nchi + 1, 32, 0, s>>>(c, h->nchi, h->glcx, h->glcw, h->gl64x, h->gl64w, h->scal, h->chi,
                                             h->wchi, h->z, h->D);
+  k_growth_norm<<<(h->nchi + 127) / 128, 128, 0, s>>>(h->nchi, h->scal, h->D);
   k_amplitude<<<1, 256, 0, s>>>(c, h->glkx, h->glkw, h->scal);
   k_sigma<<<h->nm, 256, 0, s>>>(c, b, h->glkx, h->glkw, h->scal, h->m, h->om, h->sig0, h->dlns);
   k_halo<<<h->nchi, 128, 0, s>>>(c, h->nm, h->D, h->m, h->om, h->sig0, h->dlns, h->f, h->b1, h->b2);
