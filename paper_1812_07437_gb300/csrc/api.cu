@@ -181,6 +181,9 @@ static void free_all(cov_handle* h) {
     cudaEventDestroy(se.b);
   }
   for (auto e : h->pool) cudaEventDestroy(e);
+  if (h->ev_cols) cudaEventDestroy(h->ev_cols);
+  if (h->ev_panel) cudaEventDestroy(h->ev_panel);
+  if (h->side) cudaStreamDestroy(h->side);
   h->pending.clear();
   h->pool.clear();
   void* ptrs[] = {h->gl64x, h->gl64w, h->glkx, h->glkw, h->glcx, h->glcw, h->scal, h->chi, h->wchi, h->z, h->D,

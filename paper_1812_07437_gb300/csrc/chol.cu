@@ -180,7 +180,8 @@ int wl_snr(cov_handle* h, const double* C, int64_t ldc, const double* D, int whi
     h->work_n = need;
   }
   if (!h->perm) WL_CHECK(h, cudaMalloc(&h->perm, sizeof(int) * h->M));
-  size_t need_sc = wl_chol_tc_bytes(Ms + 1);
+  size_t one_buf = (wl_chol_tc_bytes(Ms + 1) + 255) / 256 * 256;
+  size_t need_sc = 2 * one_buf;
   if (need_sc > h->chol_scratch_n) {
     if (h->chol_scratch) cudaFree(h->chol_scratch);
     h->chol_scratch = nullptr;
@@ -189,6 +190,11 @@ int wl_snr(cov_handle* h, const double* C, int64_t ldc, const double* D, int whi
     h->chol_scratch_n = need_sc;
   }
   if (!h->chol_status) WL_CHECK(h, cudaMalloc(&h->chol_status, sizeof(int)));
+  if (!h->side) {
+    WL_CHECK(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    WL_CHECK(h, cudaEventCreateWithFlags(&h->ev_cols, cudaEventDisableTiming));
+    WL_CHECK(h, cudaEventCreateWithFlags(&h->ev_panel, cudaEventDisableTiming));
+  }
   WL_CHECK(h, cudaMemsetAsync(h->chol_status, 0, sizeof(int), s));
   int* st = nullptr;
   int64_t* cnt_d = nullptr;
@@ -205,16 +211,39 @@ int wl_snr(cov_handle* h, const double* C, int64_t ldc, const double* D, int whi
   WL_LAUNCH(h, "k_snr_pack");
   wl_stage_end(h, tk, s);
   tk = wl_stage_begin(h, ST_SNR_CHOL, s);
+  // Blocked right-looking factorisation with one panel of look-ahead: the
+  // trailing update of panel p first updates the 64 columns of panel p+1,
+  // then the FP64 diagonal block, panel solve and slicing of panel p+1 run on
+  // the side stream while the rest of the update of panel p runs here.
+  uint8_t* bufs[2] = {(uint8_t*)h->chol_scratch, (uint8_t*)h->chol_scratch + one_buf};
+  auto panel = [&](int64_t k0, cudaStream_t st_) -> int {
+    int kb = (int)std::min<int64_t>(NB, Ms - k0);
+    k_potrf_diag<<<1, 256, 0, st_>>>(h->work, ldw, k0, kb, st);
+    int64_t r0 = k0 + kb, r1 = Ms + 1;
+    if (r1 > r0)
+      k_trsm_rows<<<(unsigned)((r1 - r0 + TRSM_ROWS - 1) / TRSM_ROWS), TRSM_ROWS, 0, st_>>>(h->work, ldw, k0, kb, r0,
+                                                                                            r1);
+    WL_LAUNCH(h, "Cholesky panel kernels");
+    return wl_chol_slice(h, h->work, ldw, k0, kb, r0, r1, bufs[(k0 / NB) & 1], st_);
+  };
+  int rc = panel(0, s);
+  if (rc) return rc;
   for (int64_t k0 = 0; k0 < Ms; k0 += NB) {
     int kb = (int)std::min<int64_t>(NB, Ms - k0);
-    k_potrf_diag<<<1, 256, 0, s>>>(h->work, ldw, k0, kb, st);
     int64_t r0 = k0 + kb, r1 = Ms + 1;
-    if (r1 > r0) {
-      k_trsm_rows<<<(unsigned)((r1 - r0 + TRSM_ROWS - 1) / TRSM_ROWS), TRSM_ROWS, 0, s>>>(h->work, ldw, k0, kb, r0,
-                                                                                           r1);
-      // trailing update on the tensor cores, FP64-accurate by exact slicing
-      int rc = wl_chol_update_tc(h, h->work, ldw, k0, kb, r0, r1, h->chol_scratch, h->chol_status, s);
-      if (rc) return rc;
+    const void* buf = bufs[(k0 / NB) & 1];
+    if (r0 < Ms) {
+      // columns of the next panel first, then the next panel on the side stream
+      if ((rc = wl_chol_update(h, h->work, ldw, r0, r1, buf, 0, 1, h->chol_status, s))) return rc;
+      WL_CHECK(h, cudaEventRecord(h->ev_cols, s));
+      WL_CHECK(h, cudaStreamWaitEvent(h->side, h->ev_cols, 0));
+      if ((rc = panel(r0, h->side))) return rc;
+      WL_CHECK(h, cudaEventRecord(h->ev_panel, h->side));
+      if ((rc = wl_chol_update(h, h->work, ldw, r0, r1, buf, 1, -1, h->chol_status, s))) return rc;
+      WL_CHECK(h, cudaStreamWaitEvent(s, h->ev_panel, 0));
+    } else if (r1 > r0) {
+      // only the extra D row is left below this panel
+      if ((rc = wl_chol_update(h, h->work, ldw, r0, r1, buf, 0, -1, h->chol_status, s))) return rc;
     }
   }
   WL_LAUNCH(h, "Cholesky kernels");

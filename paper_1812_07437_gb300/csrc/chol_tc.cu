@@ -111,12 +111,13 @@ __device__ __forceinline__ void cs_tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// grid.x = tile row (128 rows), grid.y = tile column (64 columns)
+// grid.x = tile row (128 rows), grid.y = tile column (64 columns) - tj0
 __global__ void __launch_bounds__(128, 1)
     k_chol_update(const __grid_constant__ CUtensorMap map_i, const __grid_constant__ CUtensorMap map_j,
                   int64_t nrows, int64_t nrows_pad, const int* __restrict__ rexp, double* Csub, int64_t ldc,
-                  int* status) {
-  int ti = blockIdx.x, tj = blockIdx.y;
+                  int* status, int tj0) {
+  int tj = blockIdx.y + tj0;
+  int ti = blockIdx.x + (tj0 * CS_BJ) / CS_BI;
   if ((int64_t)tj * CS_BJ > (int64_t)ti * CS_BI + CS_BI - 1) return;  // tile above the diagonal
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar;
@@ -287,23 +288,38 @@ static int cs_map(cov_handle* h, CUtensorMap* map, void* base, int64_t total_row
   return COV_OK;
 }
 
-// bytes of the slice workspace for up to n trailing rows
+// bytes of one slice buffer for up to n trailing rows
 size_t wl_chol_tc_bytes(int64_t n) {
   int64_t pad = (n + CS_BI - 1) / CS_BI * CS_BI;
   return (size_t)CS_S * pad * CS_K * 2 + (size_t)pad * sizeof(int);
 }
 
-// Csub (rows/cols r0..r1-1 of the workspace, leading dimension ldw) -=
-// L21 L21^T with L21 = rows r0..r1-1, columns k0..k0+kb-1, lower triangle only
-int wl_chol_update_tc(cov_handle* h, double* Wk, int64_t ldw, int64_t k0, int kb, int64_t r0, int64_t r1,
-                      void* scratch, int* status, cudaStream_t s) {
+// slices of the panel rows r0..r1-1, columns k0..k0+kb-1 of the workspace
+int wl_chol_slice(cov_handle* h, const double* Wk, int64_t ldw, int64_t k0, int kb, int64_t r0, int64_t r1,
+                  void* buf, cudaStream_t s) {
   int64_t n = r1 - r0;
   if (n <= 0) return COV_OK;
   int64_t pad = (n + CS_BI - 1) / CS_BI * CS_BI;
-  __nv_bfloat16* slices = (__nv_bfloat16*)scratch;
-  int* rexp = (int*)((uint8_t*)scratch + (size_t)CS_S * pad * CS_K * 2);
+  __nv_bfloat16* slices = (__nv_bfloat16*)buf;
+  int* rexp = (int*)((uint8_t*)buf + (size_t)CS_S * pad * CS_K * 2);
   k_chol_slice<<<(unsigned)((pad + 7) / 8), 256, 0, s>>>(Wk, ldw, k0, kb, r0, n, pad, slices, rexp);
   WL_LAUNCH(h, "k_chol_slice");
+  return COV_OK;
+}
+
+// Csub (rows/cols r0..r1-1 of the workspace) -= L21 L21^T over the column
+// tiles tj0 .. tj0+ntj-1 (64 columns each; ntj < 0: all remaining), lower
+// triangle only, from the slices in buf
+int wl_chol_update(cov_handle* h, double* Wk, int64_t ldw, int64_t r0, int64_t r1, const void* buf, int tj0, int ntj,
+                   int* status, cudaStream_t s) {
+  int64_t n = r1 - r0;
+  if (n <= 0) return COV_OK;
+  int64_t pad = (n + CS_BI - 1) / CS_BI * CS_BI;
+  int total_tj = (int)((n + CS_BJ - 1) / CS_BJ);
+  if (ntj < 0 || tj0 + ntj > total_tj) ntj = total_tj - tj0;
+  if (ntj <= 0) return COV_OK;
+  void* slices = (void*)buf;
+  const int* rexp = (const int*)((const uint8_t*)buf + (size_t)CS_S * pad * CS_K * 2);
   CUtensorMap mi, mj;
   int rc;
   if ((rc = cs_map(h, &mi, slices, CS_S * pad, CS_BI))) return rc;
@@ -313,8 +329,10 @@ int wl_chol_update_tc(cov_handle* h, double* Wk, int64_t ldw, int64_t k0, int kb
     WL_CHECK(h, cudaFuncSetAttribute(k_chol_update, cudaFuncAttributeMaxDynamicSharedMemorySize, CS_SMEM));
     attr = true;
   }
-  dim3 grid((unsigned)(pad / CS_BI), (unsigned)((n + CS_BJ - 1) / CS_BJ));
-  k_chol_update<<<grid, 128, CS_SMEM, s>>>(mi, mj, n, pad, rexp, Wk + r0 * ldw + r0, ldw, status);
+  // only tile rows that reach the requested columns
+  int ti0 = (int)(((int64_t)tj0 * CS_BJ) / CS_BI);
+  dim3 grid((unsigned)(pad / CS_BI - ti0), (unsigned)ntj);
+  k_chol_update<<<grid, 128, CS_SMEM, s>>>(mi, mj, n, pad, rexp, Wk + r0 * ldw + r0, ldw, status, tj0);
   WL_LAUNCH(h, "k_chol_update");
   return COV_OK;
 }

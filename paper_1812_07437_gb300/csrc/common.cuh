@@ -95,8 +95,10 @@ struct cov_handle {
   double* work = nullptr;   // Cholesky workspace (M+1)^2
   int64_t work_n = 0;
   int* perm = nullptr;      // [M] reorder for the cumulative S/N
-  void* chol_scratch = nullptr;  // slices of the tensor-core trailing update
+  void* chol_scratch = nullptr;  // two slice buffers of the tensor-core trailing update
   size_t chol_scratch_n = 0;
+  cudaStream_t side = nullptr;   // look-ahead stream of the Cholesky panel kernels
+  cudaEvent_t ev_cols = nullptr, ev_panel = nullptr;
   int* chol_status = nullptr;
   bool spectra_ready = false;
   bool prof = false;
@@ -140,8 +142,10 @@ int wl_syrk_tc(cov_handle* h, int nssc, double* d_C, int64_t ldc, cudaStream_t s
 int wl_split_bytes(int64_t M, int K, size_t* bytes);                      // syrk_tc.cu
 int wl_kpad(int K);  // K padded to the contraction's K granularity
 size_t wl_chol_tc_bytes(int64_t n);  // chol_tc.cu
-int wl_chol_update_tc(cov_handle* h, double* Wk, int64_t ldw, int64_t k0, int kb, int64_t r0, int64_t r1,
-                      void* scratch, int* status, cudaStream_t s);
+int wl_chol_slice(cov_handle* h, const double* Wk, int64_t ldw, int64_t k0, int kb, int64_t r0, int64_t r1,
+                  void* buf, cudaStream_t s);
+int wl_chol_update(cov_handle* h, double* Wk, int64_t ldw, int64_t r0, int64_t r1, const void* buf, int tj0, int ntj,
+                   int* status, cudaStream_t s);
 int wl_syrk_tc_rows(cov_handle* h, const void* hi, const void* lo, const double* rscale, int64_t rows, int Kp,
                     double* C, int64_t ldc, cudaStream_t s);
 int wl_split_rows(cov_handle* h, const double* X, int64_t rows, int K, void* hi, void* lo, double* rscale,
