@@ -1,18 +1,22 @@
 #!/usr/bin/env python
 """Benchmark of the joint P+B covariance path on GB300.
 
-One step = the whole path for one cosmology of the workload: device tables
-and exact counts (cov_update), spectra and data vector (cov_spectra), the full
-joint covariance with every term (cov_assemble) and the cumulative S/N of P,
-B and the joint vector (three cov_snr calls, FP64 Cholesky).  The metric is
-unique covariance elements M(M+1)/2 per second.
+Default workload: cfg3_10bin (10 tomographic bins, 20 ell bins on [10, 5000],
+N_chi = 256, N_M = 128, K = 32768, M = 181350).  Its covariance does not fit
+as a dense square (263 GB), so one step is: device tables and exact counts
+(cov_update), spectra and data vector (cov_spectra), and the whole joint
+covariance with every term written once as a resident lower-packed matrix of
+256 x 256 tiles (cov_assemble_band over all rows, 132 GB).  The metric is
+unique covariance elements M(M+1)/2 per second.  The S/N stage (FP64
+Cholesky of P, B and the joint vector) is timed in the same run on the 5-bin
+workload, whose dense square fits (--snr-workload).
 
-Default workload: cfg2_5bin (5 tomographic bins, 12 ell bins on [10, 5000],
-N_chi = 128, N_M = 96, M = 6375).  With --gpus N > 1 (torchrun) each rank runs
+Workloads whose dense square fits (e.g. --workload cfg2_5bin) run the whole
+path in one step, S/N included.  With --gpus N > 1 (torchrun) each rank runs
 its own cosmology of a Fisher-style set (weak scaling, no collective on the
 data path).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|split_bf16]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|split_bf16] [--workload NAME]
     python bench.py --impl reference ...   # the FP64 CPU oracle arm
 """
 import argparse
@@ -37,7 +41,10 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="cfg2_5bin")
+    p.add_argument("--workload", default="cfg3_10bin")
+    p.add_argument("--layout", default="auto", choices=["auto", "dense", "tiles"])
+    p.add_argument("--snr-workload", default="cfg2_5bin")
+    p.add_argument("--no-snr-run", action="store_true")
     p.add_argument("--precision", default="auto", choices=["auto", "fp64", "split_bf16"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64-form", action="store_true")
@@ -171,17 +178,116 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- GPU arm
-def launches_per_step(which_sizes, n_tri, split):
+TILE = 256
+
+
+def packed_tiles(M):
+    nt = (M + TILE - 1) // TILE
+    return nt * (nt + 1) // 2
+
+
+def band_cuts(M, n_chunks):
+    """Tile-row boundaries giving bands of roughly equal tile counts."""
+    import math
+    nt = (M + TILE - 1) // TILE
+    total = nt * (nt + 1) // 2
+    cuts = [0]
+    for k in range(1, n_chunks):
+        t = int(math.sqrt(2.0 * k * total / n_chunks))
+        if t > cuts[-1]:
+            cuts.append(min(t, nt))
+    if cuts[-1] != nt:
+        cuts.append(nt)
+    return [min(t * TILE, M) for t in cuts]
+
+
+def launches_per_step(which_sizes, n_tri, split, packed=False):
     """Kernels of libwlcov launched by one step (memsets not counted)."""
     tables = 11          # chi_max, los, growth_norm, amplitude, sigma, halo, profiles, edges, norms, kernels, sigw2
     counts = 3 if n_tri > 0 else 2
     spectra = 5 if n_tri > 0 else 3
     assemble = 7         # split: rows_t, split(T), tc(T), rows_prep, rows_split, tc(1h+SSC), gather
-    snr = 0              # FP64: rows_t, gemm(T), rows_a, gemm(1h), gather, rows_s, gemm(SSC)
+    snr = 0
     for ms in which_sizes:
         nb = (ms + 63) // 64
         snr += 2 + 4 * nb  # pack, prefix; per panel: diagonal block, panel solve, slice, tensor-core update
     return tables + counts + spectra + assemble + snr
+
+
+def timed(stream, fn, steps, h, world):
+    import torch
+    torch.cuda.synchronize()
+    h.profile(True)
+    h.stage_times()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = None
+    for _ in range(steps):
+        out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    stages = h.stage_times()
+    h.profile(False)
+    return e0.elapsed_time(e1), stages, out
+
+
+def contraction_roofline(stages, elements, K, prec, N, long_kernel):
+    """Roofline of the 1-halo (chi, M) contraction, the kernel the metric is built on."""
+    syrk_ms, syrk_calls = stages["syrk_1h"]
+    avg_ms = syrk_ms / max(syrk_calls, 1)
+    flops = 2.0 * elements * K
+    achieved = flops / (avg_ms / 1e3) / 1e12
+    if prec == N.COV_FP64:
+        return {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s", "frac": achieved / 1.25,
+                "traffic": None, "kernel": "k_gemm_lower (FP64 1-halo contraction)", "launch_ms": avg_ms,
+                "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak available)"}
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    key = "bf16_tflops_sustained" if long_kernel else "bf16_tflops"
+    peak = peaks[key]
+    issued = 3.0 * flops / (avg_ms / 1e3) / 1e12
+    return {"bound": "tensor", "achieved": issued, "peak": peak, "unit": "TFLOP/s", "frac": issued / peak,
+            "traffic": None, "kernel": "k_syrk_tc256 (tcgen05 split-BF16 1-halo + SSC contraction)",
+            "launch_ms": avg_ms, "algorithmic_tflops": achieved,
+            "peak_source": f"MEASURED_PEAKS.json {key}, of measured"}
+
+
+def dense_run(h, wl, cosmo, prec, stream, steps, warmup, world, fp64_form):
+    """The whole path on a workload whose dense M x M square fits: tables,
+    counts, spectra, the dense covariance and the three cumulative S/N
+    (P, B, joint) by FP64 Cholesky."""
+    import numpy as np
+    import torch
+    from paper_1812_07437_gb300 import native as N
+    M = h.M
+    dev = torch.device("cuda", torch.cuda.current_device())
+    D = torch.zeros(M, dtype=torch.float64, device=dev)
+    C = torch.zeros(M, M, dtype=torch.float64, device=dev)
+    which = (N.COV_WHICH_P, N.COV_WHICH_B, N.COV_WHICH_JOINT)
+
+    def step(p=prec):
+        h.update(cosmo, stream)
+        h.spectra(D, stream)
+        h.assemble(C, N.COV_TERMS_ALL, p, stream)
+        return [h.snr(C, D, w, stream) for w in which]
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            step()
+        ms, stages, snr = timed(stream, step, steps, h, world)
+        out = {"ms_per_step": ms / steps, "stages": stages, "snr": snr, "D": D, "C": C}
+        if fp64_form and prec != N.COV_FP64:
+            step(N.COV_FP64)
+            ms64, st64, snr64 = timed(stream, lambda: step(N.COV_FP64), 2, h, 1)
+            out["fp64"] = {"ms_per_step": ms64 / 2, "stages": st64, "snr": snr64}
+            rel = max(float(np.nanmax(np.abs(a / b - 1))) for a, b in zip(snr, snr64))
+            out["snr_rel_err_vs_fp64_form"] = rel
+    return out
 
 
 def run_ours(args):
@@ -205,154 +311,207 @@ def run_ours(args):
         prec_name = args.precision
     prec = N.COV_SPLIT_BF16 if prec_name == "split_bf16" else N.COV_FP64
 
+    def rank_cosmo(wl):
+        cosmo = dict(wl["cosmology"])
+        if rank > 0:  # Fisher-style +-1% steps, one cosmology per rank
+            keys = ["Om", "sigma8", "h", "ns", "Ob", "w0"]
+            k = keys[(rank - 1) % len(keys)]
+            cosmo[k] *= 1.0 + 0.01 * (1 if rank % 2 else -1)
+        return cosmo
+
     wl = workloads.get(args.workload)
-    cosmo = dict(wl["cosmology"])
-    if rank > 0:  # Fisher-style +-1% steps, one cosmology per rank
-        keys = ["Om", "sigma8", "h", "ns", "Ob", "w0"]
-        k = keys[(rank - 1) % len(keys)]
-        cosmo[k] *= 1.0 + 0.01 * (1 if rank % 2 else -1)
-        wl = workloads.get(args.workload, cosmology=cosmo)
+    cosmo = rank_cosmo(wl)
+    wl = workloads.get(args.workload, cosmology=cosmo)
     h = Handle(wl, device=local)
     M = h.M
     elements = M * (M + 1) // 2
-    D = torch.zeros(M, dtype=torch.float64, device=dev)
-    C = torch.zeros(M, M, dtype=torch.float64, device=dev)
+    K = wl["bins"]["n_chi"] * wl["bins"]["n_mass"]
+    Kc = K + (wl["bins"]["n_chi"] if prec != N.COV_FP64 else 0)  # SSC rows ride in the split contraction
     stream = torch.cuda.Stream(device=dev)
-    which = (N.COV_WHICH_P, N.COV_WHICH_B, N.COV_WHICH_JOINT)
+    packed = args.layout == "tiles" or (args.layout == "auto" and M * M * 8 > 64e9)
+    gpu_index = int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[0]) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local
+    clk = ClockSampler(gpu_index)
 
-    def step():
-        h.update(cosmo, stream)
-        h.spectra(D, stream)
-        h.assemble(C, N.COV_TERMS_ALL, prec, stream)
-        return [h.snr(C, D, w, stream) for w in which]
+    extra = {}
+    if packed:
+        # a1-a15: tables, counts, spectra and the whole lower-packed covariance
+        # (256 x 256 tiles, resident in HBM), one band call covering every row
+        D = torch.zeros(M, dtype=torch.float64, device=dev)
+        Ct = torch.empty(packed_tiles(M) * TILE * TILE, dtype=torch.float64, device=dev)
 
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            snr = step()
-        torch.cuda.synchronize()
-        h.profile(True)
-        h.stage_times()
-        gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] or 0) \
-            if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local
-        clk = ClockSampler(gpu_index)
-        clk.start()
-        time.sleep(0.4)
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            snr = step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-        ms_total = e0.elapsed_time(e1)
-        clocks = clk.stop()
-        stages = h.stage_times()
-        h.profile(False)
+        def step():
+            h.update(cosmo, stream)
+            h.spectra(D, stream)
+            h.assemble_band(0, M, Ct, N.COV_LAYOUT_TILES, N.COV_TERMS_ALL, prec, stream)
 
-        # end-to-end through the public API with host buffers: parameters in,
-        # covariance + data vector + S/N out to pinned host memory every step
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                step()
+            clk.start()
+            time.sleep(0.4)
+            ms_total, stages, _ = timed(stream, step, args.steps, h, world)
+            clocks = clk.stop()
+            # e2e through the public API: the covariance streamed to the host in
+            # bands of about equal size, band k+1 computed while band k is copied
+            cuts = band_cuts(M, 48)
+            bands = list(zip(cuts[:-1], cuts[1:]))
+            nmax = max(packed_tiles(b) - packed_tiles(a) for a, b in bands) * TILE * TILE
+            dbuf = [torch.empty(nmax, dtype=torch.float64, device=dev) for _ in range(2)]
+            hbuf = [torch.empty(nmax, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+            Dh = torch.empty(M, dtype=torch.float64, pin_memory=True)
+            copy = torch.cuda.Stream(device=dev)
+            done = [torch.cuda.Event() for _ in range(2)]
+            ready = [torch.cuda.Event() for _ in range(2)]
+            d2h = 0
+
+            def e2e_step():
+                nonlocal d2h
+                d2h = M * 8
+                h.update(cosmo, stream)
+                h.spectra(D, stream)
+                Dh.copy_(D, non_blocking=True)
+                for k, (a, b) in enumerate(bands):
+                    n = (packed_tiles(b) - packed_tiles(a)) * TILE * TILE
+                    s = k % 2
+                    stream.wait_event(done[s])
+                    h.assemble_band(a, b - a, dbuf[s][:n], N.COV_LAYOUT_TILES, N.COV_TERMS_ALL, prec, stream)
+                    ready[s].record(stream)
+                    copy.wait_event(ready[s])
+                    with torch.cuda.stream(copy):
+                        hbuf[s][:n].copy_(dbuf[s][:n], non_blocking=True)
+                    done[s].record(copy)
+                    d2h += n * 8
+                copy.synchronize()
+                stream.synchronize()
+
+            e2e_step()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                e2e_step()
+            e2e_s = (time.perf_counter() - t0) / args.steps
+            del dbuf, hbuf
+            # the FP64 GPU form on a sample of bands (the full FP64 contraction
+            # at this size runs for many minutes): same rows, both precisions
+            if not args.no_fp64_form and prec != N.COV_FP64:
+                row0 = (M // 2) // TILE * TILE
+                sample = [(row0, row0 + TILE), (M // TILE * TILE - TILE, M // TILE * TILE)]
+                n = max(packed_tiles(b) - packed_tiles(a) for a, b in sample) * TILE * TILE
+                buf = torch.empty(n, dtype=torch.float64, device=dev)
+                res = {}
+                for p, nm in ((prec, "split"), (N.COV_FP64, "fp64")):
+                    def band_step(p=p):
+                        for a, b in sample:
+                            h.assemble_band(a, b - a, buf, N.COV_LAYOUT_TILES, N.COV_TERMS_ALL, p, stream)
+                    band_step()  # builds this precision's operands
+                    ms_b, st_b, _ = timed(stream, band_step, 1, h, 1)
+                    res[nm] = ms_b
+                el = sum((b - a) * (a + b + 1) // 2 for a, b in sample)
+                extra["fp64_form"] = {
+                    "value": el / (res["fp64"] / 1e3), "unit": UNIT, "ms": res["fp64"],
+                    "split_value_same_bands": el / (res["split"] / 1e3), "split_ms": res["split"],
+                    "sample": f"rows {sample[0][0]}-{sample[0][1]} and {sample[1][0]}-{sample[1][1]} "
+                              f"({el} lower elements, every term) in each precision"}
+                del buf
+        ms_step = ms_total / args.steps
+        e2e = {"value": world * elements / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 56,
+               "d2h_bytes_per_step": d2h,
+               "how": f"cov_update + cov_spectra, then cov_assemble_band over {len(bands)} bands of about equal "
+                      "size into two device buffers, each band copied to pinned host memory on a second stream "
+                      "while the next one is assembled"}
+        snr_sizes = []
+        cfg = {"layout": "lower-packed 256x256 tiles, resident (%.1f GB)" % (Ct.numel() * 8 / 1e9)}
+    else:
+        with torch.cuda.stream(stream):
+            clk.start()
+            time.sleep(0.4)
+            r = dense_run(h, wl, cosmo, prec, stream, args.steps, args.warmup, world, not args.no_fp64_form)
+            clocks = clk.stop()
+        ms_step, stages = r["ms_per_step"], r["stages"]
+        D, C = r["D"], r["C"]
+        which = (N.COV_WHICH_P, N.COV_WHICH_B, N.COV_WHICH_JOINT)
         Ch = torch.empty(M, M, dtype=torch.float64, pin_memory=True)
         Dh = torch.empty(M, dtype=torch.float64, pin_memory=True)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            step()
-            Ch.copy_(C, non_blocking=True)
-            Dh.copy_(D, non_blocking=True)
-            stream.synchronize()
-        e2e_s = (time.perf_counter() - t0) / args.steps
-
-        # the plain FP64 form of the same step (the comparison point of the
-        # reduced-precision form): a short timed run after the main one
-        fp64 = None
-        if prec != N.COV_FP64 and not args.no_fp64_form:
-            def step64():
+        with torch.cuda.stream(stream):
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
                 h.update(cosmo, stream)
                 h.spectra(D, stream)
-                h.assemble(C, N.COV_TERMS_ALL, N.COV_FP64, stream)
-                return [h.snr(C, D, w, stream) for w in which]
-            step64()
-            torch.cuda.synchronize()
-            h.profile(True)
-            h.stage_times()
-            f0 = torch.cuda.Event(enable_timing=True)
-            f1 = torch.cuda.Event(enable_timing=True)
-            f0.record(stream)
-            for _ in range(2):
-                step64()
-            f1.record(stream)
-            torch.cuda.synchronize()
-            st64 = h.stage_times()
-            h.profile(False)
-            ms64 = f0.elapsed_time(f1) / 2
-            s1h = st64["syrk_1h"][0] / max(st64["syrk_1h"][1], 1)
-            fp64 = {"ms_per_step": ms64, "value": elements / (ms64 / 1e3), "unit": UNIT,
-                    "syrk_1h_ms": s1h, "syrk_1h_tflops": 2.0 * elements * wl["bins"]["n_chi"]
-                    * wl["bins"]["n_mass"] / (s1h / 1e3) / 1e12}
+                h.assemble(C, N.COV_TERMS_ALL, prec, stream)
+                [h.snr(C, D, w, stream) for w in which]
+                Ch.copy_(C, non_blocking=True)
+                Dh.copy_(D, non_blocking=True)
+                stream.synchronize()
+            e2e_s = (time.perf_counter() - t0) / args.steps
+        e2e = {"value": world * elements / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 56,
+               "d2h_bytes_per_step": M * M * 8 + M * 8 + 3 * wl["bins"]["n_ell"] * 8}
+        if "fp64" in r:
+            extra["fp64_form"] = {"ms_per_step": r["fp64"]["ms_per_step"],
+                                  "value": elements / (r["fp64"]["ms_per_step"] / 1e3), "unit": UNIT}
+            extra["snr_rel_err_vs_fp64_form"] = r["snr_rel_err_vs_fp64_form"]
+        extra["snr_joint_max"] = float(np.nanmax(r["snr"][2]))
+        snr_sizes = [h.n_P, h.n_B, M]
+        cfg = {"layout": "dense M x M"}
 
-    t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+    t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
     if world > 1:
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_step = float(t.item()) / args.steps
+    ms_step = float(t.item())
     value = world * elements / (ms_step / 1e3)
-
-    # roofline of the 1-halo (chi, M) contraction, the kernel the metric is built on
-    syrk_ms, syrk_calls = stages["syrk_1h"]
-    K = wl["bins"]["n_chi"] * wl["bins"]["n_mass"]
-    if prec != N.COV_FP64:
-        K += wl["bins"]["n_chi"]  # the super-sample rows ride along in the split contraction
-    flops = 2.0 * elements * K
-    avg_ms = syrk_ms / max(syrk_calls, 1)
-    achieved = flops / (avg_ms / 1e3) / 1e12
-    if prec == N.COV_FP64:
-        roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
-                "frac": achieved / 1.25, "traffic": None, "kernel": "k_gemm_lower (FP64 1-halo contraction)",
-                "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak available)"}
-    else:
-        import json as _j
-        peaks = _j.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        peak = peaks["bf16_tflops"]
-        issued = 3.0 * flops
-        roof = {"bound": "tensor", "achieved": issued / (avg_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "frac": issued / (avg_ms / 1e3) / 1e12 / peak, "traffic": None,
-                "kernel": "k_syrk_tc (tcgen05 split-BF16 1-halo contraction)",
-                "algorithmic_tflops": achieved, "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}
-
-    sizes = [h.n_P, h.n_B, M]
-    # the S/N factorisations hold most of the step: report their tensor-core
-    # trailing update too (FP64-equivalent work M^3/3 per factorisation)
-    chol_ms = stages["snr_cholesky"][0] / max(args.steps, 1)
-    chol_flops = sum(m ** 3 / 3.0 for m in sizes)
-    roof["cholesky"] = {"stage_ms_per_step": chol_ms, "fp64_equivalent_tflops": chol_flops / (chol_ms / 1e3) / 1e12,
-                        "note": "diagonal blocks and panel solves in FP64, trailing updates on tcgen05 by exact slicing"}
+    roof = contraction_roofline(stages, elements, Kc, prec, N, long_kernel=packed)
+    if snr_sizes:
+        chol_ms = stages["snr_cholesky"][0] / max(args.steps, 1)
+        roof["cholesky"] = {"stage_ms_per_step": chol_ms,
+                            "fp64_equivalent_tflops": sum(m ** 3 / 3.0 for m in snr_sizes) / (chol_ms / 1e3) / 1e12,
+                            "note": "diagonal blocks and panel solves in FP64, trailing updates on tcgen05 by "
+                                    "exact slicing"}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64" if prec == N.COV_FP64 else "bf16x3+f64",
            "data": "synthetic",
-           "config": {"workload": args.workload, "M": M, "n_P": h.n_P, "n_B": h.n_B, "K": K,
-                      "n_tomo": wl["nz"]["n_tomo"], "n_ell": wl["bins"]["n_ell"], "terms": "all",
-                      "precision": prec_name, "elements_per_step": elements,
-                      "l2": "inputs larger than L2 (factor rows %.0f MB, covariance %.0f MB)" % (
-                          M * K * 8 / 1e6, M * M * 8 / 1e6),
-                      "parallelism": f"replicas x{world}"},
+           "config": dict({"workload": args.workload, "M": M, "n_P": h.n_P, "n_B": h.n_B, "K": K,
+                           "n_tomo": wl["nz"]["n_tomo"], "n_ell": wl["bins"]["n_ell"], "terms": "all",
+                           "precision": prec_name, "elements_per_step": elements,
+                           "step": "update+spectra+assemble" + ("" if packed else "+snr(P,B,joint)"),
+                           "l2": "inputs larger than L2 (factor rows %.0f MB, covariance %.0f MB)" % (
+                               M * Kc * (4 if prec != N.COV_FP64 else 8) / 1e6, elements * 8 / 1e6),
+                           "parallelism": f"replicas x{world}"}, **cfg),
            "roofline": roof,
-           "e2e": {"value": world * elements / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 56,
-                   "d2h_bytes_per_step": M * M * 8 + M * 8 + 3 * wl["bins"]["n_ell"] * 8},
-           "gpu_launches": args.steps * launches_per_step(sizes, h.n_tri, prec != N.COV_FP64),
-           "fp64_form": fp64,
+           "e2e": e2e,
+           "gpu_launches": args.steps * launches_per_step(snr_sizes, h.n_tri, prec != N.COV_FP64, packed),
            "clocks": clocks,
-           "stages_ms_per_step": {k: v[0] / max(args.steps, 1) for k, v in stages.items()},
-           "snr_joint_max": float(np.nanmax(snr[2]))}
+           "stages_ms_per_step": {k: v[0] / max(args.steps, 1) for k, v in stages.items() if v[1]}}
+    out.update(extra)
+    h.close()
+    if packed:
+        del Ct
+    torch.cuda.empty_cache()
+    if not args.no_snr_run and packed and rank == 0:
+        # the S/N stage (a dense FP64 Cholesky per vector) on the 5-bin workload,
+        # timed in the same run with its error against the FP64 form
+        wl2 = workloads.get(args.snr_workload)
+        h2 = Handle(wl2, device=local)
+        s2 = torch.cuda.Stream(device=dev)
+        with torch.cuda.stream(s2):
+            r2 = dense_run(h2, wl2, dict(wl2["cosmology"]), prec, s2, 3, 3, 1, True)
+        st = r2["stages"]
+        M2 = h2.M
+        chol_ms = st["snr_cholesky"][0] / 3
+        out["snr_stage"] = {
+            "workload": args.snr_workload, "M": M2, "ms_per_full_step": r2["ms_per_step"],
+            "full_step_elements_per_s": M2 * (M2 + 1) // 2 / (r2["ms_per_step"] / 1e3),
+            "snr_ms_per_step": sum(st[k][0] for k in ("snr_pack", "snr_cholesky", "snr_prefix")) / 3,
+            "cholesky_ms_per_step": chol_ms,
+            "cholesky_fp64_equivalent_tflops": sum(m ** 3 / 3.0 for m in (h2.n_P, h2.n_B, M2)) / (chol_ms / 1e3) / 1e12,
+            "snr_rel_err_vs_fp64_form": r2.get("snr_rel_err_vs_fp64_form"),
+            "snr_joint_max": float(np.nanmax(r2["snr"][2]))}
+        h2.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(out), flush=True)
-    h.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 

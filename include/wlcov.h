@@ -125,6 +125,30 @@ int cov_spectra(cov_handle* h, double* d_D, void* stream);
  * preceding cov_spectra on the same handle. */
 int cov_assemble(cov_handle* h, double* d_C, int64_t ldc, unsigned terms, int precision, void* stream);
 
+/* Output layouts of cov_assemble_band. */
+#define COV_LAYOUT_ROWS 0  /* dense rows: element (r, c) at d_C[(r - row0) * ldc + c]                */
+#define COV_LAYOUT_TILES 1 /* lower-packed 256 x 256 tiles: tile (ti, tj), tj <= ti, row-major, at  */
+                           /* d_C + (ti (ti + 1) / 2 + tj - t0 (t0 + 1) / 2) * 65536, t0 = row0 / 256 */
+
+/* Streaming assembly of one band of rows (Eqs. CovPPG, CovPPNG, Ins5P, Ins6P,
+ * CovBB, Covpb, WLSSCflatskyLimber summed as in cov_assemble), for
+ * covariances too large to hold as a dense square: the 10-bin, 20-ell-bin
+ * data vector has M = 181350, 263 GB dense, 132 GB as lower tiles.
+ * Writes the lower part (columns 0 .. r) of rows r in [row0, row0 + nrows)
+ * into d_C (device, caller-owned) in the given layout:
+ *   COV_LAYOUT_ROWS : ldc >= row0 + nrows, nrows * ldc doubles;
+ *   COV_LAYOUT_TILES: ldc ignored; the band's tiles, 65536 doubles each.
+ *   With row0 = 0 and nrows = M this is the whole lower-packed matrix.
+ * Tile entries above the diagonal and below row M are not written.
+ * row0 must be a multiple of 256 and row0 + nrows a multiple of 256 or M.
+ * precision: COV_SPLIT_BF16 or COV_FP64 as in cov_assemble; COV_TERM_SSC
+ * requires COV_TERM_1H.  The operands (factor rows, trispectrum table) are
+ * built by the first band after cov_spectra (or a change of terms or
+ * precision) and reused by the following bands; a band computes exactly what
+ * cov_assemble computes for its rows.  Requires a preceding cov_spectra. */
+int cov_assemble_band(cov_handle* h, int64_t row0, int64_t nrows, double* d_C, int64_t ldc, int layout,
+                      unsigned terms, int precision, void* stream);
+
 /* Cumulative signal-to-noise (Eqs. SNprim, eq:SN): h_snr[c] (host, n_ell
  * values) = sqrt(D^T C^-1 D) over the selected entries whose largest ell bin
  * is <= c, via a Jacobi-scaled FP64 Cholesky of a workspace copy (d_C is not

@@ -288,6 +288,7 @@ extern "C" int cov_update(cov_handle* h, const cov_cosmology* cosmo, void* strea
   if (validate(cosmo, &h->nz, &h->bins) != COV_OK) return wl_fail(h, COV_ERR_INVALID, "invalid cosmology");
   h->cosmo = *cosmo;
   h->spectra_ready = false;
+  h->ops_terms = -1;
   cudaStream_t s = (cudaStream_t)stream;
   int tk = wl_stage_begin(h, ST_TABLES, s);
   int rc = wl_tables(h, s);
@@ -322,6 +323,7 @@ extern "C" int cov_counts(cov_handle* h, int64_t* N_ell, int64_t* N_tri, void* s
 
 extern "C" int cov_spectra(cov_handle* h, double* d_D, void* stream) {
   if (!h) return COV_ERR_INVALID;
+  h->ops_terms = -1;
   int tk = wl_stage_begin(h, ST_SPECTRA, (cudaStream_t)stream);
   int rc = wl_spectra(h, d_D, (cudaStream_t)stream);
   wl_stage_end(h, tk, (cudaStream_t)stream);
@@ -332,7 +334,27 @@ extern "C" int cov_assemble(cov_handle* h, double* d_C, int64_t ldc, unsigned te
   if (!h || !d_C || ldc < h->M || (terms & ~COV_TERMS_ALL)) return wl_fail(h, COV_ERR_INVALID, "bad cov_assemble args");
   if (precision != COV_FP64 && precision != COV_SPLIT_BF16) return wl_fail(h, COV_ERR_INVALID, "bad precision");
   if (!h->spectra_ready) return wl_fail(h, COV_ERR_INVALID, "cov_spectra must run before cov_assemble");
+  h->ops_terms = -1;  // the full assembly rebuilds (and may resize) the operands
   return wl_assemble(h, d_C, ldc, terms, precision, (cudaStream_t)stream);
+}
+
+extern "C" int cov_assemble_band(cov_handle* h, int64_t row0, int64_t nrows, double* d_C, int64_t ldc,
+                                 int layout, unsigned terms, int precision, void* stream) {
+  if (!h) return COV_ERR_INVALID;
+  if (!d_C || (terms & ~COV_TERMS_ALL) || (precision != COV_FP64 && precision != COV_SPLIT_BF16) ||
+      (layout != COV_LAYOUT_ROWS && layout != COV_LAYOUT_TILES))
+    return wl_fail(h, COV_ERR_INVALID, "cov_assemble_band: bad buffer, terms, precision or layout");
+  if ((terms & COV_TERM_SSC) && !(terms & COV_TERM_1H))
+    return wl_fail(h, COV_ERR_INVALID, "cov_assemble_band: COV_TERM_SSC needs COV_TERM_1H");
+  if (row0 < 0 || nrows <= 0 || row0 % 256 != 0 || row0 + nrows > h->M ||
+      (row0 + nrows != h->M && (row0 + nrows) % 256 != 0))
+    return wl_fail(h, COV_ERR_INVALID,
+                   "cov_assemble_band: the band must start on a multiple of 256 and end on one or at M");
+  if (layout == COV_LAYOUT_ROWS && ldc < row0 + nrows)
+    return wl_fail(h, COV_ERR_INVALID, "cov_assemble_band: ldc below row0 + nrows");
+  if (!h->spectra_ready) return wl_fail(h, COV_ERR_INVALID, "cov_spectra must run before cov_assemble_band");
+  OutMap out = layout == COV_LAYOUT_TILES ? out_tiles(d_C, row0) : out_rows(d_C, ldc, row0);
+  return wl_assemble_band(h, row0, nrows, out, terms, precision, (cudaStream_t)stream);
 }
 
 extern "C" int cov_snr(cov_handle* h, const double* d_C, int64_t ldc, const double* d_D, int which, double* h_snr,

@@ -106,10 +106,10 @@ __device__ __forceinline__ void tri_tile(int64_t id, int64_t* ti, int64_t* tj) {
   *tj = id - i * (i + 1) / 2;
 }
 
-__global__ void k_gather(GatherArgs g, int64_t M, double* C, int64_t ldc, int accumulate) {
+__global__ void k_gather(GatherArgs g, int64_t M, OutMap out, int accumulate, int64_t tile_off) {
   __shared__ int32_t rdA[32 * 8], rdB[32 * 8];
   int64_t ti, tj;
-  tri_tile(blockIdx.x, &ti, &tj);
+  tri_tile((int64_t)blockIdx.x + tile_off, &ti, &tj);
   int64_t a0 = ti * 32, b0 = tj * 32;
   int tid = threadIdx.y * 32 + threadIdx.x;
   for (int e = tid; e < 256; e += 256) {
@@ -123,7 +123,8 @@ __global__ void k_gather(GatherArgs g, int64_t M, double* C, int64_t ldc, int ac
     int64_t a = a0 + rr;
     if (a >= M || b >= M || b > a) continue;
     double v = gather_element(g, rdA + rr * 8, rdB + threadIdx.x * 8);
-    C[a * ldc + b] = accumulate ? C[a * ldc + b] + v : v;
+    double* p = out.at(a, b);
+    *p = accumulate ? *p + v : v;
   }
 }
 
@@ -132,14 +133,14 @@ __global__ void k_gather(GatherArgs g, int64_t M, double* C, int64_t ldc, int ac
 #define GT 64
 #define GK 16
 __global__ void __launch_bounds__(256) k_gemm_lower(const double* __restrict__ A, int64_t lda,
-                                                    const double* __restrict__ B, int64_t ldb, double* C,
-                                                    int64_t ldc, int64_t n, int64_t k, double alpha, double beta,
-                                                    int lower_only, int64_t ntiles_1d) {
+                                                    const double* __restrict__ B, int64_t ldb, OutMap out,
+                                                    int64_t n, int64_t k, double alpha, double beta,
+                                                    int lower_only, int64_t ntiles_1d, int64_t tile_off) {
   __shared__ double As[GK][GT + 1];
   __shared__ double Bs[GK][GT + 1];
   int64_t ti, tj;
   if (lower_only) {
-    tri_tile(blockIdx.x, &ti, &tj);
+    tri_tile((int64_t)blockIdx.x + tile_off, &ti, &tj);
   } else {
     ti = blockIdx.x / ntiles_1d;
     tj = blockIdx.x % ntiles_1d;
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(256) k_gemm_lower(const double* __restrict__ A
     for (int c = 0; c < 4; ++c) {
       int64_t gi = i0 + ty + 16 * r, gj = j0 + tx + 16 * c;
       if (gi < n && gj < n && (!lower_only || gj <= gi)) {
-        double* p = C + gi * ldc + gj;
+        double* p = out.at(gi, gj);
         *p = alpha * acc[r][c] + (beta == 0.0 ? 0.0 : beta * *p);
       }
     }
@@ -193,7 +194,19 @@ int wl_gemm_lower_fp64(cov_handle* h, const double* A, int64_t lda, const double
   if (n <= 0) return COV_OK;
   int64_t nt1 = (n + GT - 1) / GT;
   int64_t nblk = lower_only ? nt1 * (nt1 + 1) / 2 : nt1 * nt1;
-  k_gemm_lower<<<(unsigned)nblk, 256, 0, s>>>(A, lda, B, ldb, C, ldc, n, k, alpha, beta, lower_only ? 1 : 0, nt1);
+  k_gemm_lower<<<(unsigned)nblk, 256, 0, s>>>(A, lda, B, ldb, out_rows(C, ldc), n, k, alpha, beta,
+                                              lower_only ? 1 : 0, nt1, 0);
+  WL_LAUNCH(h, "k_gemm_lower");
+  return COV_OK;
+}
+
+// lower part of rows [out.row0, row1) of A B^T (out.row0 a multiple of 64)
+static int gemm_lower_band(cov_handle* h, const double* A, int64_t lda, int64_t row1, int64_t k, double beta,
+                           OutMap out, cudaStream_t s) {
+  int64_t t0 = out.row0 / GT, t1 = (row1 + GT - 1) / GT;
+  int64_t off = t0 * (t0 + 1) / 2;
+  k_gemm_lower<<<(unsigned)(t1 * (t1 + 1) / 2 - off), 256, 0, s>>>(A, lda, A, lda, out, row1, k, 1.0, beta, 1, t1,
+                                                                  off);
   WL_LAUNCH(h, "k_gemm_lower");
   return COV_OK;
 }
@@ -234,7 +247,8 @@ int wl_assemble(cov_handle* h, double* C, int64_t ldc, unsigned terms, int preci
       if ((rc = ensure(h, (void**)&h->Tlo, sb, "BF16 lo trispectrum rows"))) return rc;
       if ((rc = ensure(h, (void**)&h->Tscale, sizeof(double) * h->ntrow, "trispectrum row scales"))) return rc;
       if ((rc = wl_split_rows(h, h->Trows, h->ntrow, (int)K, h->Thi, h->Tlo, h->Tscale, s))) return rc;
-      if ((rc = wl_syrk_tc_rows(h, h->Thi, h->Tlo, h->Tscale, h->ntrow, wl_kpad((int)K), h->Tmat, h->ntrow, s)))
+      if ((rc = wl_syrk_tc_rows(h, h->Thi, h->Tlo, h->Tscale, h->ntrow, wl_kpad((int)K),
+                                out_rows(h->Tmat, h->ntrow), s)))
         return rc;
     }
     wl_stage_end(h, tk, s);
@@ -268,7 +282,7 @@ int wl_assemble(cov_handle* h, double* C, int64_t ldc, unsigned terms, int preci
       if ((rc = wl_rows_split(h, nssc, s))) return rc;
       wl_stage_end(h, tk, s);
       tk = wl_stage_begin(h, ST_SYRK_1H, s);
-      if ((rc = wl_syrk_tc(h, nssc, C, ldc, s))) return rc;
+      if ((rc = wl_syrk_tc(h, nssc, out_rows(C, ldc), s))) return rc;
       wl_stage_end(h, tk, s);
     }
   }
@@ -276,8 +290,8 @@ int wl_assemble(cov_handle* h, double* C, int64_t ldc, unsigned terms, int preci
   GatherArgs g{h->nt, h->nleg, terms, h->omega, h->rowdesc_d, h->Ps, h->B1hp, h->Tmat, h->ntrow, h->Nmodes, h->Ntri};
   int64_t nt32 = (M + 31) / 32;
   int tg = wl_stage_begin(h, ST_GATHER, s);
-  k_gather<<<(unsigned)(nt32 * (nt32 + 1) / 2), dim3(32, 8), 0, s>>>(g, M, C, ldc,
-                                                                  (terms & COV_TERM_1H) ? 1 : 0);
+  k_gather<<<(unsigned)(nt32 * (nt32 + 1) / 2), dim3(32, 8), 0, s>>>(g, M, out_rows(C, ldc),
+                                                                  (terms & COV_TERM_1H) ? 1 : 0, 0);
   WL_LAUNCH(h, "k_gather");
   wl_stage_end(h, tg, s);
   // 3. super-sample term, rank N_chi (already inside the split contraction)
@@ -289,6 +303,105 @@ int wl_assemble(cov_handle* h, double* C, int64_t ldc, unsigned terms, int preci
     tk = wl_stage_begin(h, ST_SYRK_SSC, s);
     if ((rc = wl_gemm_lower_fp64(h, h->Srows, h->nchi, h->Srows, h->nchi, C, ldc, M, h->nchi, 1.0, 1.0, true, s)))
       return rc;
+    wl_stage_end(h, tk, s);
+  }
+  return COV_OK;
+}
+
+// ---- band assembly -------------------------------------------------------------
+// The operands (factor rows, trispectrum table) are built once per spectra and
+// precision; each band then runs the contraction and the gather over its tile
+// rows only.
+static int prepare_operands(cov_handle* h, unsigned terms, int precision, cudaStream_t s) {
+  int rc;
+  const int64_t M = h->M, K = h->K;
+  if (terms & COV_TERM_BBPT) {
+    if ((rc = ensure(h, (void**)&h->Trows, sizeof(double) * h->ntrow * K, "trispectrum rows"))) return rc;
+    if ((rc = ensure(h, (void**)&h->Tmat, sizeof(double) * h->ntrow * h->ntrow, "trispectrum table"))) return rc;
+    int tk = wl_stage_begin(h, ST_ROWS_T, s);
+    if ((rc = wl_rows_t(h, s))) return rc;
+    wl_stage_end(h, tk, s);
+    tk = wl_stage_begin(h, ST_SYRK_T, s);
+    if (precision == COV_FP64) {
+      if ((rc = wl_gemm_lower_fp64(h, h->Trows, K, h->Trows, K, h->Tmat, h->ntrow, h->ntrow, K, 1.0, 0.0, true, s)))
+        return rc;
+    } else {
+      size_t sb = 0;
+      wl_split_bytes(h->ntrow, (int)K, &sb);
+      if ((rc = ensure(h, (void**)&h->Thi, sb, "BF16 hi trispectrum rows"))) return rc;
+      if ((rc = ensure(h, (void**)&h->Tlo, sb, "BF16 lo trispectrum rows"))) return rc;
+      if ((rc = ensure(h, (void**)&h->Tscale, sizeof(double) * h->ntrow, "trispectrum row scales"))) return rc;
+      if ((rc = wl_split_rows(h, h->Trows, h->ntrow, (int)K, h->Thi, h->Tlo, h->Tscale, s))) return rc;
+      if ((rc = wl_syrk_tc_rows(h, h->Thi, h->Tlo, h->Tscale, h->ntrow, wl_kpad((int)K),
+                                out_rows(h->Tmat, h->ntrow), s)))
+        return rc;
+    }
+    wl_stage_end(h, tk, s);
+  }
+  if (precision == COV_FP64) {
+    if (terms & COV_TERM_1H) {
+      if ((rc = ensure(h, (void**)&h->A, sizeof(double) * M * K, "FP64 factor rows"))) return rc;
+      int tk = wl_stage_begin(h, ST_ROWS_A, s);
+      if ((rc = wl_rows_a(h, s))) return rc;
+      wl_stage_end(h, tk, s);
+    }
+    if (terms & COV_TERM_SSC) {
+      if ((rc = ensure(h, (void**)&h->Srows, sizeof(double) * M * h->nchi, "SSC rows"))) return rc;
+      int tk = wl_stage_begin(h, ST_ROWS_S, s);
+      if ((rc = wl_rows_s(h, s))) return rc;
+      wl_stage_end(h, tk, s);
+    }
+  } else if (terms & COV_TERM_1H) {
+    int nssc = (terms & COV_TERM_SSC) ? h->nchi : 0;
+    size_t sb = 0;
+    wl_split_bytes(M, (int)K + h->nchi, &sb);
+    if ((rc = ensure(h, (void**)&h->Ahi, sb, "BF16 hi rows"))) return rc;
+    if ((rc = ensure(h, (void**)&h->Alo, sb, "BF16 lo rows"))) return rc;
+    if ((rc = ensure(h, (void**)&h->Ascale, sizeof(double) * M, "row scales"))) return rc;
+    if ((rc = ensure(h, (void**)&h->tc_status, sizeof(int), "status word"))) return rc;
+    if ((rc = ensure(h, (void**)&h->G2, sizeof(double) * K, "row factor table"))) return rc;
+    if ((rc = ensure(h, (void**)&h->G3, sizeof(double) * K, "row factor table"))) return rc;
+    if ((rc = ensure(h, (void**)&h->C2, sizeof(double) * h->nchi, "row factor table"))) return rc;
+    if ((rc = ensure(h, (void**)&h->C3, sizeof(double) * h->nchi, "row factor table"))) return rc;
+    int tk = wl_stage_begin(h, ST_ROWS_A, s);
+    if ((rc = wl_rows_split(h, nssc, s))) return rc;
+    wl_stage_end(h, tk, s);
+  }
+  return COV_OK;
+}
+
+int wl_assemble_band(cov_handle* h, int64_t row0, int64_t nrows, OutMap out, unsigned terms, int precision,
+                     cudaStream_t s) {
+  int rc;
+  if (h->ops_terms != (int)terms || h->ops_precision != precision) {
+    if ((rc = prepare_operands(h, terms, precision, s))) return rc;
+    h->ops_terms = (int)terms;
+    h->ops_precision = precision;
+  }
+  const int64_t row1 = row0 + nrows;
+  // 1. the (chi, M) contraction is the first writer of the band
+  if (terms & COV_TERM_1H) {
+    int tk = wl_stage_begin(h, ST_SYRK_1H, s);
+    if (precision == COV_FP64) {
+      if ((rc = gemm_lower_band(h, h->A, h->K, row1, h->K, 0.0, out, s))) return rc;
+    } else {
+      if ((rc = wl_syrk_tc(h, (terms & COV_TERM_SSC) ? h->nchi : 0, out, s, row1))) return rc;
+    }
+    wl_stage_end(h, tk, s);
+  }
+  // 2. per-element product terms
+  GatherArgs g{h->nt, h->nleg, terms, h->omega, h->rowdesc_d, h->Ps, h->B1hp, h->Tmat, h->ntrow, h->Nmodes, h->Ntri};
+  int64_t t0 = row0 / 32, t1 = (row1 + 31) / 32;
+  int64_t off = t0 * (t0 + 1) / 2;
+  int tg = wl_stage_begin(h, ST_GATHER, s);
+  k_gather<<<(unsigned)(t1 * (t1 + 1) / 2 - off), dim3(32, 8), 0, s>>>(g, row1, out, (terms & COV_TERM_1H) ? 1 : 0,
+                                                                       off);
+  WL_LAUNCH(h, "k_gather");
+  wl_stage_end(h, tg, s);
+  // 3. super-sample term of the FP64 form (the split form carries it in the contraction)
+  if (precision == COV_FP64 && (terms & COV_TERM_SSC)) {
+    int tk = wl_stage_begin(h, ST_SYRK_SSC, s);
+    if ((rc = gemm_lower_band(h, h->Srows, h->nchi, row1, h->nchi, 1.0, out, s))) return rc;
     wl_stage_end(h, tk, s);
   }
   return COV_OK;

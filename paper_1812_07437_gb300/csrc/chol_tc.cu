@@ -261,18 +261,7 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
-static PFN_cuTensorMapEncodeTiled_v12000 cs_encode() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-  }
-  return fn;
-}
+static PFN_cuTensorMapEncodeTiled_v12000 cs_encode() { return wl_encode_tiled(); }
 
 static int cs_map(cov_handle* h, CUtensorMap* map, void* base, int64_t total_rows, int box_rows) {
   auto fn = cs_encode();
@@ -324,11 +313,12 @@ int wl_chol_update(cov_handle* h, double* Wk, int64_t ldw, int64_t r0, int64_t r
   int rc;
   if ((rc = cs_map(h, &mi, slices, CS_S * pad, CS_BI))) return rc;
   if ((rc = cs_map(h, &mj, slices, CS_S * pad, CS_BJ))) return rc;
-  static bool attr = false;
-  if (!attr) {
-    WL_CHECK(h, cudaFuncSetAttribute(k_chol_update, cudaFuncAttributeMaxDynamicSharedMemorySize, CS_SMEM));
-    attr = true;
-  }
+  static std::once_flag attr_once[WL_MAX_DEVICES];
+  static int attr_rc[WL_MAX_DEVICES];
+  if (wl_once_per_device(attr_once, attr_rc, [] {
+        return (int)cudaFuncSetAttribute(k_chol_update, cudaFuncAttributeMaxDynamicSharedMemorySize, CS_SMEM);
+      }) != 0)
+    return wl_fail(h, COV_ERR_CUDA, "cudaFuncSetAttribute(k_chol_update) failed");
   // only tile rows that reach the requested columns
   int ti0 = (int)(((int64_t)tj0 * CS_BJ) / CS_BI);
   dim3 grid((unsigned)(pad / CS_BI - ti0), (unsigned)ntj);

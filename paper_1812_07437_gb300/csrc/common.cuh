@@ -2,9 +2,12 @@
 // Device helpers are header-inline (no relocatable device code).
 #pragma once
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -48,6 +51,42 @@ struct StageEvent {
   int stage;
   cudaEvent_t a, b;
 };
+
+// Where a kernel stores element (r, c) of the lower triangle (c <= r).
+//  rows : C[(r - row0) * ldc + c]                     (dense row-major band)
+//  tiles: 256 x 256 lower tiles, tile (ti, tj) (tj <= ti) stored row-major
+//         at tile index ti (ti + 1) / 2 + tj - tile0, 65536 doubles apart
+// cuTensorMapEncodeTiled from the driver, looked up once per process
+// (thread-safe: the serving scheduler runs requests on several host threads).
+PFN_cuTensorMapEncodeTiled_v12000 wl_encode_tiled();
+// Run f once per CUDA device for the calling thread's current device.
+#define WL_MAX_DEVICES 64
+template <typename F>
+inline int wl_once_per_device(std::once_flag (&flags)[WL_MAX_DEVICES], int (&rc)[WL_MAX_DEVICES], F f) {
+  int d = 0;
+  cudaGetDevice(&d);
+  if (d < 0 || d >= WL_MAX_DEVICES) return COV_ERR_INVALID;
+  std::call_once(flags[d], [&] { rc[d] = f(); });
+  return rc[d];
+}
+
+struct OutMap {
+  double* C;
+  int64_t ldc, row0, tile0;
+  int tiled;
+  __device__ __forceinline__ double* at(int64_t r, int64_t c) const {
+    if (tiled) {
+      int64_t ti = r >> 8, tj = c >> 8;
+      return C + ((ti * (ti + 1) / 2 + tj - tile0) << 16) + ((r & 255) << 8) + (c & 255);
+    }
+    return C + (r - row0) * ldc + c;
+  }
+};
+static inline OutMap out_rows(double* C, int64_t ldc, int64_t row0 = 0) { return OutMap{C, ldc, row0, 0, 0}; }
+static inline OutMap out_tiles(double* C, int64_t row0) {
+  int64_t t0 = row0 >> 8;
+  return OutMap{C, 0, row0, t0 * (t0 + 1) / 2, 1};
+}
 
 struct cov_handle {
   int device = 0;
@@ -101,6 +140,7 @@ struct cov_handle {
   cudaEvent_t ev_cols = nullptr, ev_panel = nullptr;
   int* chol_status = nullptr;
   bool spectra_ready = false;
+  int ops_terms = -1, ops_precision = -1;  // operands prepared for the band assembly (-1: none)
   bool prof = false;
   std::vector<StageEvent> pending;
   std::vector<cudaEvent_t> pool;
@@ -133,12 +173,14 @@ int wl_tables(cov_handle* h, cudaStream_t s);   // tables.cu
 int wl_counts(cov_handle* h, cudaStream_t s);   // counts.cu
 int wl_spectra(cov_handle* h, double* d_D, cudaStream_t s);  // spectra.cu
 int wl_assemble(cov_handle* h, double* d_C, int64_t ldc, unsigned terms, int precision, cudaStream_t s);
+int wl_assemble_band(cov_handle* h, int64_t row0, int64_t nrows, OutMap out, unsigned terms, int precision,
+                     cudaStream_t s);
 int wl_snr(cov_handle* h, const double* d_C, int64_t ldc, const double* d_D, int which, double* h_snr,
            cudaStream_t s);  // chol.cu
 int wl_gemm_lower_fp64(cov_handle* h, const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
                        int64_t ldc, int64_t n, int64_t k, double alpha, double beta, bool lower_only,
                        cudaStream_t s);  // assemble.cu
-int wl_syrk_tc(cov_handle* h, int nssc, double* d_C, int64_t ldc, cudaStream_t s);  // syrk_tc.cu
+int wl_syrk_tc(cov_handle* h, int nssc, OutMap out, cudaStream_t s, int64_t row1 = -1);  // syrk_tc.cu
 int wl_split_bytes(int64_t M, int K, size_t* bytes);                      // syrk_tc.cu
 int wl_kpad(int K);  // K padded to the contraction's K granularity
 size_t wl_chol_tc_bytes(int64_t n);  // chol_tc.cu
@@ -147,7 +189,7 @@ int wl_chol_slice(cov_handle* h, const double* Wk, int64_t ldw, int64_t k0, int 
 int wl_chol_update(cov_handle* h, double* Wk, int64_t ldw, int64_t r0, int64_t r1, const void* buf, int tj0, int ntj,
                    int* status, cudaStream_t s);
 int wl_syrk_tc_rows(cov_handle* h, const void* hi, const void* lo, const double* rscale, int64_t rows, int Kp,
-                    double* C, int64_t ldc, cudaStream_t s);
+                    OutMap out, cudaStream_t s, int64_t row1 = -1);
 int wl_split_rows(cov_handle* h, const double* X, int64_t rows, int K, void* hi, void* lo, double* rscale,
                   cudaStream_t s);
 

@@ -28,8 +28,8 @@
 __global__ void k_potrf_diag(double* Wk, int64_t ldw, int64_t k0, int kb, int* status);
 __global__ void k_trsm_rows(double* Wk, int64_t ldw, int64_t k0, int kb, int64_t r0, int64_t r1);
 __global__ void k_gemm_lower(const double* __restrict__ A, int64_t lda, const double* __restrict__ B, int64_t ldb,
-                             double* C, int64_t ldc, int64_t n, int64_t k, double alpha, double beta,
-                             int lower_only, int64_t ntiles_1d);
+                             OutMap out, int64_t n, int64_t k, double alpha, double beta, int lower_only,
+                             int64_t ntiles_1d, int64_t tile_off);
 
 #define NA_NB 64
 #define NA_MAX_PREFIX 64
@@ -121,8 +121,8 @@ extern "C" int cov_snr_noalloc(const double* d_C, int64_t ldc, const double* d_D
       int64_t nt1 = (n + 63) / 64;
       double* P = work + r0 * ldw + k0;
       double* Cs = work + r0 * ldw + r0;
-      k_gemm_lower<<<(unsigned)(nt1 * (nt1 + 1) / 2), 256, 0, s>>>(P, ldw, P, ldw, Cs, ldw, n, kb, -1.0, 1.0, 1,
-                                                                    nt1);
+      k_gemm_lower<<<(unsigned)(nt1 * (nt1 + 1) / 2), 256, 0, s>>>(P, ldw, P, ldw, out_rows(Cs, ldw), n, kb, -1.0,
+                                                                    1.0, 1, nt1, 0);
     }
   }
   k_na_prefix<<<n_prefix, 256, 0, s>>>(M, work, ldw, pc, d_snr);

@@ -275,7 +275,7 @@ __device__ __forceinline__ uint32_t idesc_bf16_128x256() {
 
 __global__ void __launch_bounds__(128, 1)
     k_syrk_tc256(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, int64_t M,
-                 int nk, const double* __restrict__ rscale, double* C, int64_t ldc, int* status) {
+                 int nk, const double* __restrict__ rscale, OutMap out, int* status, int64_t tile_off) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[TW_STAGES];
   __shared__ __align__(8) uint64_t empty_bar[TW_STAGES];
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(128, 1)
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t ti, tj;
-  tri_tile_tc(blockIdx.x, &ti, &tj);
+  tri_tile_tc((int64_t)blockIdx.x + tile_off, &ti, &tj);  // tile_off: first tile of a band of tile rows
   int row_i = (int)(ti * TW_BM), row_j = (int)(tj * TW_BM);
 
   if (threadIdx.x == 0) {
@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll 4
         for (int rr = 0; rr < 32; ++rr) {
           int64_t gr = r0 + rr;
-          if (gr < M && gj < M && gj <= gr) C[gr * ldc + gj] = stg[rr * 33 + lane] * sj;
+          if (gr < M && gj < M && gj <= gr) *out.at(gr, gj) = stg[rr * 33 + lane] * sj;
         }
         __syncwarp();
       }
@@ -414,18 +414,19 @@ __global__ void __launch_bounds__(128, 1)
 }
 
 // ---------------------------------------------------------------- host side
-static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+PFN_cuTensorMapEncodeTiled_v12000 wl_encode_tiled() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-  }
+      return (PFN_cuTensorMapEncodeTiled_v12000)p;
+    return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+  }();
   return fn;
 }
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() { return wl_encode_tiled(); }
 
 // 2D view of the blocked array: inner dimension 32 (64 B rows), outer
 // dimension ntiles * nk * 256 block rows; box 32 x 256 = one 16 KB block
@@ -478,21 +479,25 @@ int wl_rows_split(cov_handle* h, int nssc, cudaStream_t s) {
 
 // C (lower, FP64) = (hi + lo)(hi + lo)^T scaled, without the lo lo^T term
 int wl_syrk_tc_rows(cov_handle* h, const void* hi, const void* lo, const double* rscale, int64_t rows, int Kp,
-                    double* C, int64_t ldc, cudaStream_t s) {
+                    OutMap out, cudaStream_t s, int64_t row1) {
   CUtensorMap mhi, mlo;
   int rc;
   if ((rc = make_map(h, &mhi, (void*)hi, rows, Kp))) return rc;
   if ((rc = make_map(h, &mlo, (void*)lo, rows, Kp))) return rc;
-  static bool attr = false;
-  if (!attr) {
-    WL_CHECK(h, cudaFuncSetAttribute(k_syrk_tc256, cudaFuncAttributeMaxDynamicSharedMemorySize, TW_SMEM));
-    attr = true;
-  }
+  static std::once_flag attr_once[WL_MAX_DEVICES];
+  static int attr_rc[WL_MAX_DEVICES];
+  if (wl_once_per_device(attr_once, attr_rc, [] {
+        return (int)cudaFuncSetAttribute(k_syrk_tc256, cudaFuncAttributeMaxDynamicSharedMemorySize, TW_SMEM);
+      }) != 0)
+    return wl_fail(h, COV_ERR_CUDA, "cudaFuncSetAttribute(k_syrk_tc256) failed");
   if (!h->tc_status) WL_CHECK(h, cudaMalloc(&h->tc_status, sizeof(int)));
   WL_CHECK(h, cudaMemsetAsync(h->tc_status, 0, sizeof(int), s));
-  int64_t nt = (rows + TW_BM - 1) / TW_BM;
-  int64_t nblk = nt * (nt + 1) / 2;
-  k_syrk_tc256<<<(unsigned)nblk, 128, TW_SMEM, s>>>(mhi, mlo, rows, Kp / TW_BK, rscale, C, ldc, h->tc_status);
+  // tile rows of the band [out.row0, row1); out.row0 is a multiple of 256
+  if (row1 < 0 || row1 > rows) row1 = rows;
+  int64_t t0 = out.row0 / TW_BM, t1 = (row1 + TW_BM - 1) / TW_BM;
+  int64_t off = t0 * (t0 + 1) / 2;
+  int64_t nblk = t1 * (t1 + 1) / 2 - off;
+  k_syrk_tc256<<<(unsigned)nblk, 128, TW_SMEM, s>>>(mhi, mlo, rows, Kp / TW_BK, rscale, out, h->tc_status, off);
   WL_LAUNCH(h, "k_syrk_tc256");
   int st = 0;
   WL_CHECK(h, cudaMemcpyAsync(&st, h->tc_status, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -501,8 +506,8 @@ int wl_syrk_tc_rows(cov_handle* h, const void* hi, const void* lo, const double*
   return COV_OK;
 }
 
-int wl_syrk_tc(cov_handle* h, int nssc, double* C, int64_t ldc, cudaStream_t s) {
-  return wl_syrk_tc_rows(h, h->Ahi, h->Alo, h->Ascale, h->M, kpad(h->K + nssc), C, ldc, s);
+int wl_syrk_tc(cov_handle* h, int nssc, OutMap out, cudaStream_t s, int64_t row1) {
+  return wl_syrk_tc_rows(h, h->Ahi, h->Alo, h->Ascale, h->M, kpad(h->K + nssc), out, s, row1);
 }
 
 int wl_split_rows(cov_handle* h, const double* X, int64_t rows, int K, void* hi, void* lo, double* rscale,

@@ -76,6 +76,18 @@ class Handle:
         N.check(self.L.cov_assemble(self.h, C.c_void_p(Cmat.data_ptr()), ldc, terms, precision,
                                     _stream_ptr(stream)), self.h)
 
+    def assemble_band(self, row0, nrows, Cout, layout=None, terms=N.COV_TERMS_ALL, precision=N.COV_SPLIT_BF16,
+                      stream=None):
+        """Lower part of rows [row0, row0 + nrows) into Cout.
+
+        layout COV_LAYOUT_ROWS: Cout is 2-D with Cout[r - row0, c] (row stride >= row0 + nrows);
+        COV_LAYOUT_TILES: Cout is a flat buffer of the band's 256 x 256 lower tiles."""
+        if layout is None:
+            layout = N.COV_LAYOUT_TILES if Cout.dim() == 1 else N.COV_LAYOUT_ROWS
+        ldc = Cout.stride(0) if layout == N.COV_LAYOUT_ROWS else 0
+        N.check(self.L.cov_assemble_band(self.h, int(row0), int(nrows), C.c_void_p(Cout.data_ptr()), ldc, layout,
+                                         terms, precision, _stream_ptr(stream)), self.h)
+
     def profile(self, enable=True):
         N.check(self.L.cov_profile(self.h, 1 if enable else 0), self.h)
 

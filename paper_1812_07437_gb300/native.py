@@ -32,8 +32,11 @@ COV_WHICH_P = 0
 COV_WHICH_B = 1
 COV_WHICH_JOINT = 2
 
+COV_LAYOUT_ROWS = 0
+COV_LAYOUT_TILES = 1
+
 EXPORTED = ["cov_init", "cov_update", "cov_layout", "cov_counts", "cov_spectra", "cov_assemble", "cov_snr",
-            "cov_table", "cov_profile", "cov_stage_times", "cov_stage_name", "cov_snr_noalloc", "cov_last_error",
+            "cov_assemble_band", "cov_table", "cov_profile", "cov_stage_times", "cov_stage_name", "cov_snr_noalloc", "cov_last_error",
             "cov_free"]
 COV_NOALLOC_MAX_M = 2047
 N_STAGES = 13
@@ -79,6 +82,7 @@ def lib():
         L.cov_spectra.argtypes = [P, P, P]
         L.cov_assemble.argtypes = [P, P, i64, C.c_uint, C.c_int, P]
         L.cov_snr.argtypes = [P, P, i64, P, C.c_int, P, P]
+        L.cov_assemble_band.argtypes = [P, i64, i64, P, i64, C.c_int, C.c_uint, C.c_int, P]
         L.cov_table.argtypes = [P, C.c_char_p, P, C.POINTER(i64), P]
         L.cov_profile.argtypes = [P, C.c_int]
         L.cov_stage_times.argtypes = [P, P, P, C.c_int]

@@ -52,3 +52,27 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.cov_init(C.byref(cs), C.byref(ns), C.byref(bs2), None, C.byref(h)) == N.COV_ERR_INVALID
     assert lib.cov_spectra(None, None, None) == N.COV_ERR_INVALID
     assert lib.cov_snr(None, None, 0, None, 0, None, None) == N.COV_ERR_INVALID
+    assert lib.cov_assemble_band(None, 0, 256, None, 0, N.COV_LAYOUT_TILES, N.COV_TERMS_ALL, N.COV_SPLIT_BF16,
+                                 None) == N.COV_ERR_INVALID
+
+
+def test_tile_layout_addressing_covers_the_lower_triangle():
+    """The COV_LAYOUT_TILES map (r, c) -> offset is a bijection from the lower
+    triangle of a band onto distinct slots of its tiles, and consecutive bands
+    tile the whole packed matrix without gaps (host restatement of the
+    documented formula, checked on a ragged size)."""
+    import numpy as np
+    M = 3 * 256 + 37
+    nt = (M + 255) // 256
+
+    def off(r, c, row0):
+        ti, tj, t0 = r >> 8, c >> 8, row0 >> 8
+        return ((ti * (ti + 1) // 2 + tj - t0 * (t0 + 1) // 2) << 16) + ((r & 255) << 8) + (c & 255)
+
+    r, c = np.tril_indices(M)
+    o = off(r, c, 0)
+    assert len(np.unique(o)) == len(o)
+    assert o.max() < (nt * (nt + 1) // 2) << 16
+    for row0 in (256, 512):
+        sel = r >= row0
+        assert np.array_equal(off(r[sel], c[sel], row0) + ((row0 >> 8) * ((row0 >> 8) + 1) // 2 << 16), o[sel])
