@@ -203,6 +203,96 @@ const char* cov_stage_name(int stage);
 int cov_snr_noalloc(const double* d_C, int64_t ldc, const double* d_D, int64_t M, const int64_t* prefix,
                     int n_prefix, double* d_snr, int* d_status, void* stream);
 
+/* ---- Serving: continuous batching of covariance + S/N requests ----------
+ *
+ * A request is one covariance with every term and the three cumulative S/N
+ * curves (Eqs. SNprim, eq:SN) for one survey set-up: its own cosmology,
+ * tomographic bins and ell binning.  Requests arrive at any time and differ
+ * in size by orders of magnitude.  The server runs n_slots host workers, each
+ * with its own non-blocking CUDA stream, so the kernels of several requests
+ * overlap on the GPU.  Admission is by HBM footprint: a request starts when a
+ * worker is free and its footprint (a host-side upper estimate: tables,
+ * dense covariance, contraction operands, Cholesky workspace) fits in
+ * hbm_budget next to what running requests and resident state hold.  Requests
+ * are taken in arrival order, except that a later request that fits may start
+ * before an earlier one that does not yet fit (first fit); an earlier
+ * request is passed over at most max_bypass times, after which nothing starts
+ * before it.  A request whose footprint exceeds hbm_budget is rejected at
+ * submission (state COV_REQ_REJECTED).  The device state of a finished
+ * request (tables, counts, operands, covariance and Cholesky workspaces) stays
+ * resident, keyed by its n(z) and binning, and a later request with the same
+ * key reuses it through cov_update (new cosmology, no reallocation); idle
+ * resident state is freed, least recently used first, when a new request
+ * needs the room.  Every result equals that of the same request run alone.
+ * All calls are thread-safe.  The paper has no counterpart: this is the
+ * serving loop around cov_init/cov_update, cov_spectra, cov_assemble and
+ * cov_snr. */
+typedef struct cov_server cov_server;
+
+typedef struct {
+  int device;
+  int n_slots;          /* requests in flight at once, 1..64                        */
+  size_t hbm_budget;    /* bytes the server may hold; 0: 90% of free device memory  */
+  int precision;        /* COV_SPLIT_BF16 or COV_FP64 (the 1-halo contraction)      */
+  unsigned terms;       /* covariance terms, e.g. COV_TERMS_ALL                     */
+  int max_bypass;       /* <= 0: 4                                                  */
+  int dry_run_us;       /* > 0: no device work at all (scheduling only): each request
+                           holds its slot and footprint for dry_run_us microseconds
+                           and returns zero S/N; for testing the scheduler without
+                           a GPU                                                   */
+} cov_server_opts;
+
+typedef struct {
+  cov_cosmology cosmo;
+  cov_nz nz;
+  cov_bins bins;
+} cov_request;
+
+#define COV_REQ_QUEUED 0
+#define COV_REQ_RUNNING 1
+#define COV_REQ_DONE 2
+#define COV_REQ_FAILED 3   /* rc holds the COV_ERR_* code; message in cov_server_error */
+#define COV_REQ_REJECTED 4 /* footprint above hbm_budget */
+
+typedef struct {
+  int state, rc;
+  int64_t M;          /* data-vector length                                  */
+  int n_ell;
+  int slot;           /* worker that ran it (-1 before)                      */
+  int reused;         /* 1: ran on resident state of an earlier request      */
+  size_t footprint;   /* bytes reserved for it while it ran                  */
+  double t_submit, t_start, t_done; /* seconds on the server clock           */
+} cov_request_info;
+
+typedef struct {
+  int64_t submitted, done, failed, rejected;
+  size_t reserved;      /* bytes currently reserved (running + resident)    */
+  size_t peak_reserved; /* maximum of reserved since creation               */
+  size_t budget;
+  int max_running;      /* most requests that ran at the same time          */
+} cov_server_stats;
+
+/* Create a server (starts its workers).  COV_ERR_INVALID for bad options. */
+int cov_server_create(const cov_server_opts* opts, cov_server** out);
+/* Queue a request; returns at once with its id (>= 0).  A request that can
+ * never fit is recorded as COV_REQ_REJECTED (still COV_OK here). */
+int cov_server_submit(cov_server* s, const cov_request* r, int64_t* id);
+/* Wait up to timeout_s seconds (< 0: no limit, 0: poll) for request id to
+ * finish.  Fills *info (may be NULL) and, when done, copies its S/N into
+ * snr (host, 3 * n_ell doubles: P, B, joint; may be NULL).  Returns COV_OK
+ * when the request has finished (done, failed or rejected: see info->state),
+ * COV_ERR_TIMEOUT when it has not, COV_ERR_INVALID for an unknown id. */
+int cov_server_wait(cov_server* s, int64_t id, double timeout_s, cov_request_info* info, double* snr);
+/* Message of a failed request (empty otherwise). */
+const char* cov_server_error(cov_server* s, int64_t id);
+int cov_server_stats_get(cov_server* s, cov_server_stats* st);
+/* Seconds since creation (the clock of t_submit / t_start / t_done). */
+double cov_server_clock(cov_server* s);
+/* Host-only footprint estimate that admission uses, and the data-vector length. */
+int cov_request_footprint(const cov_request* r, int precision, unsigned terms, int64_t* M, size_t* bytes);
+/* Wait for running requests, drop queued ones, free everything. */
+void cov_server_free(cov_server* s);
+
 const char* cov_last_error(const cov_handle* h);
 void cov_free(cov_handle* h);
 

@@ -190,10 +190,89 @@ static void free_all(cov_handle* h) {
                   h->ell_d, h->m, h->om, h->sig0, h->dlns, h->f, h->b1, h->b2, h->U, h->Pl, h->dPl, h->Psh, h->zedges,
                   h->norms, h->W, h->sigw2, h->slo_d, h->shi_d, h->Nmodes, h->Ntri, h->rowtab, h->tris_d,
                   h->rowdesc_d, h->P3, h->RP3, h->B3, h->RB3, h->B1h3, h->Ps, h->B1hp, h->Bp, h->A, h->Ahi,
-                  h->Alo, h->Ascale, h->G2, h->G3, h->C2, h->C3, h->tc_status, h->Thi, h->Tlo, h->Tscale, h->Trows, h->Tmat, h->Srows, h->work, h->perm, h->chol_scratch, h->chol_status};
+                  h->Alo, h->Ascale, h->G2, h->G3, h->C2, h->C3, h->tc_status, h->Thi, h->Tlo, h->Tscale, h->Trows, h->Tmat, h->Srows, h->Fsig, h->Esig, h->Msig, h->FsigT, h->EsigT, h->MsigT, h->invN, h->omN, h->work, h->perm, h->chol_scratch, h->chol_status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (auto& c : h->tile_cache)
+    if (c.p) cudaFree(c.p);
 }
+
+// Device tables that cov_init allocates for a planned handle (pointer, bytes).
+static void init_allocs(cov_handle* h, std::vector<std::pair<void**, size_t>>& al) {
+  const size_t d = sizeof(double);
+  size_t nl = h->nl, nt = h->nt, nchi = h->nchi, nm = h->nm, ntri = std::max(h->ntri, 1);
+  al = {
+      {(void**)&h->gl64x, d * WL_N_GL_CHI}, {(void**)&h->gl64w, d * WL_N_GL_CHI},
+      {(void**)&h->glkx, d * WL_N_K},       {(void**)&h->glkw, d * WL_N_K},
+      {(void**)&h->glcx, d * nchi},         {(void**)&h->glcw, d * nchi},
+      {(void**)&h->scal, d * SC_N},         {(void**)&h->chi, d * nchi},
+      {(void**)&h->wchi, d * nchi},         {(void**)&h->z, d * nchi},
+      {(void**)&h->D, d * nchi},            {(void**)&h->ell_d, d * nl},
+      {(void**)&h->m, d * nm},              {(void**)&h->om, d * nm},
+      {(void**)&h->sig0, d * nm},           {(void**)&h->dlns, d * nm},
+      {(void**)&h->f, d * nchi * nm},       {(void**)&h->b1, d * nchi * nm},
+      {(void**)&h->b2, d * nchi * nm},      {(void**)&h->U, d * nl * nchi * nm},
+      {(void**)&h->Pl, d * nl * nchi},      {(void**)&h->dPl, d * nl * nchi},
+      {(void**)&h->Psh, d * 4 * nl * nchi},
+      {(void**)&h->zedges, d * (nt + 1)},   {(void**)&h->norms, d * nt},
+      {(void**)&h->W, d * nt * nchi},       {(void**)&h->sigw2, d * nchi},
+      {(void**)&h->slo_d, 8 * nl},          {(void**)&h->shi_d, 8 * nl},
+      {(void**)&h->Nmodes, 8 * nl},         {(void**)&h->Ntri, 8 * ntri},
+      {(void**)&h->rowtab, 4 * nl * 2 * (size_t)(h->rmax + 1)},
+      {(void**)&h->tris_d, 4 * 3 * ntri},
+      {(void**)&h->rowdesc_d, 4 * 8 * (size_t)h->M},
+      {(void**)&h->P3, d * nl * nchi},      {(void**)&h->RP3, d * nl * nchi},
+      {(void**)&h->B3, d * ntri * nchi},    {(void**)&h->RB3, d * ntri * nchi},
+      {(void**)&h->B1h3, d * ntri * nchi},  {(void**)&h->Ps, d * nl * nt * nt},
+      {(void**)&h->B1hp, d * ntri * nt * nt * nt},
+  };
+}
+
+// Host-only upper estimate of the device bytes one request holds at its peak:
+// the handle's tables, the dense covariance and data vector, the contraction
+// operands of the chosen precision, the trispectrum table, the Cholesky
+// workspace of the joint vector and the launch-order tables.  No CUDA call.
+int wl_request_bytes(const cov_nz* nz, const cov_bins* bins, int precision, unsigned terms, int64_t* M_out,
+                     size_t* bytes) {
+  cov_cosmology c0{0.31, 0.049, 0.68, 0.96, 0.83, -1.0, 2.7255};
+  if (validate(&c0, nz, bins) != COV_OK) return COV_ERR_INVALID;
+  cov_handle h;
+  h.nz = *nz;
+  h.bins = *bins;
+  plan(&h);
+  std::vector<std::pair<void**, size_t>> al;
+  init_allocs(&h, al);
+  size_t b = 0;
+  for (auto& a : al) b += a.second;
+  const size_t M = (size_t)h.M, K = (size_t)h.K, nchi = (size_t)h.nchi, nt = (size_t)h.ntrow;
+  auto pad256 = [](size_t x) { return (x + 255) / 256 * 256; };
+  auto kpad = [](size_t x) { return (x + 63) / 64 * 64; };
+  b += M * M * 8 + M * 8;                                        // covariance, data vector
+  if (terms & COV_TERM_1H) {
+    if (precision == COV_FP64)
+      b += M * K * 8 + M * nchi * 8;                             // FP64 factor and SSC rows
+    else
+      b += 2 * pad256(M) * kpad(K + nchi) * 2 + M * 8 + 16 * (K + nchi) +
+           ((size_t)h.nl + (size_t)h.ntri) * (K * 4 + nchi * 12);  // BF16 hi/lo rows, signature tables
+  }
+  if (terms & COV_TERM_BBPT) {
+    b += nt * nt * 8;                                            // trispectrum table
+    if (precision == COV_FP64)
+      b += nt * K * 8;                                           // FP64 trispectrum rows
+    else
+      b += 2 * pad256(nt) * kpad(K) * 2 + nt * 8 +
+           (size_t)h.nl * (h.nl + 1) / 2 * (K * 4 + nchi * 12);   // BF16 rows, pair signatures
+  }
+  b += (M + 1) * (M + 1) * 8 + 2 * ((wl_chol_tc_bytes((int64_t)M + 1) + 255) / 256 * 256) + M * 4;
+  size_t t = (M + 255) / 256;
+  b += WL_TILE_CACHE * (t * (t + 1) / 2) * 8;                    // launch orders
+  b += (size_t)64 << 20;                                         // small buffers, allocation granularity
+  *M_out = h.M;
+  *bytes = b;
+  return COV_OK;
+}
+
+size_t wl_handle_bytes(const cov_handle* h) { return h->allocated; }
 
 extern "C" int cov_init(const cov_cosmology* cosmo, const cov_nz* nz, const cov_bins* bins, const cov_opts* opts,
                         cov_handle** out) {
@@ -217,44 +296,18 @@ extern "C" int cov_init(const cov_cosmology* cosmo, const cov_nz* nz, const cov_
     return COV_ERR_CUDA;
   }
   plan(h);
-  const size_t d = sizeof(double);
-  int nl = h->nl, nt = h->nt, nchi = h->nchi, nm = h->nm, ntri = std::max(h->ntri, 1);
-  struct {
-    void** p;
-    size_t n;
-  } al[] = {
-      {(void**)&h->gl64x, d * WL_N_GL_CHI}, {(void**)&h->gl64w, d * WL_N_GL_CHI},
-      {(void**)&h->glkx, d * WL_N_K},       {(void**)&h->glkw, d * WL_N_K},
-      {(void**)&h->glcx, d * nchi},         {(void**)&h->glcw, d * nchi},
-      {(void**)&h->scal, d * SC_N},         {(void**)&h->chi, d * nchi},
-      {(void**)&h->wchi, d * nchi},         {(void**)&h->z, d * nchi},
-      {(void**)&h->D, d * nchi},            {(void**)&h->ell_d, d * nl},
-      {(void**)&h->m, d * nm},              {(void**)&h->om, d * nm},
-      {(void**)&h->sig0, d * nm},           {(void**)&h->dlns, d * nm},
-      {(void**)&h->f, d * nchi * nm},       {(void**)&h->b1, d * nchi * nm},
-      {(void**)&h->b2, d * nchi * nm},      {(void**)&h->U, d * (size_t)nl * nchi * nm},
-      {(void**)&h->Pl, d * nl * nchi},      {(void**)&h->dPl, d * nl * nchi},
-      {(void**)&h->Psh, d * 4 * nl * nchi},
-      {(void**)&h->zedges, d * (nt + 1)},   {(void**)&h->norms, d * nt},
-      {(void**)&h->W, d * nt * nchi},       {(void**)&h->sigw2, d * nchi},
-      {(void**)&h->slo_d, 8ul * nl},          {(void**)&h->shi_d, 8ul * nl},
-      {(void**)&h->Nmodes, 8ul * nl},         {(void**)&h->Ntri, 8 * (size_t)ntri},
-      {(void**)&h->rowtab, 4 * (size_t)nl * 2 * (h->rmax + 1)},
-      {(void**)&h->tris_d, 4 * 3 * (size_t)ntri},
-      {(void**)&h->rowdesc_d, 4 * 8 * (size_t)h->M},
-      {(void**)&h->P3, d * nl * nchi},      {(void**)&h->RP3, d * nl * nchi},
-      {(void**)&h->B3, d * (size_t)ntri * nchi}, {(void**)&h->RB3, d * (size_t)ntri * nchi},
-      {(void**)&h->B1h3, d * (size_t)ntri * nchi}, {(void**)&h->Ps, d * nl * nt * nt},
-      {(void**)&h->B1hp, d * (size_t)ntri * nt * nt * nt},
-  };
+  std::vector<std::pair<void**, size_t>> al;
+  init_allocs(h, al);
   for (auto& a : al) {
-    if ((rc = dalloc(h, a.p, a.n)) != COV_OK) {
+    if ((rc = dalloc(h, a.first, a.second)) != COV_OK) {
       g_init_err = h->err;
       free_all(h);
       delete h;
       return rc;
     }
   }
+  const size_t d = sizeof(double);
+  int nl = h->nl;
   cudaStream_t s = 0;
   cudaMemcpy(h->ell_d, h->ell.data(), d * nl, cudaMemcpyHostToDevice);
   cudaMemcpy(h->slo_d, h->s_lo.data(), 8 * nl, cudaMemcpyHostToDevice);

@@ -13,6 +13,7 @@ int wl_rows_a(cov_handle* h, cudaStream_t s);
 int wl_rows_t(cov_handle* h, cudaStream_t s);
 int wl_rows_s(cov_handle* h, cudaStream_t s);
 int wl_rows_split(cov_handle* h, int nssc, cudaStream_t s);
+int wl_trows_split(cov_handle* h, cudaStream_t s);
 
 __device__ __forceinline__ int64_t leg_pair(int L1, int L2, int nleg) {
   if (L1 > L2) {
@@ -32,9 +33,17 @@ struct GatherArgs {
   const double* B1hp;    // [ntri][nt][nt][nt]
   const double* Tmat;    // [ntrow][ntrow] lower
   int64_t ntrow;
-  const int64_t* Nm;     // N(l^b)
-  const int64_t* Ntri;   // N_tri(t)
+  const double* invN;    // 1 / N(l^b)
+  const double* omN;     // Omega / N_tri(t)
 };
+
+// 1 / N(l^b) and Omega / N_tri(t) from the exact integer counts, once per
+// assembly, so that the per-element products need no FP64 division
+__global__ void k_inv_counts(int nl, int ntri, double omega, const int64_t* Nm, const int64_t* Ntri, double* invN,
+                             double* omN) {
+  for (int i = threadIdx.x; i < nl; i += blockDim.x) invN[i] = 1.0 / (double)Nm[i];
+  for (int t = threadIdx.x; t < ntri; t += blockDim.x) omN[t] = omega / (double)Ntri[t];
+}
 
 __device__ __forceinline__ double ps(const GatherArgs& g, int b, int i, int j) {
   return g.Ps[((size_t)b * g.nt + i) * g.nt + j];
@@ -48,7 +57,7 @@ __device__ double gather_element(const GatherArgs& g, const int32_t* ra, const i
   if (ra[0] == 0 && rb[0] == 0) {
     if ((g.terms & COV_TERM_G) && ra[1] == rb[1]) {
       int b = ra[1], i = ra[4], j = ra[5], k = rb[4], l = rb[5];
-      v += (ps(g, b, i, k) * ps(g, b, j, l) + ps(g, b, i, l) * ps(g, b, j, k)) / (double)g.Nm[b];
+      v += (ps(g, b, i, k) * ps(g, b, j, l) + ps(g, b, i, l) * ps(g, b, j, k)) * g.invN[b];
     }
     return v;
   }
@@ -63,20 +72,20 @@ __device__ double gather_element(const GatherArgs& g, const int32_t* ra, const i
         if (ba[0] == ba[s[0]] && ba[1] == ba[s[1]] && ba[2] == ba[s[2]])
           tot += ps(g, ba[0], ta[0], tb[s[0]]) * ps(g, ba[1], ta[1], tb[s[1]]) * ps(g, ba[2], ta[2], tb[s[2]]);
       }
-      v += g.omega / (double)g.Ntri[ra[7]] * tot;
+      v += g.omN[ra[7]] * tot;
     }
     if (g.terms & COV_TERM_BBPT) {
       for (int x = 0; x < 3; ++x)
         for (int y = 0; y < 3; ++y) {
           if (ba[x] != bb[y]) continue;
           int x1 = (x + 1) % 3, x2 = (x + 2) % 3, y1 = (y + 1) % 3, y2 = (y + 2) % 3;
-          double nN = (double)g.Nm[ba[x]];
+          double iN = g.invN[ba[x]];
           double bbv = b1h(g, ra[7], tb[y], ta[x1], ta[x2]) * b1h(g, rb[7], ta[x], tb[y1], tb[y2]);
           int64_t r1 = leg_pair(ba[x1] * g.nt + ta[x1], ba[x2] * g.nt + ta[x2], g.nleg);
           int64_t r2 = leg_pair(bb[y1] * g.nt + tb[y1], bb[y2] * g.nt + tb[y2], g.nleg);
           int64_t hi = r1 > r2 ? r1 : r2, lo = r1 > r2 ? r2 : r1;
           double tv = g.Tmat[hi * g.ntrow + lo];
-          v += (bbv + ps(g, ba[x], ta[x], tb[y]) * tv) / nN;
+          v += (bbv + ps(g, ba[x], ta[x], tb[y]) * tv) * iN;
         }
     }
     return v;
@@ -90,8 +99,8 @@ __device__ double gather_element(const GatherArgs& g, const int32_t* ra, const i
       int y1 = (y + 1) % 3, y2 = (y + 2) % 3;
       int t = rq[7];
       v += (ps(g, b, i, rq[4 + y]) * b1h(g, t, j, rq[4 + y1], rq[4 + y2]) +
-            ps(g, b, j, rq[4 + y]) * b1h(g, t, i, rq[4 + y1], rq[4 + y2])) /
-           (double)g.Nm[b];
+            ps(g, b, j, rq[4 + y]) * b1h(g, t, i, rq[4 + y1], rq[4 + y2])) *
+           g.invN[b];
     }
   }
   return v;
@@ -211,7 +220,7 @@ static int gemm_lower_band(cov_handle* h, const double* A, int64_t lda, int64_t 
   return COV_OK;
 }
 
-static int ensure(cov_handle* h, void** p, size_t bytes, const char* what) {
+int wl_ensure(cov_handle* h, void** p, size_t bytes, const char* what) {
   if (*p) return COV_OK;
   if (h->budget && h->allocated + bytes > h->budget)
     return wl_fail(h, COV_ERR_NOMEM, std::string("hbm_budget exceeded allocating ") + what);
@@ -224,35 +233,62 @@ static int ensure(cov_handle* h, void** p, size_t bytes, const char* what) {
   h->allocated += bytes;
   return COV_OK;
 }
+static inline int ensure(cov_handle* h, void** p, size_t bytes, const char* what) {
+  return wl_ensure(h, p, bytes, what);
+}
+
+static int gather_args(cov_handle* h, unsigned terms, GatherArgs* g, cudaStream_t s) {
+  int rc;
+  if ((rc = ensure(h, (void**)&h->invN, sizeof(double) * h->nl, "inverse mode counts"))) return rc;
+  if ((rc = ensure(h, (void**)&h->omN, sizeof(double) * (h->ntri > 0 ? h->ntri : 1), "inverse triangle counts")))
+    return rc;
+  k_inv_counts<<<1, 256, 0, s>>>(h->nl, h->ntri, h->omega, h->Nmodes, h->Ntri, h->invN, h->omN);
+  WL_LAUNCH(h, "k_inv_counts");
+  *g = GatherArgs{h->nt, h->nleg, terms, h->omega, h->rowdesc_d, h->Ps, h->B1hp, h->Tmat, h->ntrow, h->invN, h->omN};
+  return COV_OK;
+}
+
+// The 1-halo trispectrum table T = R R^T of the PT term (Eq. CovBB): FP64
+// rows and an FP64 product, or BF16 hi/lo rows built straight from the bin
+// pair signatures and the tensor-core contraction.
+static int build_ttable(cov_handle* h, int precision, cudaStream_t s) {
+  int rc;
+  const int64_t K = h->K;
+  if ((rc = ensure(h, (void**)&h->Tmat, sizeof(double) * h->ntrow * h->ntrow, "trispectrum table"))) return rc;
+  if (precision == COV_FP64) {
+    if ((rc = ensure(h, (void**)&h->Trows, sizeof(double) * h->ntrow * K, "trispectrum rows"))) return rc;
+    int tk = wl_stage_begin(h, ST_ROWS_T, s);
+    if ((rc = wl_rows_t(h, s))) return rc;
+    wl_stage_end(h, tk, s);
+    tk = wl_stage_begin(h, ST_SYRK_T, s);
+    if ((rc = wl_gemm_lower_fp64(h, h->Trows, K, h->Trows, K, h->Tmat, h->ntrow, h->ntrow, K, 1.0, 0.0, true, s)))
+      return rc;
+    wl_stage_end(h, tk, s);
+    return COV_OK;
+  }
+  size_t sb = 0;
+  wl_split_bytes(h->ntrow, (int)K, &sb);
+  if ((rc = ensure(h, (void**)&h->Thi, sb, "BF16 hi trispectrum rows"))) return rc;
+  if ((rc = ensure(h, (void**)&h->Tlo, sb, "BF16 lo trispectrum rows"))) return rc;
+  if ((rc = ensure(h, (void**)&h->Tscale, sizeof(double) * h->ntrow, "trispectrum row scales"))) return rc;
+  int tk = wl_stage_begin(h, ST_ROWS_T, s);
+  if ((rc = wl_trows_split(h, s))) return rc;
+  wl_stage_end(h, tk, s);
+  tk = wl_stage_begin(h, ST_SYRK_T, s);
+  if ((rc = wl_syrk_tc_rows(h, h->Thi, h->Tlo, h->Tscale, h->ntrow, wl_kpad((int)K), out_rows(h->Tmat, h->ntrow),
+                            s)))
+    return rc;
+  wl_stage_end(h, tk, s);
+  return COV_OK;
+}
 
 int wl_assemble(cov_handle* h, double* C, int64_t ldc, unsigned terms, int precision, cudaStream_t s) {
   int rc;
   const int64_t M = h->M, K = h->K;
   bool ssc_merged = false;
   // 1. the 1-halo trispectrum table of the PT term
-  if (terms & COV_TERM_BBPT) {
-    if ((rc = ensure(h, (void**)&h->Trows, sizeof(double) * h->ntrow * K, "trispectrum rows"))) return rc;
-    if ((rc = ensure(h, (void**)&h->Tmat, sizeof(double) * h->ntrow * h->ntrow, "trispectrum table"))) return rc;
-    int tk = wl_stage_begin(h, ST_ROWS_T, s);
-    if ((rc = wl_rows_t(h, s))) return rc;
-    wl_stage_end(h, tk, s);
-    tk = wl_stage_begin(h, ST_SYRK_T, s);
-    if (precision == COV_FP64) {
-      if ((rc = wl_gemm_lower_fp64(h, h->Trows, K, h->Trows, K, h->Tmat, h->ntrow, h->ntrow, K, 1.0, 0.0, true, s)))
-        return rc;
-    } else {
-      size_t sb = 0;
-      wl_split_bytes(h->ntrow, (int)K, &sb);
-      if ((rc = ensure(h, (void**)&h->Thi, sb, "BF16 hi trispectrum rows"))) return rc;
-      if ((rc = ensure(h, (void**)&h->Tlo, sb, "BF16 lo trispectrum rows"))) return rc;
-      if ((rc = ensure(h, (void**)&h->Tscale, sizeof(double) * h->ntrow, "trispectrum row scales"))) return rc;
-      if ((rc = wl_split_rows(h, h->Trows, h->ntrow, (int)K, h->Thi, h->Tlo, h->Tscale, s))) return rc;
-      if ((rc = wl_syrk_tc_rows(h, h->Thi, h->Tlo, h->Tscale, h->ntrow, wl_kpad((int)K),
-                                out_rows(h->Tmat, h->ntrow), s)))
-        return rc;
-    }
-    wl_stage_end(h, tk, s);
-  }
+  if (terms & COV_TERM_BBPT)
+    if ((rc = build_ttable(h, precision, s))) return rc;
   // 2. 1-halo (chi, M) contraction: the first writer of the lower triangle
   if (terms & COV_TERM_1H) {
     if (precision == COV_FP64) {
@@ -287,7 +323,8 @@ int wl_assemble(cov_handle* h, double* C, int64_t ldc, unsigned terms, int preci
     }
   }
   // per-element product terms: initialise C when no 1-halo term ran
-  GatherArgs g{h->nt, h->nleg, terms, h->omega, h->rowdesc_d, h->Ps, h->B1hp, h->Tmat, h->ntrow, h->Nmodes, h->Ntri};
+  GatherArgs g;
+  if ((rc = gather_args(h, terms, &g, s))) return rc;
   int64_t nt32 = (M + 31) / 32;
   int tg = wl_stage_begin(h, ST_GATHER, s);
   k_gather<<<(unsigned)(nt32 * (nt32 + 1) / 2), dim3(32, 8), 0, s>>>(g, M, out_rows(C, ldc),
@@ -315,29 +352,8 @@ int wl_assemble(cov_handle* h, double* C, int64_t ldc, unsigned terms, int preci
 static int prepare_operands(cov_handle* h, unsigned terms, int precision, cudaStream_t s) {
   int rc;
   const int64_t M = h->M, K = h->K;
-  if (terms & COV_TERM_BBPT) {
-    if ((rc = ensure(h, (void**)&h->Trows, sizeof(double) * h->ntrow * K, "trispectrum rows"))) return rc;
-    if ((rc = ensure(h, (void**)&h->Tmat, sizeof(double) * h->ntrow * h->ntrow, "trispectrum table"))) return rc;
-    int tk = wl_stage_begin(h, ST_ROWS_T, s);
-    if ((rc = wl_rows_t(h, s))) return rc;
-    wl_stage_end(h, tk, s);
-    tk = wl_stage_begin(h, ST_SYRK_T, s);
-    if (precision == COV_FP64) {
-      if ((rc = wl_gemm_lower_fp64(h, h->Trows, K, h->Trows, K, h->Tmat, h->ntrow, h->ntrow, K, 1.0, 0.0, true, s)))
-        return rc;
-    } else {
-      size_t sb = 0;
-      wl_split_bytes(h->ntrow, (int)K, &sb);
-      if ((rc = ensure(h, (void**)&h->Thi, sb, "BF16 hi trispectrum rows"))) return rc;
-      if ((rc = ensure(h, (void**)&h->Tlo, sb, "BF16 lo trispectrum rows"))) return rc;
-      if ((rc = ensure(h, (void**)&h->Tscale, sizeof(double) * h->ntrow, "trispectrum row scales"))) return rc;
-      if ((rc = wl_split_rows(h, h->Trows, h->ntrow, (int)K, h->Thi, h->Tlo, h->Tscale, s))) return rc;
-      if ((rc = wl_syrk_tc_rows(h, h->Thi, h->Tlo, h->Tscale, h->ntrow, wl_kpad((int)K),
-                                out_rows(h->Tmat, h->ntrow), s)))
-        return rc;
-    }
-    wl_stage_end(h, tk, s);
-  }
+  if (terms & COV_TERM_BBPT)
+    if ((rc = build_ttable(h, precision, s))) return rc;
   if (precision == COV_FP64) {
     if (terms & COV_TERM_1H) {
       if ((rc = ensure(h, (void**)&h->A, sizeof(double) * M * K, "FP64 factor rows"))) return rc;
@@ -390,7 +406,8 @@ int wl_assemble_band(cov_handle* h, int64_t row0, int64_t nrows, OutMap out, uns
     wl_stage_end(h, tk, s);
   }
   // 2. per-element product terms
-  GatherArgs g{h->nt, h->nleg, terms, h->omega, h->rowdesc_d, h->Ps, h->B1hp, h->Tmat, h->ntrow, h->Nmodes, h->Ntri};
+  GatherArgs g;
+  if ((rc = gather_args(h, terms, &g, s))) return rc;
   int64_t t0 = row0 / 32, t1 = (row1 + 31) / 32;
   int64_t off = t0 * (t0 + 1) / 2;
   int tg = wl_stage_begin(h, ST_GATHER, s);

@@ -172,22 +172,34 @@ int wl_snr(cov_handle* h, const double* C, int64_t ldc, const double* D, int whi
   int64_t ldw = Ms + 1;
   int64_t need = ldw * ldw;
   if (need > h->work_n) {
-    if (h->work) cudaFree(h->work);
+    if (h->work) {
+      cudaFree(h->work);
+      h->allocated -= sizeof(double) * h->work_n;
+    }
     h->work = nullptr;
+    h->work_n = 0;
     if (h->budget && h->allocated + sizeof(double) * need > h->budget)
       return wl_fail(h, COV_ERR_NOMEM, "hbm_budget exceeded allocating the Cholesky workspace");
     WL_CHECK(h, cudaMalloc(&h->work, sizeof(double) * need));
     h->work_n = need;
+    h->allocated += sizeof(double) * need;
   }
-  if (!h->perm) WL_CHECK(h, cudaMalloc(&h->perm, sizeof(int) * h->M));
+  if (!h->perm) {
+    WL_CHECK(h, cudaMalloc(&h->perm, sizeof(int) * h->M));
+    h->allocated += sizeof(int) * h->M;
+  }
   size_t one_buf = (wl_chol_tc_bytes(Ms + 1) + 255) / 256 * 256;
   size_t need_sc = 2 * one_buf;
   if (need_sc > h->chol_scratch_n) {
-    if (h->chol_scratch) cudaFree(h->chol_scratch);
+    if (h->chol_scratch) {
+      cudaFree(h->chol_scratch);
+      h->allocated -= h->chol_scratch_n;
+    }
     h->chol_scratch = nullptr;
     h->chol_scratch_n = 0;
     WL_CHECK(h, cudaMalloc(&h->chol_scratch, need_sc));
     h->chol_scratch_n = need_sc;
+    h->allocated += need_sc;
   }
   if (!h->chol_status) WL_CHECK(h, cudaMalloc(&h->chol_status, sizeof(int)));
   if (!h->side) {

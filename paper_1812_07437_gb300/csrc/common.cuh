@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -59,6 +60,8 @@ struct StageEvent {
 // cuTensorMapEncodeTiled from the driver, looked up once per process
 // (thread-safe: the serving scheduler runs requests on several host threads).
 PFN_cuTensorMapEncodeTiled_v12000 wl_encode_tiled();
+#define WL_TILE_CACHE 4
+int wl_ensure(struct cov_handle* h, void** p, size_t bytes, const char* what);  // assemble.cu: allocate once
 // Run f once per CUDA device for the calling thread's current device.
 #define WL_MAX_DEVICES 64
 template <typename F>
@@ -125,6 +128,23 @@ struct cov_handle {
   uint16_t *Ahi = nullptr, *Alo = nullptr;  // [M][K] BF16 split rows (tensor-core form)
   double* Ascale = nullptr; // per-row power-of-two scales of the split rows
   double *G2 = nullptr, *G3 = nullptr, *C2 = nullptr, *C3 = nullptr;  // row-builder factor tables
+  // per leg-bin signature s (P: ell bin; B: nl + triangle): F[s][n][q] / 2^E[s][n] in FP32,
+  // E[s][n], and the FP64 row-block maximum max_q |F[s][n][q]|
+  double *invN = nullptr, *omN = nullptr;  // 1 / N(l^b), Omega / N_tri(t)
+  // launch orders of the tensor-core contraction, by tile-row range
+  struct TileOrder {
+    int kind = -1;
+    int64_t t0 = -1, t1 = -1, n = 0;
+    size_t cap = 0;
+    int2* p = nullptr;
+  } tile_cache[WL_TILE_CACHE];
+  int tile_cache_next = 0;
+  float* Fsig = nullptr;
+  float* FsigT = nullptr;  // the same for the bin pairs of the trispectrum rows
+  int* EsigT = nullptr;
+  double* MsigT = nullptr;
+  int* Esig = nullptr;
+  double* Msig = nullptr;
   int* tc_status = nullptr; // status word of the tensor-core contraction
   double* Trows = nullptr;  // [ntrow][K]
   double* Tmat = nullptr;   // [ntrow][ntrow] lower
@@ -183,6 +203,10 @@ int wl_gemm_lower_fp64(cov_handle* h, const double* A, int64_t lda, const double
 int wl_syrk_tc(cov_handle* h, int nssc, OutMap out, cudaStream_t s, int64_t row1 = -1);  // syrk_tc.cu
 int wl_split_bytes(int64_t M, int K, size_t* bytes);                      // syrk_tc.cu
 int wl_kpad(int K);  // K padded to the contraction's K granularity
+int wl_request_bytes(const cov_nz* nz, const cov_bins* bins, int precision, unsigned terms, int64_t* M,
+                     size_t* bytes);  // api.cu: host-only footprint estimate of one request
+size_t wl_handle_bytes(const cov_handle* h);
+void wl_set_global_error(const std::string& msg);  // api.cu: read by cov_last_error(NULL)
 size_t wl_chol_tc_bytes(int64_t n);  // chol_tc.cu
 int wl_chol_slice(cov_handle* h, const double* Wk, int64_t ldw, int64_t k0, int kb, int64_t r0, int64_t r1,
                   void* buf, cudaStream_t s);
@@ -190,9 +214,6 @@ int wl_chol_update(cov_handle* h, double* Wk, int64_t ldw, int64_t r0, int64_t r
                    int* status, cudaStream_t s);
 int wl_syrk_tc_rows(cov_handle* h, const void* hi, const void* lo, const double* rscale, int64_t rows, int Kp,
                     OutMap out, cudaStream_t s, int64_t row1 = -1);
-int wl_split_rows(cov_handle* h, const double* X, int64_t rows, int K, void* hi, void* lo, double* rscale,
-                  cudaStream_t s);
-
 // ---- device helpers ------------------------------------------------------------
 __device__ __forceinline__ DevCosmo dev_cosmo(const cov_cosmology& c) {
   return DevCosmo{c.Om, c.Ob, c.h, c.ns, c.sigma8, c.w0, c.Tcmb};
@@ -347,6 +368,11 @@ __device__ __forceinline__ double dev_nfw_u(double k, double m, double z, double
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 

@@ -57,102 +57,209 @@ __global__ void k_rows_prep(int nchi, int nm, double inv_omega, double rho, cons
   }
 }
 
+// Rows that share their ell bins share the (n, q) part of the 1-halo factor:
+// a P row of bin b has F_b[n][q] = g2[n][q] c2[n] U_b[n][q]^2, a B row of
+// triangle (a, b, c) has F_abc[n][q] = g3[n][q] c3[n] U_a U_b U_c, and the row
+// itself is F[n][q] times the product of its lensing kernels W_i(chi_n).  One
+// block per (signature s, node n) stores F[s][n][.] / 2^E[s][n] in FP32 (its
+// largest magnitude in [0.5, 1)), E[s][n] and the FP64 maximum.
+// pairs: signatures are the bin pairs b1 <= b2 (trispectrum rows, mu = 2)
+// instead of the P bins and B triangles.
+__global__ void k_rows_sig(int nl, int ntri, int nchi, int nm, const int32_t* tris, const double* U, const double* g2,
+                           const double* g3, const double* c2, const double* c3, float* F, int* E, double* Mx,
+                           int pairs) {
+  __shared__ double red[32];
+  int s = blockIdx.x, n = blockIdx.y;
+  bool isP = pairs || s < nl;
+  int a, b, c;
+  if (pairs) {
+    a = 0;
+    int base = 0;
+    while (base + (nl - a) <= s) {
+      base += nl - a;
+      ++a;
+    }
+    b = a + (s - base);
+    c = b;
+  } else if (isP) {
+    a = b = c = s;
+  } else {
+    a = tris[3 * (s - nl)];
+    b = tris[3 * (s - nl) + 1];
+    c = tris[3 * (s - nl) + 2];
+  }
+  const size_t K = (size_t)nchi * nm;
+  const double* Ua = U + a * K + (size_t)n * nm;
+  const double* Ub = U + b * K + (size_t)n * nm;
+  const double* Uc = U + c * K + (size_t)n * nm;
+  const double* g = (isP ? g2 : g3) + (size_t)n * nm;
+  double cn = isP ? c2[n] : c3[n];
+  auto value = [&](int q) { return isP ? g[q] * cn * Ua[q] * Ub[q] : g[q] * cn * Ua[q] * Ub[q] * Uc[q]; };
+  double mx = 0.0;
+  for (int q = threadIdx.x; q < nm; q += blockDim.x) mx = fmax(mx, fabs(value(q)));
+  mx = warp_max(mx);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    t = warp_max(t);
+    if (threadIdx.x == 0) red[0] = t;
+  }
+  __syncthreads();
+  mx = red[0];
+  int e = 0;
+  if (mx > 0.0) frexp(mx, &e);
+  float* Fo = F + (size_t)s * K + (size_t)n * nm;
+  for (int q = threadIdx.x; q < nm; q += blockDim.x) Fo[q] = (float)ldexp(value(q), -e);
+  if (threadIdx.x == 0) {
+    E[(size_t)s * nchi + n] = e;
+    Mx[(size_t)s * nchi + n] = mx;
+  }
+}
+
 // One block per row a: entries 0..K-1 are the 1-halo factor row; when
 // nssc > 0, entries K..K+nssc-1 are the super-sample row S[a][n] (so that one
 // contraction gives A A^T + S S^T); the rest of Kp is zero.  The row is scaled
 // by an exact power of two s_a (largest entry in [0.5, 1)) and split into
-// BF16 hi/lo.
-__global__ void k_rows_split(int64_t M, int nchi, int nm, int Kp, int nssc, const int32_t* rd, const double* W,
-                             const double* U, const double* g2, const double* g3, const double* c2,
-                             const double* c3, const double* wchi, const double* sigw2, const double* chi,
-                             const double* RP3, const double* RB3, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                             double* rscale) {
-  __shared__ double sh[32];
+// BF16 hi/lo.  FP64 work is per node (kernel products, row maximum, the
+// super-sample entries); each factor entry is one FP32 product of the
+// signature table and a per-node FP32 weight, exact to a few 2^-24, well
+// inside the 2^-17 of the hi/lo split.
+__global__ void k_rows_split(int64_t M, int nl, int nchi, int nm, int Kp, int nssc, const int32_t* rd,
+                             const double* W, const float* F, const int* E, const double* Mx, const double* wchi,
+                             const double* sigw2, const double* chi, const double* RP3, const double* RB3,
+                             __nv_bfloat16* hi, __nv_bfloat16* lo, double* rscale) {
+  extern __shared__ double rs_sh[];  // [nchi] node weights, [nchi] super-sample entries
+  __shared__ double red[32];
   int64_t a = blockIdx.x;
   if (a >= M) return;
   const int32_t* r = rd + 8 * a;
-  int K = nchi * nm;
+  const int K = nchi * nm;
   const bool isP = (r[0] == 0);
-  const double* g = isP ? g2 : g3;
-  const double* cp = isP ? c2 : c3;
-  const double* U1 = U + (size_t)r[1] * nchi * nm;
-  const double* U2 = U + (size_t)r[2] * nchi * nm;
-  const double* U3 = U + (size_t)r[3] * nchi * nm;
+  const int sg = isP ? r[1] : nl + r[7];
   const double* W1 = W + r[4] * nchi;
   const double* W2 = W + r[5] * nchi;
   const double* W3 = W + (isP ? r[4] : r[6]) * nchi;
-  auto value = [&](int kk) -> double {
-    if (kk < K) {
-      int n = kk / nm;
-      double v = g[kk] * cp[n] * W1[n] * W2[n] * U1[kk] * U2[kk];
-      if (!isP) v *= W3[n] * U3[kk];
-      return v;
-    }
-    int n = kk - K;
-    if (n >= nssc) return 0.0;
-    double ch = chi[n], v = sqrt(wchi[n] * sigw2[n]) * W1[n] * W2[n];
-    if (isP) return v / (ch * ch) * RP3[r[1] * nchi + n];
-    double c2_ = ch * ch;
-    return v * W3[n] / (c2_ * c2_) * RB3[r[7] * nchi + n];
-  };
-  int Kt = K + nssc;
+  const int* Es = E + (size_t)sg * nchi;
+  const double* Ms = Mx + (size_t)sg * nchi;
+  double* wsh = rs_sh;
+  double* ssh = rs_sh + nchi;
+  // pass 1 (per node): kernel products, super-sample entries, row maximum
   double mx = 0.0;
-  for (int kk = threadIdx.x; kk < Kt; kk += blockDim.x) mx = fmax(mx, fabs(value(kk)));
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+  for (int n = threadIdx.x; n < nchi; n += blockDim.x) {
+    double w = W1[n] * W2[n];
+    if (!isP) w *= W3[n];
+    wsh[n] = w;
+    mx = fmax(mx, fabs(w) * Ms[n]);
+    double v = 0.0;
+    if (n < nssc) {
+      double ch = chi[n], c2_ = ch * ch;
+      v = sqrt(wchi[n] * sigw2[n]) * w;
+      v = isP ? v / c2_ * RP3[r[1] * nchi + n] : v / (c2_ * c2_) * RB3[r[7] * nchi + n];
+      mx = fmax(mx, fabs(v));
+    }
+    ssh[n] = v;
+  }
+  mx = warp_max(mx);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x < 32) {
-    double t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
-    if (threadIdx.x == 0) sh[0] = t;
+    double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    t = warp_max(t);
+    if (threadIdx.x == 0) red[0] = t;
   }
   __syncthreads();
-  mx = sh[0];
+  mx = red[0];
   int ex = 0;
   if (mx > 0.0) frexp(mx, &ex);
-  double inv = ldexp(1.0, -ex);
-  int nk = Kp / TW_BK;
-  for (int kk = threadIdx.x; kk < Kp; kk += blockDim.x) {
-    double x = (kk < Kt) ? value(kk) * inv : 0.0;
-    __nv_bfloat16 h = __float2bfloat16_rn((float)x);
-    __nv_bfloat16 l = __float2bfloat16_rn((float)(x - (double)__bfloat162float(h)));
-    hi[blk_off(a, kk, nk)] = h;
-    lo[blk_off(a, kk, nk)] = l;
+  // pass 2 (per node): FP32 weights relative to the row scale 2^ex
+  float* wf = (float*)(rs_sh + 2 * nchi);
+  float* sf = wf + nchi;
+  for (int n = threadIdx.x; n < nchi; n += blockDim.x) {
+    wf[n] = (float)ldexp(wsh[n], Es[n] - ex);
+    sf[n] = (float)ldexp(ssh[n], -ex);
+  }
+  __syncthreads();
+  // pass 3 (per entry pair): one FP32 product, BF16 hi/lo split, paired stores
+  const float* Fs = F + (size_t)sg * K;
+  const int Kt = K + nssc;
+  const int nk = Kp / TW_BK;
+  auto value = [&](int kk) -> float {
+    if (kk < K) return Fs[kk] * wf[(unsigned)kk / (unsigned)nm];
+    return kk < Kt ? sf[kk - K] : 0.0f;
+  };
+  for (int kk = 2 * threadIdx.x; kk < Kp; kk += 2 * blockDim.x) {
+    float x0 = value(kk), x1 = value(kk + 1);
+    __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
+    __nv_bfloat162 l2 = __floats2bfloat162_rn(x0 - __low2float(h2), x1 - __high2float(h2));
+    int64_t o = blk_off(a, kk, nk);
+    *(__nv_bfloat162*)(hi + o) = h2;
+    *(__nv_bfloat162*)(lo + o) = l2;
   }
   if (threadIdx.x == 0) rscale[a] = ldexp(1.0, ex);
 }
 
-// split already-built FP64 rows X[rows][K] into scaled BF16 hi/lo rows [rows][Kp]
-__global__ void k_split_rows(const double* X, int64_t rows, int K, int Kp, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                             double* rscale) {
-  __shared__ double sh[32];
-  int64_t a = blockIdx.x;
-  if (a >= rows) return;
-  const double* x = X + a * K;
+// Trispectrum rows of the PT term, one block per leg pair (L1 <= L2),
+// L = bin * n_t + tomo: T[(n, q)] = sqrt(w_n omega_q f_nq) (m_q/rho)^2
+// chi_n^-3 W_t1 W_t2 U_b1 U_b2, i.e. the pair signature (b1, b2) times the
+// node weight sqrt(Omega) W_t1(chi_n) W_t2(chi_n); scaled and split as
+// k_rows_split does.
+__global__ void k_trows_split(int64_t ntrow, int nleg, int nt, int nl, int nchi, int nm, int Kp, double sqrt_omega,
+                              const double* W, const float* F, const int* E, const double* Mx, __nv_bfloat16* hi,
+                              __nv_bfloat16* lo, double* rscale) {
+  extern __shared__ double ts_sh[];  // [nchi] node weights (FP64), then [nchi] FP32
+  __shared__ double red[32];
+  int64_t r = blockIdx.x;
+  if (r >= ntrow) return;
+  int L1 = 0;
+  int64_t base = 0;
+  while (base + (nleg - L1) <= r) {
+    base += nleg - L1;
+    ++L1;
+  }
+  int L2 = L1 + (int)(r - base);
+  int b1 = L1 / nt, t1 = L1 % nt, b2 = L2 / nt, t2 = L2 % nt;
+  int lo_b = b1 < b2 ? b1 : b2, hi_b = b1 < b2 ? b2 : b1;
+  int sg = lo_b * nl - lo_b * (lo_b - 1) / 2 + (hi_b - lo_b);
+  const int K = nchi * nm;
+  const double* W1 = W + t1 * nchi;
+  const double* W2 = W + t2 * nchi;
+  const int* Es = E + (size_t)sg * nchi;
+  const double* Ms = Mx + (size_t)sg * nchi;
+  double* wsh = ts_sh;
   double mx = 0.0;
-  for (int kk = threadIdx.x; kk < K; kk += blockDim.x) mx = fmax(mx, fabs(x[kk]));
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+  for (int n = threadIdx.x; n < nchi; n += blockDim.x) {
+    double w = W1[n] * W2[n] * sqrt_omega;
+    wsh[n] = w;
+    mx = fmax(mx, fabs(w) * Ms[n]);
+  }
+  mx = warp_max(mx);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x < 32) {
-    double t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
-    if (threadIdx.x == 0) sh[0] = t;
+    double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    t = warp_max(t);
+    if (threadIdx.x == 0) red[0] = t;
   }
   __syncthreads();
-  mx = sh[0];
+  mx = red[0];
   int ex = 0;
   if (mx > 0.0) frexp(mx, &ex);
-  double inv = ldexp(1.0, -ex);
-  int nk = Kp / TW_BK;
-  for (int kk = threadIdx.x; kk < Kp; kk += blockDim.x) {
-    double v = (kk < K) ? x[kk] * inv : 0.0;
-    __nv_bfloat16 h = __float2bfloat16_rn((float)v);
-    __nv_bfloat16 l = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
-    hi[blk_off(a, kk, nk)] = h;
-    lo[blk_off(a, kk, nk)] = l;
+  float* wf = (float*)(ts_sh + nchi);
+  for (int n = threadIdx.x; n < nchi; n += blockDim.x) wf[n] = (float)ldexp(wsh[n], Es[n] - ex);
+  __syncthreads();
+  const float* Fs = F + (size_t)sg * K;
+  const int nk = Kp / TW_BK;
+  for (int kk = 2 * threadIdx.x; kk < Kp; kk += 2 * blockDim.x) {
+    float x0 = kk < K ? Fs[kk] * wf[(unsigned)kk / (unsigned)nm] : 0.0f;
+    float x1 = kk + 1 < K ? Fs[kk + 1] * wf[(unsigned)(kk + 1) / (unsigned)nm] : 0.0f;
+    __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
+    __nv_bfloat162 l2 = __floats2bfloat162_rn(x0 - __low2float(h2), x1 - __high2float(h2));
+    int64_t o = blk_off(r, kk, nk);
+    *(__nv_bfloat162*)(hi + o) = h2;
+    *(__nv_bfloat162*)(lo + o) = l2;
   }
-  if (threadIdx.x == 0) rscale[a] = ldexp(1.0, ex);
+  if (threadIdx.x == 0) rscale[r] = ldexp(1.0, ex);
 }
 
 // ---------------------------------------------------------------- PTX helpers
@@ -275,7 +382,7 @@ __device__ __forceinline__ uint32_t idesc_bf16_128x256() {
 
 __global__ void __launch_bounds__(128, 1)
     k_syrk_tc256(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, int64_t M,
-                 int nk, const double* __restrict__ rscale, OutMap out, int* status, int64_t tile_off) {
+                 int nk, const double* __restrict__ rscale, OutMap out, int* status, const int2* __restrict__ tiles) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[TW_STAGES];
   __shared__ __align__(8) uint64_t empty_bar[TW_STAGES];
@@ -286,7 +393,11 @@ __global__ void __launch_bounds__(128, 1)
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t ti, tj;
-  tri_tile_tc((int64_t)blockIdx.x + tile_off, &ti, &tj);  // tile_off: first tile of a band of tile rows
+  {
+    int2 t = tiles[blockIdx.x];  // grouped order: about one wave shares a 12 x 12 block of tiles
+    ti = t.x;
+    tj = t.y;
+  }
   int row_i = (int)(ti * TW_BM), row_j = (int)(tj * TW_BM);
 
   if (threadIdx.x == 0) {
@@ -413,6 +524,194 @@ __global__ void __launch_bounds__(128, 1)
   }
 }
 
+// ---------------------------------------------------------------- 2 x 2 clusters
+// Four CTAs of a cluster compute the 2 x 2 tiles (I0 + r, J0 + c), r, c in
+// {0, 1}, of a 512 x 512 super-tile.  Row panel I0 + r is needed by CTAs
+// (r, 0) and (r, 1), column panel J0 + c by (0, c) and (1, c); each CTA loads
+// one 128-row half of its row panel and one half of its column panel and
+// multicasts each half to the two CTAs that use it, so every CTA receives the
+// same 64 KB per K block while reading only 32 KB from L2 (the contraction is
+// bound by L2 bandwidth, not by HBM or the tensor pipe).  A CTA's stage s is
+// written by itself, its row peer and its column peer, so its MMA completion
+// is multicast to the empty barriers of those three, and each empty barrier
+// counts three arrivals.  Tiles above the diagonal or past the band are
+// computed (their halves feed the neighbours) but not stored.
+#define MC_BOX_ROWS 128
+#define MC_HALF_BYTES (MC_BOX_ROWS * TW_BK * 2)  // 8 KB
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_2d_mc(const CUtensorMap* map, uint64_t* bar, void* dst, int c0, int c1,
+                                               uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, "
+      "{%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+
+__global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128, 1)
+    k_syrk_tc256_mc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
+                    int64_t M, int nk, const double* __restrict__ rscale, OutMap out, int* status,
+                    const int2* __restrict__ supers, int64_t t1) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[TW_STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[TW_STAGES];
+  __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ volatile int abort_flag;
+
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const int rr = (int)(rank >> 1), cc = (int)(rank & 1);
+  const int2 sup = supers[blockIdx.x >> 2];
+  const int64_t ti = (int64_t)sup.x + rr, tj = (int64_t)sup.y + cc;
+  const int row_i = (int)(ti * TW_BM), row_j = (int)(tj * TW_BM);
+  const bool store = ti < t1 && tj <= ti;
+  // CTAs (rr, 0), (rr, 1) share the row panel; (0, cc), (1, cc) the column panel
+  const uint16_t row_mask = (uint16_t)(3u << (2 * rr));
+  const uint16_t col_mask = (uint16_t)((1u << cc) | (1u << (2 + cc)));
+  const uint16_t writers = (uint16_t)(row_mask | col_mask);  // self, row peer, column peer
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int st = 0; st < TW_STAGES; ++st) {
+      mbar_init(&full_bar[st], 1);
+      mbar_init(&empty_bar[st], 3);
+    }
+    mbar_init(&acc_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  cluster_sync_all();  // every barrier of the cluster is initialised before any multicast
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  uint32_t tmem = tmem_base_sh;
+
+  if (warp == 0 && lane == 0) {
+    // my halves: rows cc*128.. of the row panel, rows rr*128.. of the column panel
+    for (int kb = 0; kb < TW_PREFETCH && kb < nk; ++kb) {
+      tma_prefetch_2d(&map_hi, 0, (int)((ti * nk + kb) * TW_BM) + cc * MC_BOX_ROWS);
+      tma_prefetch_2d(&map_lo, 0, (int)((ti * nk + kb) * TW_BM) + cc * MC_BOX_ROWS);
+      tma_prefetch_2d(&map_hi, 0, (int)((tj * nk + kb) * TW_BM) + rr * MC_BOX_ROWS);
+      tma_prefetch_2d(&map_lo, 0, (int)((tj * nk + kb) * TW_BM) + rr * MC_BOX_ROWS);
+    }
+    int issued = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      int st = kb % TW_STAGES;
+      uint32_t ph = (uint32_t)(kb / TW_STAGES) & 1u;
+      if (!mbar_wait(&empty_bar[st], ph ^ 1u, &abort_flag, status)) break;
+      issued = kb + 1;
+      uint8_t* sp = smem + (size_t)st * TW_STAGE_BYTES;
+      mbar_expect_tx(&full_bar[st], TW_STAGE_BYTES);
+      int yi = (int)((ti * nk + kb) * TW_BM) + cc * MC_BOX_ROWS;
+      int yj = (int)((tj * nk + kb) * TW_BM) + rr * MC_BOX_ROWS;
+      if (kb + TW_PREFETCH < nk) {
+        tma_prefetch_2d(&map_hi, 0, yi + TW_PREFETCH * TW_BM);
+        tma_prefetch_2d(&map_lo, 0, yi + TW_PREFETCH * TW_BM);
+        tma_prefetch_2d(&map_hi, 0, yj + TW_PREFETCH * TW_BM);
+        tma_prefetch_2d(&map_lo, 0, yj + TW_PREFETCH * TW_BM);
+      }
+      tma_load_2d_mc(&map_hi, &full_bar[st], sp + 0 * TW_OP_BYTES + cc * MC_HALF_BYTES, 0, yi, row_mask);
+      tma_load_2d_mc(&map_lo, &full_bar[st], sp + 1 * TW_OP_BYTES + cc * MC_HALF_BYTES, 0, yi, row_mask);
+      tma_load_2d_mc(&map_hi, &full_bar[st], sp + 2 * TW_OP_BYTES + rr * MC_HALF_BYTES, 0, yj, col_mask);
+      tma_load_2d_mc(&map_lo, &full_bar[st], sp + 3 * TW_OP_BYTES + rr * MC_HALF_BYTES, 0, yj, col_mask);
+    }
+    // wait until the three consumers have released the last use of every
+    // stage: no peer signals this CTA's barriers after that
+    for (int kb = issued; kb < issued + TW_STAGES && !abort_flag; ++kb) {
+      if (kb < TW_STAGES) continue;  // stage never used
+      int st = kb % TW_STAGES;
+      uint32_t ph = (uint32_t)(kb / TW_STAGES) & 1u;
+      if (!mbar_wait(&empty_bar[st], ph ^ 1u, &abort_flag, status)) break;
+    }
+    if (abort_flag) {  // bounded drain of the copies this CTA has in flight
+      for (int kb = issued - TW_STAGES < 0 ? 0 : issued - TW_STAGES; kb < issued; ++kb) {
+        uint32_t ph = (uint32_t)(kb / TW_STAGES) & 1u;
+        for (uint32_t i = 0; i < TC_SPIN_LIMIT && !mbar_try(&full_bar[kb % TW_STAGES], ph); ++i) {
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t idesc = idesc_bf16_128x256();
+    for (int kb = 0; kb < nk; ++kb) {
+      int st = kb % TW_STAGES;
+      uint32_t ph = (uint32_t)(kb / TW_STAGES) & 1u;
+      if (!mbar_wait(&full_bar[st], ph, &abort_flag, status)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint32_t sa = smem_u32(smem + (size_t)st * TW_STAGE_BYTES);
+      uint32_t a_hi = sa, a_lo = sa + TW_OP_BYTES, b_hi = sa + 2 * TW_OP_BYTES, b_lo = sa + 3 * TW_OP_BYTES;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint32_t dt = tmem + (uint32_t)(256 * h);
+        uint32_t aoff = (uint32_t)(h * 128 * 64);
+#pragma unroll
+        for (int k = 0; k < TW_BK / 16; ++k) {
+          uint32_t off = k * 32;
+          uint32_t first = (kb == 0 && k == 0) ? 0u : 1u;
+          umma_bf16(dt, umma_desc_sw64(a_hi + aoff + off), umma_desc_sw64(b_hi + off), idesc, first);
+          umma_bf16(dt, umma_desc_sw64(a_hi + aoff + off), umma_desc_sw64(b_lo + off), idesc, 1u);
+          umma_bf16(dt, umma_desc_sw64(a_lo + aoff + off), umma_desc_sw64(b_hi + off), idesc, 1u);
+        }
+      }
+      umma_commit_mc(&empty_bar[st], writers);
+    }
+    umma_commit(&acc_bar);
+  }
+  __syncwarp();
+  bool have = mbar_wait(&acc_bar, 0u, &abort_flag, status);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (have && !abort_flag && store) {
+    double* stg = (double*)smem + warp * (32 * 33);
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+      int64_t r0 = (int64_t)row_i + 128 * h + warp * 32;
+      int64_t gi = r0 + lane;
+      double si = (gi < M) ? rscale[gi] : 0.0;
+#pragma unroll 1
+      for (int c = 0; c < 8; ++c) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(256 * h + c * 32), v);
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) stg[lane * 33 + jj] = (double)v[jj] * si;
+        __syncwarp();
+        int64_t gj = (int64_t)row_j + c * 32 + lane;
+        double sj = (gj < M) ? rscale[gj] : 0.0;
+#pragma unroll 4
+        for (int r2 = 0; r2 < 32; ++r2) {
+          int64_t gr = r0 + r2;
+          if (gr < M && gj < M && gj <= gr) *out.at(gr, gj) = stg[r2 * 33 + lane] * sj;
+        }
+        __syncwarp();
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  cluster_sync_all();  // no CTA leaves while a peer may still write into it
+}
+
 // ---------------------------------------------------------------- host side
 PFN_cuTensorMapEncodeTiled_v12000 wl_encode_tiled() {
   static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
@@ -430,13 +729,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() { return wl_encode_tiled();
 
 // 2D view of the blocked array: inner dimension 32 (64 B rows), outer
 // dimension ntiles * nk * 256 block rows; box 32 x 256 = one 16 KB block
-static int make_map(cov_handle* h, CUtensorMap* map, void* base, int64_t rows, int64_t kp) {
+static int make_map(cov_handle* h, CUtensorMap* map, void* base, int64_t rows, int64_t kp, int box_rows = TW_BM) {
   auto fn = encode_fn();
   if (!fn) return wl_fail(h, COV_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
   int64_t ntiles = (rows + TW_BM - 1) / TW_BM;
   cuuint64_t dims[2] = {(cuuint64_t)TW_BK, (cuuint64_t)(ntiles * (kp / TW_BK) * TW_BM)};
   cuuint64_t strides[1] = {(cuuint64_t)TW_BK * 2};
-  cuuint32_t box[2] = {(cuuint32_t)TW_BK, (cuuint32_t)TW_BM};
+  cuuint32_t box[2] = {(cuuint32_t)TW_BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -466,18 +765,140 @@ static int zero_last_tile(cov_handle* h, void* base, int64_t rows, int K, cudaSt
 int wl_rows_split(cov_handle* h, int nssc, cudaStream_t s) {
   double rho = WL_RHO_CRIT0 * h->cosmo.Om;
   int Kt = h->K + nssc;
-  if (int rc = zero_last_tile(h, h->Ahi, h->M, Kt, s)) return rc;
-  if (int rc = zero_last_tile(h, h->Alo, h->M, Kt, s)) return rc;
+  int nsig = h->nl + h->ntri;
+  int rc;
+  if ((rc = wl_ensure(h, (void**)&h->Fsig, sizeof(float) * (size_t)nsig * h->K, "row signature table"))) return rc;
+  if ((rc = wl_ensure(h, (void**)&h->Esig, sizeof(int) * (size_t)nsig * h->nchi, "row signature exponents")))
+    return rc;
+  if ((rc = wl_ensure(h, (void**)&h->Msig, sizeof(double) * (size_t)nsig * h->nchi, "row signature maxima")))
+    return rc;
+  if ((rc = zero_last_tile(h, h->Ahi, h->M, Kt, s))) return rc;
+  if ((rc = zero_last_tile(h, h->Alo, h->M, Kt, s))) return rc;
   k_rows_prep<<<(h->K + 255) / 256, 256, 0, s>>>(h->nchi, h->nm, 1.0 / h->omega, rho, h->chi, h->wchi, h->m, h->om,
                                                    h->f, h->G2, h->G3, h->C2, h->C3);
-  k_rows_split<<<(unsigned)h->M, 256, 0, s>>>(h->M, h->nchi, h->nm, kpad(Kt), nssc, h->rowdesc_d, h->W, h->U, h->G2,
-                                               h->G3, h->C2, h->C3, h->wchi, h->sigw2, h->chi, h->RP3, h->RB3,
-                                               (__nv_bfloat16*)h->Ahi, (__nv_bfloat16*)h->Alo, (double*)h->Ascale);
+  WL_LAUNCH(h, "k_rows_prep");
+  k_rows_sig<<<dim3((unsigned)nsig, (unsigned)h->nchi), 128, 0, s>>>(h->nl, h->ntri, h->nchi, h->nm, h->tris_d, h->U,
+                                                                     h->G2, h->G3, h->C2, h->C3, h->Fsig, h->Esig,
+                                                                     h->Msig, 0);
+  WL_LAUNCH(h, "k_rows_sig");
+  size_t smem = (size_t)h->nchi * (2 * sizeof(double) + 2 * sizeof(float));  // <= 96 KB for N_chi <= 4096
+  static std::once_flag attr_once[WL_MAX_DEVICES];
+  static int attr_rc[WL_MAX_DEVICES];
+  if (wl_once_per_device(attr_once, attr_rc, [] {
+        return (int)cudaFuncSetAttribute(k_rows_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         4096 * (2 * sizeof(double) + 2 * sizeof(float)));
+      }) != 0)
+    return wl_fail(h, COV_ERR_CUDA, "cudaFuncSetAttribute(k_rows_split) failed");
+  k_rows_split<<<(unsigned)h->M, 256, smem, s>>>(h->M, h->nl, h->nchi, h->nm, kpad(Kt), nssc, h->rowdesc_d, h->W,
+                                                  h->Fsig, h->Esig, h->Msig, h->wchi, h->sigw2, h->chi, h->RP3,
+                                                  h->RB3, (__nv_bfloat16*)h->Ahi, (__nv_bfloat16*)h->Alo,
+                                                  (double*)h->Ascale);
   WL_LAUNCH(h, "k_rows_split");
   return COV_OK;
 }
 
+// BF16 hi/lo trispectrum rows straight from the pair signatures (no FP64
+// row array): the PT term's table T = rows rows^T in the split form.
+int wl_trows_split(cov_handle* h, cudaStream_t s) {
+  double rho = WL_RHO_CRIT0 * h->cosmo.Om;
+  int npair = h->nl * (h->nl + 1) / 2;
+  int rc;
+  if ((rc = wl_ensure(h, (void**)&h->FsigT, sizeof(float) * (size_t)npair * h->K, "pair signature table")))
+    return rc;
+  if ((rc = wl_ensure(h, (void**)&h->EsigT, sizeof(int) * (size_t)npair * h->nchi, "pair signature exponents")))
+    return rc;
+  if ((rc = wl_ensure(h, (void**)&h->MsigT, sizeof(double) * (size_t)npair * h->nchi, "pair signature maxima")))
+    return rc;
+  if ((rc = wl_ensure(h, (void**)&h->G2, sizeof(double) * h->K, "row factor table"))) return rc;
+  if ((rc = wl_ensure(h, (void**)&h->G3, sizeof(double) * h->K, "row factor table"))) return rc;
+  if ((rc = wl_ensure(h, (void**)&h->C2, sizeof(double) * h->nchi, "row factor table"))) return rc;
+  if ((rc = wl_ensure(h, (void**)&h->C3, sizeof(double) * h->nchi, "row factor table"))) return rc;
+  if ((rc = zero_last_tile(h, h->Thi, h->ntrow, h->K, s))) return rc;
+  if ((rc = zero_last_tile(h, h->Tlo, h->ntrow, h->K, s))) return rc;
+  k_rows_prep<<<(h->K + 255) / 256, 256, 0, s>>>(h->nchi, h->nm, 1.0 / h->omega, rho, h->chi, h->wchi, h->m, h->om,
+                                                   h->f, h->G2, h->G3, h->C2, h->C3);
+  WL_LAUNCH(h, "k_rows_prep");
+  k_rows_sig<<<dim3((unsigned)npair, (unsigned)h->nchi), 128, 0, s>>>(h->nl, h->ntri, h->nchi, h->nm, h->tris_d, h->U,
+                                                                      h->G2, h->G3, h->C2, h->C3, h->FsigT, h->EsigT,
+                                                                      h->MsigT, 1);
+  WL_LAUNCH(h, "k_rows_sig");
+  size_t smem = (size_t)h->nchi * (sizeof(double) + sizeof(float));
+  k_trows_split<<<(unsigned)h->ntrow, 256, smem, s>>>(h->ntrow, h->nleg, h->nt, h->nl, h->nchi, h->nm, kpad(h->K),
+                                                       sqrt(h->omega), h->W, h->FsigT, h->EsigT, h->MsigT,
+                                                       (__nv_bfloat16*)h->Thi, (__nv_bfloat16*)h->Tlo, h->Tscale);
+  WL_LAUNCH(h, "k_trows_split");
+  return COV_OK;
+}
+
 // C (lower, FP64) = (hi + lo)(hi + lo)^T scaled, without the lo lo^T term
+// Launch orders, cached per (tile-row range, kind).  kind 0: the lower tiles
+// (ti, tj), tj <= ti, of tile rows [t0, t1), row by row.  kind 1: the 2 x 2
+// super-tiles (top-left tile (t0 + 2 I, 2 J)) that hold at least one of them,
+// row by row; the cluster kernel computes all four tiles of each and stores
+// the ones inside the band's lower part.
+int wl_tile_order(cov_handle* h, int kind, int64_t t0, int64_t t1, const int2** tiles, int64_t* n) {
+  for (auto& c : h->tile_cache)
+    if (c.p && c.kind == kind && c.t0 == t0 && c.t1 == t1) {
+      *tiles = c.p;
+      *n = c.n;
+      return COV_OK;
+    }
+  std::vector<int2> v;
+  if (kind == 0) {
+    for (int64_t ti = t0; ti < t1; ++ti)
+      for (int64_t tj = 0; tj <= ti; ++tj) v.push_back(make_int2((int)ti, (int)tj));
+  } else {
+    for (int64_t i0 = t0; i0 < t1; i0 += 2) {
+      int64_t last = std::min<int64_t>(i0 + 1, t1 - 1);  // last tile row of this super-row inside the band
+      for (int64_t j0 = 0; j0 <= last; j0 += 2) v.push_back(make_int2((int)i0, (int)j0));
+    }
+  }
+  auto& c = h->tile_cache[h->tile_cache_next];
+  h->tile_cache_next = (h->tile_cache_next + 1) % WL_TILE_CACHE;
+  if (c.p && c.cap < v.size()) {
+    cudaFree(c.p);
+    h->allocated -= sizeof(int2) * c.cap;
+    c.p = nullptr;
+  }
+  if (!c.p) {
+    WL_CHECK(h, cudaMalloc(&c.p, sizeof(int2) * v.size()));
+    c.cap = v.size();
+    h->allocated += sizeof(int2) * c.cap;
+  }
+  WL_CHECK(h, cudaMemcpy(c.p, v.data(), sizeof(int2) * v.size(), cudaMemcpyHostToDevice));
+  c.kind = kind;
+  c.t0 = t0;
+  c.t1 = t1;
+  c.n = (int64_t)v.size();
+  *tiles = c.p;
+  *n = c.n;
+  return COV_OK;
+}
+
+// Whether 4-CTA clusters of the multicast kernel can be resident on this device.
+static int mc_clusters_ok() {
+  static std::once_flag once[WL_MAX_DEVICES];
+  static int ok[WL_MAX_DEVICES];
+  int d = 0;
+  cudaGetDevice(&d);
+  if (d < 0 || d >= WL_MAX_DEVICES) return 0;
+  std::call_once(once[d], [&] {
+    ok[d] = 0;
+    if (cudaFuncSetAttribute(k_syrk_tc256_mc, cudaFuncAttributeMaxDynamicSharedMemorySize, TW_SMEM) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(4);
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = TW_SMEM;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, (void*)k_syrk_tc256_mc, &cfg) == cudaSuccess && n > 0) ok[d] = n;
+    cudaGetLastError();
+  });
+  return ok[d];
+}
+
 int wl_syrk_tc_rows(cov_handle* h, const void* hi, const void* lo, const double* rscale, int64_t rows, int Kp,
                     OutMap out, cudaStream_t s, int64_t row1) {
   CUtensorMap mhi, mlo;
@@ -495,10 +916,21 @@ int wl_syrk_tc_rows(cov_handle* h, const void* hi, const void* lo, const double*
   // tile rows of the band [out.row0, row1); out.row0 is a multiple of 256
   if (row1 < 0 || row1 > rows) row1 = rows;
   int64_t t0 = out.row0 / TW_BM, t1 = (row1 + TW_BM - 1) / TW_BM;
-  int64_t off = t0 * (t0 + 1) / 2;
-  int64_t nblk = t1 * (t1 + 1) / 2 - off;
-  k_syrk_tc256<<<(unsigned)nblk, 128, TW_SMEM, s>>>(mhi, mlo, rows, Kp / TW_BK, rscale, out, h->tc_status, off);
-  WL_LAUNCH(h, "k_syrk_tc256");
+  const int2* tiles = nullptr;
+  int64_t nblk = 0;
+  if (mc_clusters_ok()) {
+    CUtensorMap chi, clo;
+    if ((rc = make_map(h, &chi, (void*)hi, rows, Kp, MC_BOX_ROWS))) return rc;
+    if ((rc = make_map(h, &clo, (void*)lo, rows, Kp, MC_BOX_ROWS))) return rc;
+    if ((rc = wl_tile_order(h, 1, t0, t1, &tiles, &nblk))) return rc;
+    k_syrk_tc256_mc<<<(unsigned)(4 * nblk), 128, TW_SMEM, s>>>(chi, clo, rows, Kp / TW_BK, rscale, out,
+                                                                h->tc_status, tiles, t1);
+    WL_LAUNCH(h, "k_syrk_tc256_mc");
+  } else {
+    if ((rc = wl_tile_order(h, 0, t0, t1, &tiles, &nblk))) return rc;
+    k_syrk_tc256<<<(unsigned)nblk, 128, TW_SMEM, s>>>(mhi, mlo, rows, Kp / TW_BK, rscale, out, h->tc_status, tiles);
+    WL_LAUNCH(h, "k_syrk_tc256");
+  }
   int st = 0;
   WL_CHECK(h, cudaMemcpyAsync(&st, h->tc_status, sizeof(int), cudaMemcpyDeviceToHost, s));
   WL_CHECK(h, cudaStreamSynchronize(s));
@@ -510,11 +942,3 @@ int wl_syrk_tc(cov_handle* h, int nssc, OutMap out, cudaStream_t s, int64_t row1
   return wl_syrk_tc_rows(h, h->Ahi, h->Alo, h->Ascale, h->M, kpad(h->K + nssc), out, s, row1);
 }
 
-int wl_split_rows(cov_handle* h, const double* X, int64_t rows, int K, void* hi, void* lo, double* rscale,
-                  cudaStream_t s) {
-  if (int rc = zero_last_tile(h, hi, rows, K, s)) return rc;
-  if (int rc = zero_last_tile(h, lo, rows, K, s)) return rc;
-  k_split_rows<<<(unsigned)rows, 256, 0, s>>>(X, rows, K, kpad(K), (__nv_bfloat16*)hi, (__nv_bfloat16*)lo, rscale);
-  WL_LAUNCH(h, "k_split_rows");
-  return COV_OK;
-}

@@ -36,8 +36,16 @@ COV_LAYOUT_ROWS = 0
 COV_LAYOUT_TILES = 1
 
 EXPORTED = ["cov_init", "cov_update", "cov_layout", "cov_counts", "cov_spectra", "cov_assemble", "cov_snr",
-            "cov_assemble_band", "cov_table", "cov_profile", "cov_stage_times", "cov_stage_name", "cov_snr_noalloc", "cov_last_error",
-            "cov_free"]
+            "cov_assemble_band", "cov_table", "cov_profile", "cov_stage_times", "cov_stage_name", "cov_snr_noalloc",
+            "cov_last_error", "cov_free", "cov_server_create", "cov_server_submit", "cov_server_wait",
+            "cov_server_error", "cov_server_stats_get", "cov_server_clock", "cov_request_footprint",
+            "cov_server_free"]
+
+COV_REQ_QUEUED = 0
+COV_REQ_RUNNING = 1
+COV_REQ_DONE = 2
+COV_REQ_FAILED = 3
+COV_REQ_REJECTED = 4
 COV_NOALLOC_MAX_M = 2047
 N_STAGES = 13
 HAS_SPLIT_BF16 = True
@@ -60,6 +68,27 @@ class cov_bins(C.Structure):
 
 class cov_opts(C.Structure):
     _fields_ = [("device", C.c_int), ("hbm_budget", C.c_size_t)]
+
+
+class cov_server_opts(C.Structure):
+    _fields_ = [("device", C.c_int), ("n_slots", C.c_int), ("hbm_budget", C.c_size_t), ("precision", C.c_int),
+                ("terms", C.c_uint), ("max_bypass", C.c_int), ("dry_run_us", C.c_int)]
+
+
+class cov_request(C.Structure):
+    _fields_ = [("cosmo", cov_cosmology), ("nz", cov_nz), ("bins", cov_bins)]
+
+
+class cov_request_info(C.Structure):
+    _fields_ = [("state", C.c_int), ("rc", C.c_int), ("M", C.c_int64), ("n_ell", C.c_int), ("slot", C.c_int),
+                ("reused", C.c_int), ("footprint", C.c_size_t), ("t_submit", C.c_double), ("t_start", C.c_double),
+                ("t_done", C.c_double)]
+
+
+class cov_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("done", C.c_int64), ("failed", C.c_int64), ("rejected", C.c_int64),
+                ("reserved", C.c_size_t), ("peak_reserved", C.c_size_t), ("budget", C.c_size_t),
+                ("max_running", C.c_int)]
 
 
 _lib = None
@@ -93,8 +122,21 @@ def lib():
         L.cov_last_error.restype = C.c_char_p
         L.cov_free.argtypes = [P]
         L.cov_free.restype = None
+        L.cov_server_create.argtypes = [C.POINTER(cov_server_opts), C.POINTER(P)]
+        L.cov_server_submit.argtypes = [P, C.POINTER(cov_request), C.POINTER(i64)]
+        L.cov_server_wait.argtypes = [P, i64, C.c_double, C.POINTER(cov_request_info), P]
+        L.cov_server_error.argtypes = [P, i64]
+        L.cov_server_error.restype = C.c_char_p
+        L.cov_server_stats_get.argtypes = [P, C.POINTER(cov_server_stats)]
+        L.cov_server_clock.argtypes = [P]
+        L.cov_server_clock.restype = C.c_double
+        L.cov_request_footprint.argtypes = [C.POINTER(cov_request), C.c_int, C.c_uint, C.POINTER(i64),
+                                            C.POINTER(C.c_size_t)]
+        L.cov_server_free.argtypes = [P]
+        L.cov_server_free.restype = None
         for n in EXPORTED:
-            if n not in ("cov_last_error", "cov_free", "cov_stage_name"):
+            if n not in ("cov_last_error", "cov_free", "cov_stage_name", "cov_server_error", "cov_server_clock",
+                         "cov_server_free"):
                 getattr(L, n).restype = C.c_int
         _lib = L
     return _lib

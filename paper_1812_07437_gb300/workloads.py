@@ -10,6 +10,11 @@ cosmology and binning of the benchmark configurations:
   ell bins in [10, 5000], N_chi = 128, N_M = 96, every covariance term.
 * ``cfg3_10bin`` 10 equipopulated bins (same n(z) and photo-z), 20 log ell
   bins in [10, 5000], N_chi = 256, N_M = 128, every term.
+* ``cfg3_5bin`` / ``cfg3_4bin`` the 10-bin binning and quadrature (20 ell
+  bins, N_chi = 256, N_M = 128, K = 32768) with 5 (M = 24400) or 4
+  (M = 12944) tomographic bins: the reduced 10-bin configuration whose dense
+  square fits (S/N of the split form against the FP64 form), and the
+  few-GB case on which the 10-bin contraction is profiled.
 * ``tiny_*`` / ``mid_*`` small cases that the oracle finishes in seconds but
   that still span several kernel tiles and a ragged tail.
 
@@ -47,6 +52,8 @@ WORKLOADS = {
     "cfg1_1bin": _wl("cfg1_1bin", 1, 0.0, 8, 20.0, 3000.0, 64, 64, TERM_G | TERM_1H),
     "cfg2_5bin": _wl("cfg2_5bin", 5, 0.05, 12, 10.0, 5000.0, 128, 96, TERMS_ALL),
     "cfg3_10bin": _wl("cfg3_10bin", 10, 0.05, 20, 10.0, 5000.0, 256, 128, TERMS_ALL),
+    "cfg3_5bin": _wl("cfg3_5bin", 5, 0.05, 20, 10.0, 5000.0, 256, 128, TERMS_ALL),
+    "cfg3_4bin": _wl("cfg3_4bin", 4, 0.05, 20, 10.0, 5000.0, 256, 128, TERMS_ALL),
     # small cases for element-by-element parity of whole matrices
     "tiny_2bin": _wl("tiny_2bin", 2, 0.05, 5, 100.0, 800.0, 16, 12, TERMS_ALL),
     "mid_2bin": _wl("mid_2bin", 2, 0.0, 8, 20.0, 3000.0, 40, 36, TERMS_ALL),
@@ -63,3 +70,24 @@ def get(name, **overrides):
         else:
             wl[key] = val
     return wl
+
+
+def serving_requests(n, rate_hz, seed=2024, n_chi=128, n_mass=96):
+    """A seeded stream of survey set-ups for the serving loop: Poisson
+    arrivals at rate_hz; tomographic bins uniform in 1..10; ell bins uniform
+    in 8..24 on [10, 5000]; each cosmological parameter uniform within +-5% of
+    the fiducial.  Returns [(arrival time in s, workload dict)].  The
+    quadrature (N_chi, N_M) is that of cfg2_5bin unless given."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, n))
+    out = []
+    for k in range(n):
+        nt = int(rng.integers(1, 11))
+        nl = int(rng.integers(8, 25))
+        cos = {p: v * (1.0 + rng.uniform(-0.05, 0.05)) for p, v in FIDUCIAL.items() if p != "Tcmb"}
+        cos["Tcmb"] = FIDUCIAL["Tcmb"]
+        wl = _wl(f"serve_{k}", nt, 0.05, nl, 10.0, 5000.0, n_chi, n_mass, TERMS_ALL)
+        wl["cosmology"] = cos
+        out.append((float(t[k]), wl))
+    return out

@@ -27,6 +27,7 @@ from paper_1812_07437_gb300 import workloads  # noqa: E402
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.join(HERE, "golden"))
 import make_counts  # noqa: E402
+import make_snr  # noqa: E402
 
 TOL_ELEM = 1e-4
 TOL_SNR = 1e-3
@@ -122,3 +123,44 @@ def test_cfg2_split_bf16_matches_fp64_form(cfg2):
         s64 = h.snr(C64, D, which)
         ss = h.snr(Cs, D, which)
         assert np.max(np.abs(ss / s64 - 1)) <= TOL_SNR
+
+
+WHICH = (("P", N.COV_WHICH_P), ("B", N.COV_WHICH_B), ("J", N.COV_WHICH_JOINT))
+
+
+def _snr_rel(got, ref):
+    m = np.isfinite(ref)
+    assert np.array_equal(m, np.isfinite(got))
+    return float(np.max(np.abs(got[m] / ref[m] - 1)))
+
+
+def test_cfg2_snr_matches_stored_oracle(cfg2):
+    """Cumulative S/N of cfg2 against the oracle's own (full FP64 covariance,
+    scipy Cholesky; tests/golden/make_snr.py): FP64 form to 1e-10, split-BF16
+    form to 1e-3."""
+    h, r, C64, D = cfg2
+    ref = make_snr.load("cfg2_5bin")
+    Cs, _ = _cov(h, N.COV_TERMS_ALL, N.COV_SPLIT_BF16)
+    for tag, w in WHICH:
+        assert _snr_rel(h.snr(C64, D, w), ref[tag]) <= 1e-10, tag
+        assert _snr_rel(h.snr(Cs, D, w), ref[tag]) <= TOL_SNR, tag
+
+
+@pytest.mark.skipif(not os.path.exists(os.path.join(HERE, "golden", "snr_cfg3_5bin.txt")),
+                    reason="oracle S/N of cfg3_5bin not written")
+def test_cfg3_5bin_snr_matches_stored_oracle():
+    """The 10-bin quadrature and binning with 5 tomographic bins (M = 24400),
+    the largest configuration whose full oracle S/N can be computed on the
+    host: FP64 form to 1e-10, split-BF16 form to 1e-3."""
+    from paper_1812_07437_gb300.handle import Handle
+    h = Handle(workloads.get("cfg3_5bin"))
+    ref = make_snr.load("cfg3_5bin")
+    C, D = _cov(h, N.COV_TERMS_ALL, N.COV_FP64)
+    s64 = [h.snr(C, D, w) for _, w in WHICH]
+    h.assemble(C, N.COV_TERMS_ALL, N.COV_SPLIT_BF16)
+    torch.cuda.synchronize()
+    ss = [h.snr(C, D, w) for _, w in WHICH]
+    for k, (tag, _) in enumerate(WHICH):
+        assert _snr_rel(s64[k], ref[tag]) <= 1e-10, tag
+        assert _snr_rel(ss[k], ref[tag]) <= TOL_SNR, tag
+    h.close()
