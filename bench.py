@@ -46,9 +46,12 @@ def parse():
     p.add_argument("--snr-workload", default="cfg2_5bin")
     p.add_argument("--no-snr-run", action="store_true")
     p.add_argument("--no-serve", action="store_true")
-    p.add_argument("--serve-requests", type=int, default=64)
+    p.add_argument("--snr-10bin", action="store_true",
+                   help="also time the cumulative S/N of the workload itself, in place on its packed tiles "
+                        "(one extra assembly and FP64-accurate Cholesky per row set; minutes at 10 bins)")
+    p.add_argument("--serve-requests", type=int, default=24)
     p.add_argument("--serve-rate", type=float, default=200.0)
-    p.add_argument("--serve-budget-gb", type=float, default=96.0)
+    p.add_argument("--serve-budget-gb", type=float, default=64.0)
     p.add_argument("--serve-slots", type=int, default=4)
     p.add_argument("--precision", default="auto", choices=["auto", "fp64", "split_bf16"])
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -242,6 +245,24 @@ def timed(stream, fn, steps, h, world):
     return e0.elapsed_time(e1), stages, out
 
 
+# DRAM bytes (read + write) of one full-size contraction launch, from a one-pass
+# ncu capture (profiles/launches_cfg3_10bin.md), valid only while the kernel
+# source it was taken on is unchanged (sha256 of csrc/syrk_tc.cu).
+TRAFFIC = {
+    # workload: (bytes per launch, sha256 of syrk_tc.cu at capture)
+}
+
+
+def measured_traffic(workload):
+    import hashlib
+    ent = TRAFFIC.get(workload)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_1812_07437_gb300", "csrc", "syrk_tc.cu")
+    with open(src, "rb") as fh:
+        return ent[0] if hashlib.sha256(fh.read()).hexdigest() == ent[1] else None
+
+
 def contraction_roofline(stages, elements, K, prec, N, long_kernel):
     """Roofline of the 1-halo (chi, M) contraction, the kernel the metric is built on."""
     syrk_ms, syrk_calls = stages["syrk_1h"]
@@ -257,7 +278,7 @@ def contraction_roofline(stages, elements, K, prec, N, long_kernel):
     peak = peaks[key]
     issued = 3.0 * flops / (avg_ms / 1e3) / 1e12
     return {"bound": "tensor", "achieved": issued, "peak": peak, "unit": "TFLOP/s", "frac": issued / peak,
-            "traffic": None, "kernel": "k_syrk_tc256 (tcgen05 split-BF16 1-halo + SSC contraction)",
+            "traffic": None, "kernel": "k_syrk_tc256_mc (tcgen05 split-BF16 1-halo + SSC contraction, 2x2 clusters)",
             "launch_ms": avg_ms, "algorithmic_tflops": achieved,
             "peak_source": f"MEASURED_PEAKS.json {key}, of measured"}
 
@@ -330,6 +351,46 @@ def serving_run(prec, n_req, rate, budget_gb, slots, device, seed=2024):
             "peak_reserved_gb": st["peak_reserved"] / 1e9, "budget_gb": st["budget"] / 1e9, "slots": slots}
 
 
+def snr_tiles_run(wl, prec, device, row_sets):
+    """Cumulative S/N of the workload's own data vector without a dense square:
+    a handle in cumulative row order assembles its lower-packed tiles (plus one
+    row for D) and cov_snr_tiles factorises them in place."""
+    import numpy as np
+    import torch
+    from paper_1812_07437_gb300 import native as N
+    from paper_1812_07437_gb300.handle import Handle, packed_tiles
+    dev = torch.device("cuda", device)
+    out = {}
+    for name, rows in row_sets:
+        h = Handle(wl, device=device, rows=rows, order=N.COV_ORDER_CUMULATIVE)
+        D = torch.zeros(h.M, dtype=torch.float64, device=dev)
+        Ct = torch.empty(packed_tiles(h.M + 1) * 65536, dtype=torch.float64, device=dev)
+        st = torch.cuda.Stream(device=dev)
+        with torch.cuda.stream(st):
+            torch.cuda.synchronize()
+            h.profile(True)
+            h.stage_times()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(st)
+            h.spectra(D, st)
+            h.assemble_band(0, h.M, Ct, N.COV_LAYOUT_TILES, N.COV_TERMS_ALL, prec, st)
+            e1.record(st)
+            snr = h.snr_tiles(Ct, D, st)
+            e2.record(st)
+            torch.cuda.synchronize()
+            stg = h.stage_times()
+            h.profile(False)
+        chol_ms = stg["snr_cholesky"][0]
+        out[name] = {"M": h.M, "assemble_ms": e0.elapsed_time(e1), "snr_ms": e1.elapsed_time(e2),
+                     "cholesky_ms": chol_ms,
+                     "cholesky_fp64_equivalent_tflops": h.M ** 3 / 3.0 / (chol_ms / 1e3) / 1e12,
+                     "snr": [float(x) for x in snr], "snr_max": float(np.nanmax(snr))}
+        del Ct, D
+        h.close()
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -400,8 +461,10 @@ def run_ours(args):
             dbuf = [torch.empty(nmax, dtype=torch.float64, device=dev) for _ in range(2)]
             hbuf = [torch.empty(nmax, dtype=torch.float64, pin_memory=True) for _ in range(2)]
             Dh = torch.empty(M, dtype=torch.float64, pin_memory=True)
-            copy = torch.cuda.Stream(device=dev)
-            done = [torch.cuda.Event() for _ in range(2)]
+            # each band leaves in four chunks on four copy streams (several copy engines)
+            NC = 4
+            copies = [torch.cuda.Stream(device=dev) for _ in range(NC)]
+            done = [[torch.cuda.Event() for _ in range(NC)] for _ in range(2)]
             ready = [torch.cuda.Event() for _ in range(2)]
             d2h = 0
 
@@ -414,15 +477,19 @@ def run_ours(args):
                 for k, (a, b) in enumerate(bands):
                     n = (packed_tiles(b) - packed_tiles(a)) * TILE * TILE
                     s = k % 2
-                    stream.wait_event(done[s])
+                    for e in done[s]:
+                        stream.wait_event(e)
                     h.assemble_band(a, b - a, dbuf[s][:n], N.COV_LAYOUT_TILES, N.COV_TERMS_ALL, prec, stream)
                     ready[s].record(stream)
-                    copy.wait_event(ready[s])
-                    with torch.cuda.stream(copy):
-                        hbuf[s][:n].copy_(dbuf[s][:n], non_blocking=True)
-                    done[s].record(copy)
+                    for c, cs in enumerate(copies):
+                        lo_, hi_ = c * n // NC, (c + 1) * n // NC
+                        cs.wait_event(ready[s])
+                        with torch.cuda.stream(cs):
+                            hbuf[s][lo_:hi_].copy_(dbuf[s][lo_:hi_], non_blocking=True)
+                        done[s][c].record(cs)
                     d2h += n * 8
-                copy.synchronize()
+                for cs in copies:
+                    cs.synchronize()
                 stream.synchronize()
 
             e2e_step()
@@ -458,8 +525,8 @@ def run_ours(args):
         e2e = {"value": world * elements / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 56,
                "d2h_bytes_per_step": d2h,
                "how": f"cov_update + cov_spectra, then cov_assemble_band over {len(bands)} bands of about equal "
-                      "size into two device buffers, each band copied to pinned host memory on a second stream "
-                      "while the next one is assembled"}
+                      "size into two device buffers, each band copied to pinned host memory in four chunks on "
+                      "four copy streams while the next one is assembled"}
         snr_sizes = []
         cfg = {"layout": "lower-packed 256x256 tiles, resident (%.1f GB)" % (Ct.numel() * 8 / 1e9)}
     else:
@@ -501,6 +568,9 @@ def run_ours(args):
     ms_step = float(t.item())
     value = world * elements / (ms_step / 1e3)
     roof = contraction_roofline(stages, elements, Kc, prec, N, long_kernel=packed)
+    if prec != N.COV_FP64:
+        roof["traffic"] = measured_traffic(args.workload)
+        roof["algorithmic_bytes"] = elements * 8 + 2 * 2 * M * Kc  # tiles written once, hi/lo operands read once
     if snr_sizes:
         chol_ms = stages["snr_cholesky"][0] / max(args.steps, 1)
         roof["cholesky"] = {"stage_ms_per_step": chol_ms,
@@ -548,12 +618,14 @@ def run_ours(args):
             "snr_rel_err_vs_fp64_form": r2.get("snr_rel_err_vs_fp64_form"),
             "snr_joint_max": float(np.nanmax(r2["snr"][2]))}
         h2.close()
+    if args.snr_10bin and rank == 0 and world == 1:
+        out["snr_tiles"] = snr_tiles_run(workloads.get(args.workload), prec, local,
+                                         [("joint", N.COV_ROWS_JOINT), ("B", N.COV_ROWS_B), ("P", N.COV_ROWS_P)])
     if not args.no_serve and packed and rank == 0 and world == 1:
         sv = serving_run(prec, args.serve_requests, args.serve_rate, args.serve_budget_gb, args.serve_slots, local)
         # the same mix offered at about half the rate the first run achieved
         rate2 = max(0.05, 0.5 * sv["achieved_rate_hz"])
-        sv2 = serving_run(prec, max(8, args.serve_requests // 4), rate2, args.serve_budget_gb, args.serve_slots,
-                          local, seed=2025)
+        sv2 = serving_run(prec, 8, rate2, args.serve_budget_gb, args.serve_slots, local, seed=2025)
         out["serving"] = {"workload": "Poisson stream, n_t uniform 1..10, n_ell uniform 8..24 on [10, 5000], "
                                       "cosmology within +-5% of the fiducial, N_chi=128, N_M=96, every term, "
                                       "covariance + 3 cumulative S/N per request",

@@ -79,9 +79,21 @@ typedef struct {
   double m_min, m_max, k_max;
 } cov_bins;
 
+/* Row set and row order of the data vector (Sec. 5). */
+#define COV_ROWS_JOINT 0      /* P rows and B rows                                    */
+#define COV_ROWS_P 1          /* power-spectrum rows only                             */
+#define COV_ROWS_B 2          /* bispectrum rows only                                 */
+#define COV_ORDER_NATURAL 0   /* P rows (ell bin slowest, i <= j), then B rows         */
+                              /* (triangle: c slowest, then a, b; tomography fastest)  */
+#define COV_ORDER_CUMULATIVE 1 /* by largest ell bin c: the P rows of bin c, then the */
+                               /* B rows whose largest bin is c, for c = 0, 1, ...    */
+
 typedef struct {
   int device;        /* CUDA device ordinal                                  */
   size_t hbm_budget; /* bytes the handle may allocate; 0 = no limit          */
+  int rows;          /* COV_ROWS_*                                           */
+  int order;         /* COV_ORDER_*: the cumulative order makes every        */
+                     /* cumulative S/N selection a leading block (cov_snr_tiles) */
 } cov_opts;
 
 typedef struct cov_handle cov_handle;
@@ -148,6 +160,21 @@ int cov_assemble(cov_handle* h, double* d_C, int64_t ldc, unsigned terms, int pr
  * cov_assemble computes for its rows.  Requires a preceding cov_spectra. */
 int cov_assemble_band(cov_handle* h, int64_t row0, int64_t nrows, double* d_C, int64_t ldc, int layout,
                       unsigned terms, int precision, void* stream);
+
+/* Cumulative signal-to-noise of the handle's whole row set (Eqs. SNprim,
+ * eq:SN) in place on its lower-packed covariance: the form for data vectors
+ * whose dense square (and a scaled copy of it) does not fit.  Requires a
+ * handle created with order COV_ORDER_CUMULATIVE (the rows of every
+ * cumulative selection then form a leading block) and d_Ct (device) holding
+ * the lower-packed 256 x 256 tiles of rows 0..M, i.e. the tiles of M + 1 rows
+ * ((t (t + 1) / 2) * 65536 doubles, t = M / 256 + 1), as written by
+ * cov_assemble_band(h, 0, M, d_Ct, 0, COV_LAYOUT_TILES, ...).  d_Ct is
+ * overwritten: Jacobi scaling, D' = d^-1/2 D (d_D: device, M) as row M, and
+ * the same blocked FP64-accurate Cholesky as cov_snr; h_snr (host, n_ell)
+ * receives S/N for ell_max = bin 0 .. n_ell - 1 of the handle's rows (P, B or
+ * joint by the handle's row set).  COV_ERR_NOT_PD / COV_ERR_TIMEOUT as for
+ * cov_snr; COV_ERR_INVALID for a handle not in cumulative order. */
+int cov_snr_tiles(cov_handle* h, double* d_Ct, const double* d_D, double* h_snr, void* stream);
 
 /* Cumulative signal-to-noise (Eqs. SNprim, eq:SN): h_snr[c] (host, n_ell
  * values) = sqrt(D^T C^-1 D) over the selected entries whose largest ell bin

@@ -117,23 +117,46 @@ static int plan(cov_handle* h) {
           h->tris.push_back(c);
         }
   h->ntri = (int)(h->tris.size() / 3);
-  // data-vector rows
+  // data-vector rows: P rows of bin b (i <= j), B rows of triangle t (the
+  // tomographic triples of its bins); natural order P then B, or cumulative
+  // order by largest ell bin (P rows of bin c, then the B rows of the
+  // triangles whose largest bin is c: those are contiguous, c being slowest)
   h->rowdesc.clear();
-  for (int bb = 0; bb < h->nl; ++bb)
+  const bool wantP = h->row_set != COV_ROWS_B, wantB = h->row_set != COV_ROWS_P;
+  std::vector<int> tt;
+  auto emitP = [&](int bb) {
     for (int i = 0; i < h->nt; ++i)
       for (int j = i; j < h->nt; ++j) {
         int32_t d[8] = {0, bb, bb, bb, i, j, -1, bb};
         h->rowdesc.insert(h->rowdesc.end(), d, d + 8);
       }
-  h->nP = (int64_t)h->rowdesc.size() / 8;
-  std::vector<int> tt;
-  for (int t = 0; t < h->ntri; ++t) {
+  };
+  auto emitB = [&](int t) {
     int a = h->tris[3 * t], bb = h->tris[3 * t + 1], c = h->tris[3 * t + 2];
     tomo_triples(a, bb, c, h->nt, tt);
     for (size_t k = 0; k < tt.size(); k += 3) {
       int32_t d[8] = {1, a, bb, c, tt[k], tt[k + 1], tt[k + 2], t};
       h->rowdesc.insert(h->rowdesc.end(), d, d + 8);
     }
+  };
+  h->nP = 0;
+  if (h->row_order == COV_ORDER_CUMULATIVE) {
+    for (int c = 0; c < h->nl; ++c) {
+      if (wantP) {
+        size_t before = h->rowdesc.size();
+        emitP(c);
+        h->nP += (int64_t)(h->rowdesc.size() - before) / 8;
+      }
+      if (wantB)
+        for (int t = 0; t < h->ntri; ++t)
+          if (h->tris[3 * t + 2] == c) emitB(t);
+    }
+  } else {
+    if (wantP)
+      for (int bb = 0; bb < h->nl; ++bb) emitP(bb);
+    h->nP = (int64_t)h->rowdesc.size() / 8;
+    if (wantB)
+      for (int t = 0; t < h->ntri; ++t) emitB(t);
   }
   h->M = (int64_t)h->rowdesc.size() / 8;
   h->nB = h->M - h->nP;
@@ -193,8 +216,7 @@ static void free_all(cov_handle* h) {
                   h->Alo, h->Ascale, h->G2, h->G3, h->C2, h->C3, h->tc_status, h->Thi, h->Tlo, h->Tscale, h->Trows, h->Tmat, h->Srows, h->Fsig, h->Esig, h->Msig, h->FsigT, h->EsigT, h->MsigT, h->invN, h->omN, h->work, h->perm, h->chol_scratch, h->chol_status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  for (auto& c : h->tile_cache)
-    if (c.p) cudaFree(c.p);
+  if (h->tile_ring) cudaFree(h->tile_ring);
 }
 
 // Device tables that cov_init allocates for a planned handle (pointer, bytes).
@@ -264,8 +286,8 @@ int wl_request_bytes(const cov_nz* nz, const cov_bins* bins, int precision, unsi
            (size_t)h.nl * (h.nl + 1) / 2 * (K * 4 + nchi * 12);   // BF16 rows, pair signatures
   }
   b += (M + 1) * (M + 1) * 8 + 2 * ((wl_chol_tc_bytes((int64_t)M + 1) + 255) / 256 * 256) + M * 4;
-  size_t t = (M + 255) / 256;
-  b += WL_TILE_CACHE * (t * (t + 1) / 2) * 8;                    // launch orders
+  size_t t = (std::max(M, nt) + 255) / 256 + 1;
+  b += WL_TILE_CACHE * (t * (t + 1) / 2) * 8;                    // launch-order ring
   b += (size_t)64 << 20;                                         // small buffers, allocation granularity
   *M_out = h.M;
   *bytes = b;
@@ -288,6 +310,13 @@ extern "C" int cov_init(const cov_cosmology* cosmo, const cov_nz* nz, const cov_
   h->bins = *bins;
   h->device = opts ? opts->device : 0;
   h->budget = opts ? opts->hbm_budget : 0;
+  h->row_set = opts ? opts->rows : COV_ROWS_JOINT;
+  h->row_order = opts ? opts->order : COV_ORDER_NATURAL;
+  if (h->row_set < 0 || h->row_set > 2 || h->row_order < 0 || h->row_order > 1) {
+    g_init_err = "invalid row set or row order";
+    delete h;
+    return COV_ERR_INVALID;
+  }
   int rc;
   cudaError_t e = cudaSetDevice(h->device);
   if (e != cudaSuccess) {
@@ -408,6 +437,14 @@ extern "C" int cov_assemble_band(cov_handle* h, int64_t row0, int64_t nrows, dou
   if (!h->spectra_ready) return wl_fail(h, COV_ERR_INVALID, "cov_spectra must run before cov_assemble_band");
   OutMap out = layout == COV_LAYOUT_TILES ? out_tiles(d_C, row0) : out_rows(d_C, ldc, row0);
   return wl_assemble_band(h, row0, nrows, out, terms, precision, (cudaStream_t)stream);
+}
+
+extern "C" int cov_snr_tiles(cov_handle* h, double* d_Ct, const double* d_D, double* h_snr, void* stream) {
+  if (!h) return COV_ERR_INVALID;
+  if (!d_Ct || !d_D || !h_snr) return wl_fail(h, COV_ERR_INVALID, "cov_snr_tiles: null buffer");
+  if (h->row_order != COV_ORDER_CUMULATIVE)
+    return wl_fail(h, COV_ERR_INVALID, "cov_snr_tiles needs a handle created with COV_ORDER_CUMULATIVE");
+  return wl_snr_tiles(h, d_Ct, d_D, h_snr, (cudaStream_t)stream);
 }
 
 extern "C" int cov_snr(cov_handle* h, const double* d_C, int64_t ldc, const double* d_D, int which, double* h_snr,

@@ -386,6 +386,11 @@ static int prepare_operands(cov_handle* h, unsigned terms, int precision, cudaSt
   return COV_OK;
 }
 
+// Band assembly.  In the split form the band is cut into sub-bands of about
+// equal tile counts; the contraction of sub-band k+1 (main stream) runs while
+// the per-element products of sub-band k (side stream) are added, so the
+// gather's FP64 work and read-modify-write traffic hide under the tensor-core
+// kernel, which leaves most of each SM's issue slots and HBM bandwidth free.
 int wl_assemble_band(cov_handle* h, int64_t row0, int64_t nrows, OutMap out, unsigned terms, int precision,
                      cudaStream_t s) {
   int rc;
@@ -395,28 +400,62 @@ int wl_assemble_band(cov_handle* h, int64_t row0, int64_t nrows, OutMap out, uns
     h->ops_precision = precision;
   }
   const int64_t row1 = row0 + nrows;
-  // 1. the (chi, M) contraction is the first writer of the band
-  if (terms & COV_TERM_1H) {
-    int tk = wl_stage_begin(h, ST_SYRK_1H, s);
-    if (precision == COV_FP64) {
-      if ((rc = gemm_lower_band(h, h->A, h->K, row1, h->K, 0.0, out, s))) return rc;
-    } else {
-      if ((rc = wl_syrk_tc(h, (terms & COV_TERM_SSC) ? h->nchi : 0, out, s, row1))) return rc;
-    }
-    wl_stage_end(h, tk, s);
-  }
-  // 2. per-element product terms
   GatherArgs g;
   if ((rc = gather_args(h, terms, &g, s))) return rc;
-  int64_t t0 = row0 / 32, t1 = (row1 + 31) / 32;
-  int64_t off = t0 * (t0 + 1) / 2;
+  const int acc = (terms & COV_TERM_1H) ? 1 : 0;
+  auto gather = [&](int64_t r0, int64_t r1, cudaStream_t st) {
+    int64_t t0 = r0 / 32, t1 = (r1 + 31) / 32;
+    int64_t off = t0 * (t0 + 1) / 2;
+    k_gather<<<(unsigned)(t1 * (t1 + 1) / 2 - off), dim3(32, 8), 0, st>>>(g, r1, out, acc, off);
+  };
+  if (precision != COV_FP64 && (terms & COV_TERM_1H)) {
+    const int nssc = (terms & COV_TERM_SSC) ? h->nchi : 0;
+    if (!h->side) {
+      WL_CHECK(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+      WL_CHECK(h, cudaEventCreateWithFlags(&h->ev_cols, cudaEventDisableTiming));
+      WL_CHECK(h, cudaEventCreateWithFlags(&h->ev_panel, cudaEventDisableTiming));
+    }
+    // sub-band cuts at tile rows, about equal numbers of tiles each
+    const int64_t ta = row0 / 256, tb = (row1 + 255) / 256;
+    const int nsub = (int)std::min<int64_t>(8, tb - ta);
+    std::vector<int64_t> cut{row0};
+    const double tot = 0.5 * (double)(tb * (tb + 1) - ta * (ta + 1));
+    for (int k = 1; k < nsub; ++k) {
+      double want = 0.5 * (double)(ta * (ta + 1)) + tot * k / nsub;
+      int64_t t = (int64_t)std::floor(std::sqrt(2.0 * want));
+      int64_t r = std::min(t * 256, row1);
+      if (r > cut.back()) cut.push_back(r);
+    }
+    if (cut.back() != row1) cut.push_back(row1);
+    if ((rc = wl_tc_status_reset(h, s))) return rc;
+    WL_CHECK(h, cudaEventRecord(h->ev_panel, s));  // the side stream starts after the operands
+    WL_CHECK(h, cudaStreamWaitEvent(h->side, h->ev_panel, 0));
+    int tk = wl_stage_begin(h, ST_SYRK_1H, s);
+    for (size_t k = 0; k + 1 < cut.size(); ++k) {
+      if ((rc = wl_syrk_tc_part(h, nssc, out, cut[k], cut[k + 1], s))) return rc;
+      WL_CHECK(h, cudaEventRecord(h->ev_cols, s));
+      WL_CHECK(h, cudaStreamWaitEvent(h->side, h->ev_cols, 0));
+      int tg = wl_stage_begin(h, ST_GATHER, h->side);
+      gather(cut[k], cut[k + 1], h->side);
+      WL_LAUNCH(h, "k_gather");
+      wl_stage_end(h, tg, h->side);
+    }
+    wl_stage_end(h, tk, s);
+    WL_CHECK(h, cudaEventRecord(h->ev_panel, h->side));
+    WL_CHECK(h, cudaStreamWaitEvent(s, h->ev_panel, 0));
+    return wl_tc_status_check(h, s);
+  }
+  // FP64 form, or no 1-halo term: contraction, products, super-sample term in turn
+  if (terms & COV_TERM_1H) {
+    int tk = wl_stage_begin(h, ST_SYRK_1H, s);
+    if ((rc = gemm_lower_band(h, h->A, h->K, row1, h->K, 0.0, out, s))) return rc;
+    wl_stage_end(h, tk, s);
+  }
   int tg = wl_stage_begin(h, ST_GATHER, s);
-  k_gather<<<(unsigned)(t1 * (t1 + 1) / 2 - off), dim3(32, 8), 0, s>>>(g, row1, out, (terms & COV_TERM_1H) ? 1 : 0,
-                                                                       off);
+  gather(row0, row1, s);
   WL_LAUNCH(h, "k_gather");
   wl_stage_end(h, tg, s);
-  // 3. super-sample term of the FP64 form (the split form carries it in the contraction)
-  if (precision == COV_FP64 && (terms & COV_TERM_SSC)) {
+  if ((terms & COV_TERM_SSC) && (terms & COV_TERM_1H)) {
     int tk = wl_stage_begin(h, ST_SYRK_SSC, s);
     if ((rc = gemm_lower_band(h, h->Srows, h->nchi, row1, h->nchi, 1.0, out, s))) return rc;
     wl_stage_end(h, tk, s);

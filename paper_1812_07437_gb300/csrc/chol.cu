@@ -37,7 +37,7 @@ __global__ void k_snr_pack(int64_t Ms, const int* perm, const double* C, int64_t
 
 // in-place Cholesky of the kb x kb diagonal block at (k0, k0); one block of
 // 256 threads, thread (tx, ty) owns rows ty + 16 r and columns tx + 16 c
-__global__ void k_potrf_diag(double* Wk, int64_t ldw, int64_t k0, int kb, int* status) {
+__global__ void k_potrf_diag(OutMap W, int64_t k0, int kb, int* status) {
   __shared__ double L[NB][NB + 1];
   int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
@@ -45,7 +45,7 @@ __global__ void k_potrf_diag(double* Wk, int64_t ldw, int64_t k0, int kb, int* s
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       int i = ty + 16 * r, l = tx + 16 * c;
-      L[i][l] = (i < kb && l <= i) ? Wk[(k0 + i) * ldw + k0 + l] : 0.0;
+      L[i][l] = (i < kb && l <= i) ? *W.at(k0 + i, k0 + l) : 0.0;
     }
   __shared__ double inv_sh;
   __syncthreads();
@@ -89,7 +89,7 @@ __global__ void k_potrf_diag(double* Wk, int64_t ldw, int64_t k0, int kb, int* s
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       int i = ty + 16 * r, l = tx + 16 * c;
-      if (i < kb && l <= i) Wk[(k0 + i) * ldw + k0 + l] = L[i][l];
+      if (i < kb && l <= i) *W.at(k0 + i, k0 + l) = L[i][l];
     }
 }
 
@@ -98,19 +98,19 @@ __global__ void k_potrf_diag(double* Wk, int64_t ldw, int64_t k0, int kb, int* s
 // (32 rows per block): every lane runs the whole recurrence of its own row in
 // registers, reading L11 from shared memory by broadcast, so no FP64 issue slot
 // is spent on masked lanes
-__global__ void k_trsm_rows(double* Wk, int64_t ldw, int64_t k0, int kb, int64_t r0, int64_t r1) {
+__global__ void k_trsm_rows(OutMap W, int64_t k0, int kb, int64_t r0, int64_t r1) {
   __shared__ double L[NB][NB + 1];
   __shared__ double invd[NB];
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     int i = e >> 6, l = e & 63;
-    L[i][l] = (i < kb && l <= i) ? Wk[(k0 + i) * ldw + k0 + l] : 0.0;
+    L[i][l] = (i < kb && l <= i) ? *W.at(k0 + i, k0 + l) : 0.0;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < kb; i += blockDim.x) invd[i] = 1.0 / L[i][i];
   __syncthreads();
   int64_t r = r0 + (int64_t)blockIdx.x * TRSM_ROWS + threadIdx.x;
   if (r >= r1) return;
-  double* row = Wk + r * ldw + k0;
+  double* row = W.at(r, k0);  // kb <= 64 consecutive entries (k0 is a multiple of 64)
   double x[NB];
 #pragma unroll
   for (int j = 0; j < NB; ++j) x[j] = (j < kb) ? row[j] : 0.0;
@@ -136,17 +136,115 @@ __global__ void k_trsm_rows(double* Wk, int64_t ldw, int64_t k0, int kb, int64_t
     if (j < kb) row[j] = x[j];
 }
 
-__global__ void k_snr_prefix(int64_t Ms, const double* Wk, int64_t ldw, const int64_t* cnt, int nl, double* out) {
+__global__ void k_snr_prefix(int64_t Ms, OutMap W, const int64_t* cnt, int nl, double* out) {
   __shared__ double sh[32];
   int c = blockIdx.x;
   int64_t n = cnt[c];
   double s = 0.0;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    double y = Wk[Ms * ldw + i];
+    double y = *W.at(Ms, i);
     s += y * y;
   }
   s = block_sum(s, sh);
   if (threadIdx.x == 0) out[c] = (n > 0) ? sqrt(s) : nan("");
+}
+
+// Scratch of the factorisation of Ms rows (slice buffers, status words, the
+// side stream of the look-ahead), allocated once and grown on demand.
+static int chol_scratch(cov_handle* h, int64_t Ms, size_t* one_buf) {
+  *one_buf = (wl_chol_tc_bytes(Ms + 1) + 255) / 256 * 256;
+  size_t need_sc = 2 * *one_buf;
+  if (need_sc > h->chol_scratch_n) {
+    if (h->chol_scratch) {
+      cudaFree(h->chol_scratch);
+      h->allocated -= h->chol_scratch_n;
+    }
+    h->chol_scratch = nullptr;
+    h->chol_scratch_n = 0;
+    WL_CHECK(h, cudaMalloc(&h->chol_scratch, need_sc));
+    h->chol_scratch_n = need_sc;
+    h->allocated += need_sc;
+  }
+  if (!h->chol_status) WL_CHECK(h, cudaMalloc(&h->chol_status, sizeof(int)));
+  if (!h->side) {
+    WL_CHECK(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    WL_CHECK(h, cudaEventCreateWithFlags(&h->ev_cols, cudaEventDisableTiming));
+    WL_CHECK(h, cudaEventCreateWithFlags(&h->ev_panel, cudaEventDisableTiming));
+  }
+  return COV_OK;
+}
+
+// Blocked right-looking Cholesky of the leading Ms x Ms block of the
+// workspace Wm (rows 0..Ms; row Ms carries D' along and ends up as
+// y = L^-1 D'), then (S/N)^2 for every cumulative selection as the prefix
+// sums of y^2 up to cnt[c] entries.
+static int factor_and_prefix(cov_handle* h, OutMap Wm, int64_t Ms, const std::vector<int64_t>& cnt, double* h_snr,
+                             cudaStream_t s) {
+  size_t one_buf = 0;
+  int rc;
+  if ((rc = chol_scratch(h, Ms, &one_buf))) return rc;
+  WL_CHECK(h, cudaMemsetAsync(h->chol_status, 0, sizeof(int), s));
+  int* st = nullptr;
+  int64_t* cnt_d = nullptr;
+  double* out_d = nullptr;
+  WL_CHECK(h, cudaMallocAsync(&st, sizeof(int), s));
+  WL_CHECK(h, cudaMallocAsync(&cnt_d, sizeof(int64_t) * h->nl, s));
+  WL_CHECK(h, cudaMallocAsync(&out_d, sizeof(double) * h->nl, s));
+  WL_CHECK(h, cudaMemsetAsync(st, 0, sizeof(int), s));
+  WL_CHECK(h, cudaMemcpyAsync(cnt_d, cnt.data(), sizeof(int64_t) * h->nl, cudaMemcpyHostToDevice, s));
+  int tk = wl_stage_begin(h, ST_SNR_CHOL, s);
+  // One panel of look-ahead: the trailing update of panel p first updates the
+  // 64 columns of panel p+1, then the FP64 diagonal block, panel solve and
+  // slicing of panel p+1 run on the side stream while the rest of the update
+  // of panel p runs here.
+  uint8_t* bufs[2] = {(uint8_t*)h->chol_scratch, (uint8_t*)h->chol_scratch + one_buf};
+  auto panel = [&](int64_t k0, cudaStream_t st_) -> int {
+    int kb = (int)std::min<int64_t>(NB, Ms - k0);
+    k_potrf_diag<<<1, 256, 0, st_>>>(Wm, k0, kb, st);
+    int64_t r0 = k0 + kb, r1 = Ms + 1;
+    if (r1 > r0)
+      k_trsm_rows<<<(unsigned)((r1 - r0 + TRSM_ROWS - 1) / TRSM_ROWS), TRSM_ROWS, 0, st_>>>(Wm, k0, kb, r0, r1);
+    WL_LAUNCH(h, "Cholesky panel kernels");
+    return wl_chol_slice(h, Wm, k0, kb, r0, r1, bufs[(k0 / NB) & 1], st_);
+  };
+  if ((rc = panel(0, s))) return rc;
+  for (int64_t k0 = 0; k0 < Ms; k0 += NB) {
+    int kb = (int)std::min<int64_t>(NB, Ms - k0);
+    int64_t r0 = k0 + kb, r1 = Ms + 1;
+    const void* buf = bufs[(k0 / NB) & 1];
+    if (r0 < Ms) {
+      if ((rc = wl_chol_update(h, Wm, r0, r1, buf, 0, 1, h->chol_status, s))) return rc;
+      WL_CHECK(h, cudaEventRecord(h->ev_cols, s));
+      WL_CHECK(h, cudaStreamWaitEvent(h->side, h->ev_cols, 0));
+      if ((rc = panel(r0, h->side))) return rc;
+      WL_CHECK(h, cudaEventRecord(h->ev_panel, h->side));
+      if ((rc = wl_chol_update(h, Wm, r0, r1, buf, 1, -1, h->chol_status, s))) return rc;
+      WL_CHECK(h, cudaStreamWaitEvent(s, h->ev_panel, 0));
+    } else if (r1 > r0) {
+      // only the extra D row is left below this panel
+      if ((rc = wl_chol_update(h, Wm, r0, r1, buf, 0, -1, h->chol_status, s))) return rc;
+    }
+  }
+  WL_LAUNCH(h, "Cholesky kernels");
+  wl_stage_end(h, tk, s);
+  tk = wl_stage_begin(h, ST_SNR_PREFIX, s);
+  k_snr_prefix<<<h->nl, 256, 0, s>>>(Ms, Wm, cnt_d, h->nl, out_d);
+  wl_stage_end(h, tk, s);
+  int status = 0, tstatus = 0;
+  WL_CHECK(h, cudaMemcpyAsync(h_snr, out_d, sizeof(double) * h->nl, cudaMemcpyDeviceToHost, s));
+  WL_CHECK(h, cudaMemcpyAsync(&status, st, sizeof(int), cudaMemcpyDeviceToHost, s));
+  WL_CHECK(h, cudaMemcpyAsync(&tstatus, h->chol_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  WL_CHECK(h, cudaFreeAsync(st, s));
+  WL_CHECK(h, cudaFreeAsync(cnt_d, s));
+  WL_CHECK(h, cudaFreeAsync(out_d, s));
+  WL_CHECK(h, cudaStreamSynchronize(s));
+  if (tstatus) return wl_fail(h, COV_ERR_TIMEOUT, "Cholesky trailing update: a bounded mbarrier wait expired");
+  if (status) return wl_fail(h, COV_ERR_NOT_PD, "Cholesky met a non-positive pivot");
+  return COV_OK;
+}
+
+static int maxbin_of(const cov_handle* h, int64_t a) {
+  return h->rowdesc[8 * a] == 0 ? h->rowdesc[8 * a + 1] : h->rowdesc[8 * a + 3];
 }
 
 int wl_snr(cov_handle* h, const double* C, int64_t ldc, const double* D, int which, double* h_snr, cudaStream_t s) {
@@ -158,13 +256,12 @@ int wl_snr(cov_handle* h, const double* C, int64_t ldc, const double* D, int whi
     if (which == COV_WHICH_B && type != 1) continue;
     sel.push_back((int)a);
   }
-  auto maxbin = [&](int a) { return h->rowdesc[8 * a] == 0 ? h->rowdesc[8 * a + 1] : h->rowdesc[8 * a + 3]; };
-  std::stable_sort(sel.begin(), sel.end(), [&](int x, int y) { return maxbin(x) < maxbin(y); });
+  std::stable_sort(sel.begin(), sel.end(), [&](int x, int y) { return maxbin_of(h, x) < maxbin_of(h, y); });
   int64_t Ms = (int64_t)sel.size();
   std::vector<int64_t> cnt(h->nl, 0);
   for (int c = 0; c < h->nl; ++c)
     for (int64_t i = 0; i < Ms; ++i)
-      if (maxbin(sel[i]) <= c) cnt[c] = i + 1;
+      if (maxbin_of(h, sel[i]) <= c) cnt[c] = i + 1;
   if (Ms == 0) {
     for (int c = 0; c < h->nl; ++c) h_snr[c] = nan("");
     return COV_OK;
@@ -188,90 +285,61 @@ int wl_snr(cov_handle* h, const double* C, int64_t ldc, const double* D, int whi
     WL_CHECK(h, cudaMalloc(&h->perm, sizeof(int) * h->M));
     h->allocated += sizeof(int) * h->M;
   }
-  size_t one_buf = (wl_chol_tc_bytes(Ms + 1) + 255) / 256 * 256;
-  size_t need_sc = 2 * one_buf;
-  if (need_sc > h->chol_scratch_n) {
-    if (h->chol_scratch) {
-      cudaFree(h->chol_scratch);
-      h->allocated -= h->chol_scratch_n;
-    }
-    h->chol_scratch = nullptr;
-    h->chol_scratch_n = 0;
-    WL_CHECK(h, cudaMalloc(&h->chol_scratch, need_sc));
-    h->chol_scratch_n = need_sc;
-    h->allocated += need_sc;
-  }
-  if (!h->chol_status) WL_CHECK(h, cudaMalloc(&h->chol_status, sizeof(int)));
-  if (!h->side) {
-    WL_CHECK(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
-    WL_CHECK(h, cudaEventCreateWithFlags(&h->ev_cols, cudaEventDisableTiming));
-    WL_CHECK(h, cudaEventCreateWithFlags(&h->ev_panel, cudaEventDisableTiming));
-  }
-  WL_CHECK(h, cudaMemsetAsync(h->chol_status, 0, sizeof(int), s));
-  int* st = nullptr;
-  int64_t* cnt_d = nullptr;
-  double* out_d = nullptr;
-  WL_CHECK(h, cudaMallocAsync(&st, sizeof(int), s));
-  WL_CHECK(h, cudaMallocAsync(&cnt_d, sizeof(int64_t) * h->nl, s));
-  WL_CHECK(h, cudaMallocAsync(&out_d, sizeof(double) * h->nl, s));
-  WL_CHECK(h, cudaMemsetAsync(st, 0, sizeof(int), s));
   WL_CHECK(h, cudaMemcpyAsync(h->perm, sel.data(), sizeof(int) * Ms, cudaMemcpyHostToDevice, s));
-  WL_CHECK(h, cudaMemcpyAsync(cnt_d, cnt.data(), sizeof(int64_t) * h->nl, cudaMemcpyHostToDevice, s));
   dim3 gp((unsigned)(Ms + 1), (unsigned)((Ms + 1 + 255) / 256));
   int tk = wl_stage_begin(h, ST_SNR_PACK, s);
   k_snr_pack<<<gp, 256, 0, s>>>(Ms, h->perm, C, ldc, D, h->work, ldw);
   WL_LAUNCH(h, "k_snr_pack");
   wl_stage_end(h, tk, s);
-  tk = wl_stage_begin(h, ST_SNR_CHOL, s);
-  // Blocked right-looking factorisation with one panel of look-ahead: the
-  // trailing update of panel p first updates the 64 columns of panel p+1,
-  // then the FP64 diagonal block, panel solve and slicing of panel p+1 run on
-  // the side stream while the rest of the update of panel p runs here.
-  uint8_t* bufs[2] = {(uint8_t*)h->chol_scratch, (uint8_t*)h->chol_scratch + one_buf};
-  auto panel = [&](int64_t k0, cudaStream_t st_) -> int {
-    int kb = (int)std::min<int64_t>(NB, Ms - k0);
-    k_potrf_diag<<<1, 256, 0, st_>>>(h->work, ldw, k0, kb, st);
-    int64_t r0 = k0 + kb, r1 = Ms + 1;
-    if (r1 > r0)
-      k_trsm_rows<<<(unsigned)((r1 - r0 + TRSM_ROWS - 1) / TRSM_ROWS), TRSM_ROWS, 0, st_>>>(h->work, ldw, k0, kb, r0,
-                                                                                            r1);
-    WL_LAUNCH(h, "Cholesky panel kernels");
-    return wl_chol_slice(h, h->work, ldw, k0, kb, r0, r1, bufs[(k0 / NB) & 1], st_);
-  };
-  int rc = panel(0, s);
-  if (rc) return rc;
-  for (int64_t k0 = 0; k0 < Ms; k0 += NB) {
-    int kb = (int)std::min<int64_t>(NB, Ms - k0);
-    int64_t r0 = k0 + kb, r1 = Ms + 1;
-    const void* buf = bufs[(k0 / NB) & 1];
-    if (r0 < Ms) {
-      // columns of the next panel first, then the next panel on the side stream
-      if ((rc = wl_chol_update(h, h->work, ldw, r0, r1, buf, 0, 1, h->chol_status, s))) return rc;
-      WL_CHECK(h, cudaEventRecord(h->ev_cols, s));
-      WL_CHECK(h, cudaStreamWaitEvent(h->side, h->ev_cols, 0));
-      if ((rc = panel(r0, h->side))) return rc;
-      WL_CHECK(h, cudaEventRecord(h->ev_panel, h->side));
-      if ((rc = wl_chol_update(h, h->work, ldw, r0, r1, buf, 1, -1, h->chol_status, s))) return rc;
-      WL_CHECK(h, cudaStreamWaitEvent(s, h->ev_panel, 0));
-    } else if (r1 > r0) {
-      // only the extra D row is left below this panel
-      if ((rc = wl_chol_update(h, h->work, ldw, r0, r1, buf, 0, -1, h->chol_status, s))) return rc;
+  int rc = factor_and_prefix(h, out_rows(h->work, ldw), Ms, cnt, h_snr, s);
+  WL_CHECK(h, cudaStreamSynchronize(s));  // sel is host memory read by an async copy
+  return rc;
+}
+
+// In place on the lower-packed tiles (rows in cumulative order): Jacobi
+// scaling of every element, D' written as row M, then the same
+// factorisation.  The diagonal is saved first (the scaling overwrites it).
+__global__ void k_tiles_diag(int64_t M, OutMap W, double* dg) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < M) dg[r] = *W.at(r, r);
+}
+
+// one block per 32 x 32 lower block of the leading M x M part, plus the D row
+__global__ void k_tiles_scale(int64_t M, OutMap W, const double* dg, const double* D) {
+  int64_t id = blockIdx.x;
+  int64_t bi = (int64_t)((sqrt(8.0 * (double)id + 1.0) - 1.0) * 0.5);
+  while (bi * (bi + 1) / 2 > id) --bi;
+  while ((bi + 1) * (bi + 2) / 2 <= id) ++bi;
+  int64_t bj = id - bi * (bi + 1) / 2;
+  int64_t c = bj * 32 + threadIdx.x;
+  for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
+    int64_t r = bi * 32 + rr;
+    if (c > r || c >= M) continue;
+    if (r < M) {
+      double* p = W.at(r, c);
+      *p = *p / sqrt(dg[r] * dg[c]);
+    } else if (r == M) {
+      *W.at(r, c) = D[c] / sqrt(dg[c]);
     }
   }
-  WL_LAUNCH(h, "Cholesky kernels");
+}
+
+int wl_snr_tiles(cov_handle* h, double* Ct, const double* D, double* h_snr, cudaStream_t s) {
+  const int64_t M = h->M;
+  std::vector<int64_t> cnt(h->nl, 0);
+  for (int c = 0; c < h->nl; ++c)
+    for (int64_t a = 0; a < M; ++a)
+      if (maxbin_of(h, a) <= c) cnt[c] = a + 1;
+  OutMap Wm = out_tiles(Ct, 0);
+  double* dg = nullptr;
+  WL_CHECK(h, cudaMallocAsync(&dg, sizeof(double) * M, s));
+  int tk = wl_stage_begin(h, ST_SNR_PACK, s);
+  k_tiles_diag<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(M, Wm, dg);
+  int64_t nb = (M + 1 + 31) / 32;
+  k_tiles_scale<<<(unsigned)(nb * (nb + 1) / 2), dim3(32, 8), 0, s>>>(M, Wm, dg, D);
+  WL_LAUNCH(h, "k_tiles_scale");
   wl_stage_end(h, tk, s);
-  tk = wl_stage_begin(h, ST_SNR_PREFIX, s);
-  k_snr_prefix<<<h->nl, 256, 0, s>>>(Ms, h->work, ldw, cnt_d, h->nl, out_d);
-  wl_stage_end(h, tk, s);
-  int status = 0, tstatus = 0;
-  WL_CHECK(h, cudaMemcpyAsync(h_snr, out_d, sizeof(double) * h->nl, cudaMemcpyDeviceToHost, s));
-  WL_CHECK(h, cudaMemcpyAsync(&status, st, sizeof(int), cudaMemcpyDeviceToHost, s));
-  WL_CHECK(h, cudaMemcpyAsync(&tstatus, h->chol_status, sizeof(int), cudaMemcpyDeviceToHost, s));
-  WL_CHECK(h, cudaFreeAsync(st, s));
-  WL_CHECK(h, cudaFreeAsync(cnt_d, s));
-  WL_CHECK(h, cudaFreeAsync(out_d, s));
-  WL_CHECK(h, cudaStreamSynchronize(s));
-  if (tstatus) return wl_fail(h, COV_ERR_TIMEOUT, "Cholesky trailing update: a bounded mbarrier wait expired");
-  if (status) return wl_fail(h, COV_ERR_NOT_PD, "Cholesky met a non-positive pivot");
-  return COV_OK;
+  WL_CHECK(h, cudaFreeAsync(dg, s));
+  int rc = factor_and_prefix(h, Wm, M, cnt, h_snr, s);
+  return rc;
 }

@@ -40,14 +40,14 @@
 
 // slices of the panel rows r0..r1-1 (columns k0..k0+kb-1 of the workspace);
 // rows up to the padded count are written (zeros past r1)
-__global__ void k_chol_slice(const double* Wk, int64_t ldw, int64_t k0, int kb, int64_t r0, int64_t nrows,
-                             int64_t nrows_pad, __nv_bfloat16* slices, int* rexp) {
+__global__ void k_chol_slice(const OutMap W, int64_t k0, int kb, int64_t r0, int64_t nrows, int64_t nrows_pad,
+                             __nv_bfloat16* slices, int* rexp) {
   int64_t r = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   int lane = threadIdx.x & 31;
   if (r >= nrows_pad) return;
   double x0 = 0.0, x1 = 0.0;
   if (r < nrows) {
-    const double* row = Wk + (r0 + r) * ldw + k0;
+    const double* row = W.at(r0 + r, k0);
     if (lane < kb) x0 = row[lane];
     if (lane + 32 < kb) x1 = row[lane + 32];
   }
@@ -114,8 +114,8 @@ __device__ __forceinline__ void cs_tmem_ld32(uint32_t taddr, float* v) {
 // grid.x = tile row (128 rows), grid.y = tile column (64 columns) - tj0
 __global__ void __launch_bounds__(128, 1)
     k_chol_update(const __grid_constant__ CUtensorMap map_i, const __grid_constant__ CUtensorMap map_j,
-                  int64_t nrows, int64_t nrows_pad, const int* __restrict__ rexp, double* Csub, int64_t ldc,
-                  int* status, int tj0) {
+                  int64_t nrows, int64_t nrows_pad, const int* __restrict__ rexp, OutMap W, int64_t r0, int* status,
+                  int tj0) {
   int tj = blockIdx.y + tj0;
   int ti = blockIdx.x + (tj0 * CS_BJ) / CS_BI;
   if ((int64_t)tj * CS_BJ > (int64_t)ti * CS_BI + CS_BI - 1) return;  // tile above the diagonal
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(128, 1)
       int64_t gr = (int64_t)row_i + rr, gc = (int64_t)row_j + cc;
       if (gr < nrows && gc < nrows && gc <= gr) {
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(cs_smem_u32(ctile + e)),
-                     "l"(Csub + gr * ldc + gc)
+                     "l"(W.at(r0 + gr, r0 + gc))
                      : "memory");
       }
     }
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(128, 1)
           // exact power of two 2^(e_r + e_j - 14 - 40) built from its exponent bits
           int ex = er + ej - 54;
           double sc = (ex > -1000 && ex < 1000) ? __longlong_as_double((long long)(ex + 1023) << 52) : ldexp(1.0, ex);
-          Csub[gr * ldc + gj] = ctile[lr * CS_BJ + c * 32 + lane] - stg[rr * 33 + lane] * sc;
+          *W.at(r0 + gr, r0 + gj) = ctile[lr * CS_BJ + c * 32 + lane] - stg[rr * 33 + lane] * sc;
         }
       }
       __syncwarp();
@@ -284,14 +284,13 @@ size_t wl_chol_tc_bytes(int64_t n) {
 }
 
 // slices of the panel rows r0..r1-1, columns k0..k0+kb-1 of the workspace
-int wl_chol_slice(cov_handle* h, const double* Wk, int64_t ldw, int64_t k0, int kb, int64_t r0, int64_t r1,
-                  void* buf, cudaStream_t s) {
+int wl_chol_slice(cov_handle* h, OutMap W, int64_t k0, int kb, int64_t r0, int64_t r1, void* buf, cudaStream_t s) {
   int64_t n = r1 - r0;
   if (n <= 0) return COV_OK;
   int64_t pad = (n + CS_BI - 1) / CS_BI * CS_BI;
   __nv_bfloat16* slices = (__nv_bfloat16*)buf;
   int* rexp = (int*)((uint8_t*)buf + (size_t)CS_S * pad * CS_K * 2);
-  k_chol_slice<<<(unsigned)((pad + 7) / 8), 256, 0, s>>>(Wk, ldw, k0, kb, r0, n, pad, slices, rexp);
+  k_chol_slice<<<(unsigned)((pad + 7) / 8), 256, 0, s>>>(W, k0, kb, r0, n, pad, slices, rexp);
   WL_LAUNCH(h, "k_chol_slice");
   return COV_OK;
 }
@@ -299,8 +298,8 @@ int wl_chol_slice(cov_handle* h, const double* Wk, int64_t ldw, int64_t k0, int 
 // Csub (rows/cols r0..r1-1 of the workspace) -= L21 L21^T over the column
 // tiles tj0 .. tj0+ntj-1 (64 columns each; ntj < 0: all remaining), lower
 // triangle only, from the slices in buf
-int wl_chol_update(cov_handle* h, double* Wk, int64_t ldw, int64_t r0, int64_t r1, const void* buf, int tj0, int ntj,
-                   int* status, cudaStream_t s) {
+int wl_chol_update(cov_handle* h, OutMap W, int64_t r0, int64_t r1, const void* buf, int tj0, int ntj, int* status,
+                   cudaStream_t s) {
   int64_t n = r1 - r0;
   if (n <= 0) return COV_OK;
   int64_t pad = (n + CS_BI - 1) / CS_BI * CS_BI;
@@ -322,7 +321,7 @@ int wl_chol_update(cov_handle* h, double* Wk, int64_t ldw, int64_t r0, int64_t r
   // only tile rows that reach the requested columns
   int ti0 = (int)(((int64_t)tj0 * CS_BJ) / CS_BI);
   dim3 grid((unsigned)(pad / CS_BI - ti0), (unsigned)ntj);
-  k_chol_update<<<grid, 128, CS_SMEM, s>>>(mi, mj, n, pad, rexp, Wk + r0 * ldw + r0, ldw, status, tj0);
+  k_chol_update<<<grid, 128, CS_SMEM, s>>>(mi, mj, n, pad, rexp, W, r0, status, tj0);
   WL_LAUNCH(h, "k_chol_update");
   return COV_OK;
 }

@@ -60,7 +60,7 @@ struct StageEvent {
 // cuTensorMapEncodeTiled from the driver, looked up once per process
 // (thread-safe: the serving scheduler runs requests on several host threads).
 PFN_cuTensorMapEncodeTiled_v12000 wl_encode_tiled();
-#define WL_TILE_CACHE 4
+#define WL_TILE_CACHE 16
 int wl_ensure(struct cov_handle* h, void** p, size_t bytes, const char* what);  // assemble.cu: allocate once
 // Run f once per CUDA device for the calling thread's current device.
 #define WL_MAX_DEVICES 64
@@ -135,9 +135,10 @@ struct cov_handle {
   struct TileOrder {
     int kind = -1;
     int64_t t0 = -1, t1 = -1, n = 0;
-    size_t cap = 0;
-    int2* p = nullptr;
+    int2* p = nullptr;  // a slot of tile_ring
   } tile_cache[WL_TILE_CACHE];
+  int2* tile_ring = nullptr;
+  size_t tile_ring_cap = 0;  // entries per slot
   int tile_cache_next = 0;
   float* Fsig = nullptr;
   float* FsigT = nullptr;  // the same for the bin pairs of the trispectrum rows
@@ -160,6 +161,7 @@ struct cov_handle {
   cudaEvent_t ev_cols = nullptr, ev_panel = nullptr;
   int* chol_status = nullptr;
   bool spectra_ready = false;
+  int row_set = 0, row_order = 0;  // COV_ROWS_*, COV_ORDER_*
   int ops_terms = -1, ops_precision = -1;  // operands prepared for the band assembly (-1: none)
   bool prof = false;
   std::vector<StageEvent> pending;
@@ -193,6 +195,7 @@ int wl_tables(cov_handle* h, cudaStream_t s);   // tables.cu
 int wl_counts(cov_handle* h, cudaStream_t s);   // counts.cu
 int wl_spectra(cov_handle* h, double* d_D, cudaStream_t s);  // spectra.cu
 int wl_assemble(cov_handle* h, double* d_C, int64_t ldc, unsigned terms, int precision, cudaStream_t s);
+int wl_snr_tiles(cov_handle* h, double* Ct, const double* D, double* h_snr, cudaStream_t s);  // chol.cu
 int wl_assemble_band(cov_handle* h, int64_t row0, int64_t nrows, OutMap out, unsigned terms, int precision,
                      cudaStream_t s);
 int wl_snr(cov_handle* h, const double* d_C, int64_t ldc, const double* d_D, int which, double* h_snr,
@@ -201,6 +204,9 @@ int wl_gemm_lower_fp64(cov_handle* h, const double* A, int64_t lda, const double
                        int64_t ldc, int64_t n, int64_t k, double alpha, double beta, bool lower_only,
                        cudaStream_t s);  // assemble.cu
 int wl_syrk_tc(cov_handle* h, int nssc, OutMap out, cudaStream_t s, int64_t row1 = -1);  // syrk_tc.cu
+int wl_syrk_tc_part(cov_handle* h, int nssc, OutMap out, int64_t r0, int64_t r1, cudaStream_t s);
+int wl_tc_status_reset(cov_handle* h, cudaStream_t s);
+int wl_tc_status_check(cov_handle* h, cudaStream_t s);
 int wl_split_bytes(int64_t M, int K, size_t* bytes);                      // syrk_tc.cu
 int wl_kpad(int K);  // K padded to the contraction's K granularity
 int wl_request_bytes(const cov_nz* nz, const cov_bins* bins, int precision, unsigned terms, int64_t* M,
@@ -208,10 +214,9 @@ int wl_request_bytes(const cov_nz* nz, const cov_bins* bins, int precision, unsi
 size_t wl_handle_bytes(const cov_handle* h);
 void wl_set_global_error(const std::string& msg);  // api.cu: read by cov_last_error(NULL)
 size_t wl_chol_tc_bytes(int64_t n);  // chol_tc.cu
-int wl_chol_slice(cov_handle* h, const double* Wk, int64_t ldw, int64_t k0, int kb, int64_t r0, int64_t r1,
-                  void* buf, cudaStream_t s);
-int wl_chol_update(cov_handle* h, double* Wk, int64_t ldw, int64_t r0, int64_t r1, const void* buf, int tj0, int ntj,
-                   int* status, cudaStream_t s);
+int wl_chol_slice(cov_handle* h, OutMap W, int64_t k0, int kb, int64_t r0, int64_t r1, void* buf, cudaStream_t s);
+int wl_chol_update(cov_handle* h, OutMap W, int64_t r0, int64_t r1, const void* buf, int tj0, int ntj, int* status,
+                   cudaStream_t s);
 int wl_syrk_tc_rows(cov_handle* h, const void* hi, const void* lo, const double* rscale, int64_t rows, int Kp,
                     OutMap out, cudaStream_t s, int64_t row1 = -1);
 // ---- device helpers ------------------------------------------------------------

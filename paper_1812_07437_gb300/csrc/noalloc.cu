@@ -25,8 +25,8 @@
 #include "common.cuh"
 
 // kernels of the handle-based path, reused unchanged
-__global__ void k_potrf_diag(double* Wk, int64_t ldw, int64_t k0, int kb, int* status);
-__global__ void k_trsm_rows(double* Wk, int64_t ldw, int64_t k0, int kb, int64_t r0, int64_t r1);
+__global__ void k_potrf_diag(OutMap W, int64_t k0, int kb, int* status);
+__global__ void k_trsm_rows(OutMap W, int64_t k0, int kb, int64_t r0, int64_t r1);
 __global__ void k_gemm_lower(const double* __restrict__ A, int64_t lda, const double* __restrict__ B, int64_t ldb,
                              OutMap out, int64_t n, int64_t k, double alpha, double beta, int lower_only,
                              int64_t ntiles_1d, int64_t tile_off);
@@ -113,10 +113,10 @@ extern "C" int cov_snr_noalloc(const double* d_C, int64_t ldc, const double* d_D
   k_na_pack<<<gp, 256, 0, s>>>(M, d_C, ldc, d_D, work, ldw);
   for (int64_t k0 = 0; k0 < M; k0 += NA_NB) {
     int kb = (int)((M - k0) < NA_NB ? (M - k0) : NA_NB);
-    k_potrf_diag<<<1, 256, 0, s>>>(work, ldw, k0, kb, d_status);
+    k_potrf_diag<<<1, 256, 0, s>>>(out_rows(work, ldw), k0, kb, d_status);
     int64_t r0 = k0 + kb, r1 = M + 1;
     if (r1 > r0) {
-      k_trsm_rows<<<(unsigned)((r1 - r0 + 31) / 32), 32, 0, s>>>(work, ldw, k0, kb, r0, r1);
+      k_trsm_rows<<<(unsigned)((r1 - r0 + 31) / 32), 32, 0, s>>>(out_rows(work, ldw), k0, kb, r0, r1);
       int64_t n = r1 - r0;
       int64_t nt1 = (n + 63) / 64;
       double* P = work + r0 * ldw + k0;

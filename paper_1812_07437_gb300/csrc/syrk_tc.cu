@@ -537,6 +537,7 @@ __global__ void __launch_bounds__(128, 1)
 // counts three arrivals.  Tiles above the diagonal or past the band are
 // computed (their halves feed the neighbours) but not stored.
 #define MC_BOX_ROWS 128
+#define MC_GROUP 4  // super-rows per launch-order group
 #define MC_HALF_BYTES (MC_BOX_ROWS * TW_BK * 2)  // 8 KB
 
 __device__ __forceinline__ uint32_t cluster_rank() {
@@ -833,9 +834,9 @@ int wl_trows_split(cov_handle* h, cudaStream_t s) {
 // C (lower, FP64) = (hi + lo)(hi + lo)^T scaled, without the lo lo^T term
 // Launch orders, cached per (tile-row range, kind).  kind 0: the lower tiles
 // (ti, tj), tj <= ti, of tile rows [t0, t1), row by row.  kind 1: the 2 x 2
-// super-tiles (top-left tile (t0 + 2 I, 2 J)) that hold at least one of them,
-// row by row; the cluster kernel computes all four tiles of each and stores
-// the ones inside the band's lower part.
+// super-tiles (top-left tile (t0 + 2 I, 2 J)) that hold at least one of them;
+// the cluster kernel computes all four tiles of each and stores the ones
+// inside the band's lower part.
 int wl_tile_order(cov_handle* h, int kind, int64_t t0, int64_t t1, const int2** tiles, int64_t* n) {
   for (auto& c : h->tile_cache)
     if (c.p && c.kind == kind && c.t0 == t0 && c.t1 == t1) {
@@ -848,23 +849,35 @@ int wl_tile_order(cov_handle* h, int kind, int64_t t0, int64_t t1, const int2** 
     for (int64_t ti = t0; ti < t1; ++ti)
       for (int64_t tj = 0; tj <= ti; ++tj) v.push_back(make_int2((int)ti, (int)tj));
   } else {
-    for (int64_t i0 = t0; i0 < t1; i0 += 2) {
-      int64_t last = std::min<int64_t>(i0 + 1, t1 - 1);  // last tile row of this super-row inside the band
-      for (int64_t j0 = 0; j0 <= last; j0 += 2) v.push_back(make_int2((int)i0, (int)j0));
+    // groups of MC_GROUP super-rows; inside a group, column by column, so the
+    // ~37 clusters of one wave share a few row and column panels in L2
+    for (int64_t g0 = t0; g0 < t1; g0 += 2 * MC_GROUP) {
+      int64_t g1 = std::min<int64_t>(g0 + 2 * MC_GROUP, t1);
+      int64_t jmax = g1 - 1;  // last tile row of the group
+      for (int64_t j0 = 0; j0 <= jmax; j0 += 2)
+        for (int64_t i0 = g0; i0 < g1; i0 += 2) {
+          int64_t last = std::min<int64_t>(i0 + 1, t1 - 1);
+          if (j0 <= last) v.push_back(make_int2((int)i0, (int)j0));
+        }
     }
   }
-  auto& c = h->tile_cache[h->tile_cache_next];
+  // One allocation for the whole ring, sized for the largest matrix of the
+  // handle, so that no entry is ever freed: launches of one band call use
+  // fewer than WL_TILE_CACHE entries and may still be in flight when the next
+  // entry is written; band calls end with a stream synchronisation.
+  if (!h->tile_ring) {
+    int64_t t = (std::max<int64_t>(h->M, h->ntrow) + 255) / 256 + 1;
+    h->tile_ring_cap = (size_t)(t * (t + 1) / 2);
+    size_t bytes = sizeof(int2) * h->tile_ring_cap * WL_TILE_CACHE;
+    WL_CHECK(h, cudaMalloc(&h->tile_ring, bytes));
+    h->allocated += bytes;
+    for (int k = 0; k < WL_TILE_CACHE; ++k) h->tile_cache[k].p = nullptr;
+  }
+  if (v.size() > h->tile_ring_cap) return wl_fail(h, COV_ERR_INVALID, "launch order larger than its ring slot");
+  int slot = h->tile_cache_next;
   h->tile_cache_next = (h->tile_cache_next + 1) % WL_TILE_CACHE;
-  if (c.p && c.cap < v.size()) {
-    cudaFree(c.p);
-    h->allocated -= sizeof(int2) * c.cap;
-    c.p = nullptr;
-  }
-  if (!c.p) {
-    WL_CHECK(h, cudaMalloc(&c.p, sizeof(int2) * v.size()));
-    c.cap = v.size();
-    h->allocated += sizeof(int2) * c.cap;
-  }
+  auto& c = h->tile_cache[slot];
+  c.p = h->tile_ring + (size_t)slot * h->tile_ring_cap;
   WL_CHECK(h, cudaMemcpy(c.p, v.data(), sizeof(int2) * v.size(), cudaMemcpyHostToDevice));
   c.kind = kind;
   c.t0 = t0;
@@ -899,23 +912,15 @@ static int mc_clusters_ok() {
   return ok[d];
 }
 
-int wl_syrk_tc_rows(cov_handle* h, const void* hi, const void* lo, const double* rscale, int64_t rows, int Kp,
-                    OutMap out, cudaStream_t s, int64_t row1) {
-  CUtensorMap mhi, mlo;
+// Launch the contraction over tile rows [r0, row1) of out's band (no status
+// handling): the 2 x 2 cluster kernel when 4-CTA clusters can be placed, else
+// one CTA per tile.
+static int launch_tc(cov_handle* h, const void* hi, const void* lo, const double* rscale, int64_t rows, int Kp,
+                     OutMap out, int64_t r0, int64_t row1, cudaStream_t s) {
   int rc;
-  if ((rc = make_map(h, &mhi, (void*)hi, rows, Kp))) return rc;
-  if ((rc = make_map(h, &mlo, (void*)lo, rows, Kp))) return rc;
-  static std::once_flag attr_once[WL_MAX_DEVICES];
-  static int attr_rc[WL_MAX_DEVICES];
-  if (wl_once_per_device(attr_once, attr_rc, [] {
-        return (int)cudaFuncSetAttribute(k_syrk_tc256, cudaFuncAttributeMaxDynamicSharedMemorySize, TW_SMEM);
-      }) != 0)
-    return wl_fail(h, COV_ERR_CUDA, "cudaFuncSetAttribute(k_syrk_tc256) failed");
-  if (!h->tc_status) WL_CHECK(h, cudaMalloc(&h->tc_status, sizeof(int)));
-  WL_CHECK(h, cudaMemsetAsync(h->tc_status, 0, sizeof(int), s));
-  // tile rows of the band [out.row0, row1); out.row0 is a multiple of 256
   if (row1 < 0 || row1 > rows) row1 = rows;
-  int64_t t0 = out.row0 / TW_BM, t1 = (row1 + TW_BM - 1) / TW_BM;
+  int64_t t0 = r0 / TW_BM, t1 = (row1 + TW_BM - 1) / TW_BM;
+  if (t1 <= t0) return COV_OK;
   const int2* tiles = nullptr;
   int64_t nblk = 0;
   if (mc_clusters_ok()) {
@@ -927,10 +932,34 @@ int wl_syrk_tc_rows(cov_handle* h, const void* hi, const void* lo, const double*
                                                                 h->tc_status, tiles, t1);
     WL_LAUNCH(h, "k_syrk_tc256_mc");
   } else {
+    CUtensorMap mhi, mlo;
+    if ((rc = make_map(h, &mhi, (void*)hi, rows, Kp))) return rc;
+    if ((rc = make_map(h, &mlo, (void*)lo, rows, Kp))) return rc;
+    static std::once_flag attr_once[WL_MAX_DEVICES];
+    static int attr_rc[WL_MAX_DEVICES];
+    if (wl_once_per_device(attr_once, attr_rc, [] {
+          return (int)cudaFuncSetAttribute(k_syrk_tc256, cudaFuncAttributeMaxDynamicSharedMemorySize, TW_SMEM);
+        }) != 0)
+      return wl_fail(h, COV_ERR_CUDA, "cudaFuncSetAttribute(k_syrk_tc256) failed");
     if ((rc = wl_tile_order(h, 0, t0, t1, &tiles, &nblk))) return rc;
     k_syrk_tc256<<<(unsigned)nblk, 128, TW_SMEM, s>>>(mhi, mlo, rows, Kp / TW_BK, rscale, out, h->tc_status, tiles);
     WL_LAUNCH(h, "k_syrk_tc256");
   }
+  return COV_OK;
+}
+
+// The contraction kernels raise a device status word when a bounded wait
+// expires; it is cleared before a group of launches and read after them.
+int wl_tc_status_reset(cov_handle* h, cudaStream_t s) {
+  if (!h->tc_status) {
+    WL_CHECK(h, cudaMalloc(&h->tc_status, sizeof(int)));
+    h->allocated += sizeof(int);
+  }
+  WL_CHECK(h, cudaMemsetAsync(h->tc_status, 0, sizeof(int), s));
+  return COV_OK;
+}
+
+int wl_tc_status_check(cov_handle* h, cudaStream_t s) {
   int st = 0;
   WL_CHECK(h, cudaMemcpyAsync(&st, h->tc_status, sizeof(int), cudaMemcpyDeviceToHost, s));
   WL_CHECK(h, cudaStreamSynchronize(s));
@@ -938,7 +967,20 @@ int wl_syrk_tc_rows(cov_handle* h, const void* hi, const void* lo, const double*
   return COV_OK;
 }
 
+int wl_syrk_tc_rows(cov_handle* h, const void* hi, const void* lo, const double* rscale, int64_t rows, int Kp,
+                    OutMap out, cudaStream_t s, int64_t row1) {
+  int rc;
+  if ((rc = wl_tc_status_reset(h, s))) return rc;
+  if ((rc = launch_tc(h, hi, lo, rscale, rows, Kp, out, out.row0, row1, s))) return rc;
+  return wl_tc_status_check(h, s);
+}
+
 int wl_syrk_tc(cov_handle* h, int nssc, OutMap out, cudaStream_t s, int64_t row1) {
   return wl_syrk_tc_rows(h, h->Ahi, h->Alo, h->Ascale, h->M, kpad(h->K + nssc), out, s, row1);
+}
+
+// 1-halo (+ SSC) contraction of rows [r0, r1) into out, launch only
+int wl_syrk_tc_part(cov_handle* h, int nssc, OutMap out, int64_t r0, int64_t r1, cudaStream_t s) {
+  return launch_tc(h, h->Ahi, h->Alo, h->Ascale, h->M, kpad(h->K + nssc), out, r0, r1, s);
 }
 

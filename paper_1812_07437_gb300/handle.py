@@ -18,10 +18,10 @@ def _stream_ptr(stream):
 
 
 class Handle:
-    def __init__(self, wl, device=0, hbm_budget=0):
+    def __init__(self, wl, device=0, hbm_budget=0, rows=N.COV_ROWS_JOINT, order=N.COV_ORDER_NATURAL):
         self.L = N.lib()
         cs, ns, bs = N.structs_from_workload(wl)
-        opts = N.cov_opts(int(device), int(hbm_budget))
+        opts = N.cov_opts(int(device), int(hbm_budget), int(rows), int(order))
         h = C.c_void_p()
         N.check(self.L.cov_init(C.byref(cs), C.byref(ns), C.byref(bs), C.byref(opts), C.byref(h)))
         self.h = h
@@ -104,3 +104,16 @@ class Handle:
         N.check(self.L.cov_snr(self.h, C.c_void_p(Cmat.data_ptr()), Cmat.stride(0), C.c_void_p(D.data_ptr()),
                                which, out.ctypes.data_as(C.c_void_p), _stream_ptr(stream)), self.h)
         return out
+
+    def snr_tiles(self, Ct, D, stream=None):
+        """In-place cumulative S/N of the handle's rows on its lower-packed tiles (cumulative-order handles)."""
+        out = np.zeros(self.n_ell, dtype=np.float64)
+        N.check(self.L.cov_snr_tiles(self.h, C.c_void_p(Ct.data_ptr()), C.c_void_p(D.data_ptr()),
+                                     out.ctypes.data_as(C.c_void_p), _stream_ptr(stream)), self.h)
+        return out
+
+
+def packed_tiles(rows):
+    """Number of 256 x 256 lower tiles holding rows 0..rows-1."""
+    t = (rows + 255) // 256
+    return t * (t + 1) // 2
