@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--snr-workload", default="cfg2_5bin")
     p.add_argument("--no-snr-run", action="store_true")
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--batch-bins", default="3,5", help="tomographic bin counts of the batched Fisher run")
     p.add_argument("--snr-10bin", action="store_true",
                    help="also time the cumulative S/N of the workload itself, in place on its packed tiles "
                         "(one extra assembly and FP64-accurate Cholesky per row set; minutes at 10 bins)")
@@ -245,22 +247,32 @@ def timed(stream, fn, steps, h, world):
     return e0.elapsed_time(e1), stages, out
 
 
-# DRAM bytes (read + write) of one full-size contraction launch, from a one-pass
-# ncu capture (profiles/launches_cfg3_10bin.md), valid only while the kernel
-# source it was taken on is unchanged (sha256 of csrc/syrk_tc.cu).
+# DRAM bytes (read + write) of the contraction of one full-size band call (its
+# eight sub-band launches), from one-pass ncu captures of those launches
+# (profiles/launches_cfg3_10bin.md).  A figure is valid only while the
+# contraction kernel, its launch order and its tile constants are unchanged:
+# their source text is fingerprinted.
 TRAFFIC = {
-    # workload: (bytes per launch, sha256 of syrk_tc.cu at capture)
+    # workload: (bytes per band call, fingerprint at capture)
+    "cfg3_10bin": (4.1816e12, "b298612482447a40"),
 }
 
 
-def measured_traffic(workload):
+def kernel_fingerprint():
     import hashlib
+    src = open(os.path.join(ROOT, "paper_1812_07437_gb300", "csrc", "syrk_tc.cu")).read()
+    parts = [ln for ln in src.splitlines() if ln.startswith("#define TW_") or ln.startswith("#define MC_")]
+    a = src.index("// ---------------------------------------------------------------- 2 x 2 clusters")
+    b = src.index("// ---------------------------------------------------------------- host side")
+    parts.append(src[a:b])
+    c = src.index("int wl_tile_order(")
+    parts.append(src[c:src.index("\n}\n", c)])
+    return hashlib.sha256("\n".join(parts).encode()).hexdigest()[:16]
+
+
+def measured_traffic(workload):
     ent = TRAFFIC.get(workload)
-    if not ent:
-        return None
-    src = os.path.join(ROOT, "paper_1812_07437_gb300", "csrc", "syrk_tc.cu")
-    with open(src, "rb") as fh:
-        return ent[0] if hashlib.sha256(fh.read()).hexdigest() == ent[1] else None
+    return ent[0] if ent and kernel_fingerprint() == ent[1] else None
 
 
 def contraction_roofline(stages, elements, K, prec, N, long_kernel):
@@ -349,6 +361,57 @@ def serving_run(prec, n_req, rate, budget_gb, slots, device, seed=2024):
             "M_served_max": max((x["M"] for x in done), default=0),
             "reused_resident": sum(x["reused"] for x in done), "max_running": st["max_running"],
             "peak_reserved_gb": st["peak_reserved"] / 1e9, "budget_gb": st["budget"] / 1e9, "slots": slots}
+
+
+def batch_run(prec, device, bins_list):
+    """The batched Fisher set: 64 cosmologies (fiducial, +-1% and +-2% steps in
+    six parameters, seeded draws within +-5%) for each tomographic bin count,
+    16 ell bins, N_chi = 256, N_M = 128; one eager and tuned first cosmology,
+    then graph replays.  For the smallest set-up the same 64 cosmologies also
+    run through the plain calls, for the replay speed-up."""
+    import numpy as np
+    import torch
+    from paper_1812_07437_gb300 import native as N
+    from paper_1812_07437_gb300 import workloads
+    from paper_1812_07437_gb300.handle import Handle
+    cos = workloads.fisher_cosmologies()
+    dev = torch.device("cuda", device)
+    out = {"cosmologies": len(cos), "ell_bins": 16, "n_chi": 256, "n_mass": 128}
+    for k, nt in enumerate(bins_list):
+        wl = workloads.fisher_workload(nt)
+        h = Handle(wl, device=device)
+        st = torch.cuda.Stream(device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        snr, _, info = h.batch_snr(cos, precision=prec, tune=True, stream=st)
+        total = time.perf_counter() - t0
+        el = h.M * (h.M + 1) // 2
+        r = {"M": h.M, "total_s": total, "first_ms": info["first_ms"], "capture_ms": info["capture_ms"],
+             "replay_ms_per_cosmology": info["replay_ms"], "tuned": {"tc_kernel": info["tc_kernel"],
+                                                                      "chol_lookahead": info["chol_lookahead"],
+                                                                      "candidate_ms": info["candidate_ms"]},
+             "elements_per_s_replays": el / (info["replay_ms"] / 1e3), "snr_joint_fiducial": float(snr[0, 2, -1])}
+        if k == 0:
+            D = torch.zeros(h.M, dtype=torch.float64, device=dev)
+            C = torch.zeros(h.M, h.M, dtype=torch.float64, device=dev)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            worst = 0.0
+            with torch.cuda.stream(st):
+                for j, c in enumerate(cos):
+                    h.update(c, st)
+                    h.spectra(D, st)
+                    h.assemble(C, N.COV_TERMS_ALL, prec, st)
+                    s3 = np.stack([h.snr(C, D, w, st) for w in (0, 1, 2)])
+                    m = np.isfinite(s3)
+                    worst = max(worst, float(np.max(np.abs(snr[j][m] / s3[m] - 1.0))))
+            torch.cuda.synchronize()
+            r["plain_ms_per_cosmology"] = (time.perf_counter() - t1) / len(cos) * 1e3
+            r["max_rel_diff_vs_plain"] = worst
+        out[f"{nt}bin"] = r
+        h.close()
+        torch.cuda.empty_cache()
+    return out
 
 
 def snr_tiles_run(wl, prec, device, row_sets):
@@ -461,10 +524,8 @@ def run_ours(args):
             dbuf = [torch.empty(nmax, dtype=torch.float64, device=dev) for _ in range(2)]
             hbuf = [torch.empty(nmax, dtype=torch.float64, pin_memory=True) for _ in range(2)]
             Dh = torch.empty(M, dtype=torch.float64, pin_memory=True)
-            # each band leaves in four chunks on four copy streams (several copy engines)
-            NC = 4
-            copies = [torch.cuda.Stream(device=dev) for _ in range(NC)]
-            done = [[torch.cuda.Event() for _ in range(NC)] for _ in range(2)]
+            copy = torch.cuda.Stream(device=dev)
+            done = [torch.cuda.Event() for _ in range(2)]
             ready = [torch.cuda.Event() for _ in range(2)]
             d2h = 0
 
@@ -477,19 +538,15 @@ def run_ours(args):
                 for k, (a, b) in enumerate(bands):
                     n = (packed_tiles(b) - packed_tiles(a)) * TILE * TILE
                     s = k % 2
-                    for e in done[s]:
-                        stream.wait_event(e)
+                    stream.wait_event(done[s])
                     h.assemble_band(a, b - a, dbuf[s][:n], N.COV_LAYOUT_TILES, N.COV_TERMS_ALL, prec, stream)
                     ready[s].record(stream)
-                    for c, cs in enumerate(copies):
-                        lo_, hi_ = c * n // NC, (c + 1) * n // NC
-                        cs.wait_event(ready[s])
-                        with torch.cuda.stream(cs):
-                            hbuf[s][lo_:hi_].copy_(dbuf[s][lo_:hi_], non_blocking=True)
-                        done[s][c].record(cs)
+                    copy.wait_event(ready[s])
+                    with torch.cuda.stream(copy):
+                        hbuf[s][:n].copy_(dbuf[s][:n], non_blocking=True)
+                    done[s].record(copy)
                     d2h += n * 8
-                for cs in copies:
-                    cs.synchronize()
+                copy.synchronize()
                 stream.synchronize()
 
             e2e_step()
@@ -525,8 +582,8 @@ def run_ours(args):
         e2e = {"value": world * elements / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 56,
                "d2h_bytes_per_step": d2h,
                "how": f"cov_update + cov_spectra, then cov_assemble_band over {len(bands)} bands of about equal "
-                      "size into two device buffers, each band copied to pinned host memory in four chunks on "
-                      "four copy streams while the next one is assembled"}
+                      "size into two device buffers, each band copied to pinned host memory on a second stream "
+                      "while the next one is assembled"}
         snr_sizes = []
         cfg = {"layout": "lower-packed 256x256 tiles, resident (%.1f GB)" % (Ct.numel() * 8 / 1e9)}
     else:
@@ -618,6 +675,8 @@ def run_ours(args):
             "snr_rel_err_vs_fp64_form": r2.get("snr_rel_err_vs_fp64_form"),
             "snr_joint_max": float(np.nanmax(r2["snr"][2]))}
         h2.close()
+    if not args.no_batch and packed and rank == 0 and world == 1:
+        out["fisher_batch"] = batch_run(prec, local, [int(x) for x in args.batch_bins.split(",") if x])
     if args.snr_10bin and rank == 0 and world == 1:
         out["snr_tiles"] = snr_tiles_run(workloads.get(args.workload), prec, local,
                                          [("joint", N.COV_ROWS_JOINT), ("B", N.COV_ROWS_B), ("P", N.COV_ROWS_P)])

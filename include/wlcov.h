@@ -230,6 +230,40 @@ const char* cov_stage_name(int stage);
 int cov_snr_noalloc(const double* d_C, int64_t ldc, const double* d_D, int64_t M, const int64_t* prefix,
                     int n_prefix, double* d_snr, int* d_status, void* stream);
 
+/* ---- Batched cosmologies: one survey set-up, many cosmologies -------------
+ *
+ * For each of n cosmologies (cosmos, host array), the data vector (Eq.
+ * nProjection; into h_D + k M when h_D is not NULL, host) and the three
+ * cumulative S/N curves (Eqs. SNprim, eq:SN; h_snr + 3 k n_ell, host, in the
+ * order P, B, joint) of the handle's survey set-up, with the covariance terms
+ * `terms` in `precision`: the Fisher pattern (finite-difference steps around a
+ * fiducial cosmology) and emulator training sets.  The first cosmology runs
+ * eagerly and prepares everything; with COV_BATCH_TUNE it first runs once per
+ * candidate launch configuration (tensor-core contraction in 2 x 2 clusters or
+ * one CTA per tile; Cholesky with or without panel look-ahead), keeps the
+ * fastest for this handle and reports the candidate times in *info.  The
+ * cosmology-dependent step (tables, spectra, dense covariance, three S/N) is
+ * then captured once as a CUDA graph and replayed for the other cosmologies,
+ * each after a copy of its parameters to the device; the exact counts are
+ * computed once.  Results equal those of cov_update + cov_spectra +
+ * cov_assemble + cov_snr for each cosmology.  The handle keeps a dense M x M
+ * covariance and the (M + 1)^2 Cholesky workspace.  A non-positive pivot or an
+ * expired wait in any cosmology fails the whole batch (COV_ERR_NOT_PD /
+ * COV_ERR_TIMEOUT).  Afterwards the handle holds the last cosmology. */
+#define COV_BATCH_TUNE 1u
+
+typedef struct {
+  int tc_kernel;          /* contraction kernel used: 1 = 2 x 2 clusters, 0 = one CTA per tile, -1 = automatic */
+  int chol_lookahead;     /* 1: Cholesky panel look-ahead on a side stream                                    */
+  double candidate_ms[4]; /* tuning: (clusters, look-ahead), (clusters, none), (one CTA, look-ahead), (one CTA, none) */
+  double first_ms;        /* the first cosmology, tuning included                                             */
+  double capture_ms;      /* capture and instantiation of the step                                            */
+  double replay_ms;       /* per further cosmology (host clock, copies included)                              */
+} cov_batch_info;
+
+int cov_batch_snr(cov_handle* h, const cov_cosmology* cosmos, int n, unsigned terms, int precision, double* h_D,
+                  double* h_snr, unsigned flags, cov_batch_info* info, void* stream);
+
 /* ---- Serving: continuous batching of covariance + S/N requests ----------
  *
  * A request is one covariance with every term and the three cumulative S/N

@@ -213,10 +213,18 @@ static void free_all(cov_handle* h) {
                   h->ell_d, h->m, h->om, h->sig0, h->dlns, h->f, h->b1, h->b2, h->U, h->Pl, h->dPl, h->Psh, h->zedges,
                   h->norms, h->W, h->sigw2, h->slo_d, h->shi_d, h->Nmodes, h->Ntri, h->rowtab, h->tris_d,
                   h->rowdesc_d, h->P3, h->RP3, h->B3, h->RB3, h->B1h3, h->Ps, h->B1hp, h->Bp, h->A, h->Ahi,
-                  h->Alo, h->Ascale, h->G2, h->G3, h->C2, h->C3, h->tc_status, h->Thi, h->Tlo, h->Tscale, h->Trows, h->Tmat, h->Srows, h->Fsig, h->Esig, h->Msig, h->FsigT, h->EsigT, h->MsigT, h->invN, h->omN, h->work, h->perm, h->chol_scratch, h->chol_status};
+                  h->Alo, h->Ascale, h->G2, h->G3, h->C2, h->C3, h->tc_status, h->Thi, h->Tlo, h->Tscale, h->Trows, h->Tmat, h->Srows, h->cosmo_d, h->Fsig, h->Esig, h->Msig, h->FsigT, h->EsigT, h->MsigT, h->invN, h->omN, h->work, h->perm, h->chol_scratch, h->chol_status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->tile_ring) cudaFree(h->tile_ring);
+  for (auto& z : h->sel) {
+    if (z.perm) cudaFree(z.perm);
+    if (z.cnt) cudaFree(z.cnt);
+    if (z.out) cudaFree(z.out);
+  }
+  if (h->piv_status) cudaFree(h->piv_status);
+  if (h->batch_C) cudaFree(h->batch_C);
+  if (h->batch_D) cudaFree(h->batch_D);
 }
 
 // Device tables that cov_init allocates for a planned handle (pointer, bytes).
@@ -247,6 +255,7 @@ static void init_allocs(cov_handle* h, std::vector<std::pair<void**, size_t>>& a
       {(void**)&h->B3, d * ntri * nchi},    {(void**)&h->RB3, d * ntri * nchi},
       {(void**)&h->B1h3, d * ntri * nchi},  {(void**)&h->Ps, d * nl * nt * nt},
       {(void**)&h->B1hp, d * ntri * nt * nt * nt},
+      {(void**)&h->cosmo_d, sizeof(cov_cosmology)},
   };
 }
 
@@ -344,6 +353,7 @@ extern "C" int cov_init(const cov_cosmology* cosmo, const cov_nz* nz, const cov_
   if (h->ntri) cudaMemcpy(h->tris_d, h->tris.data(), 4 * h->tris.size(), cudaMemcpyHostToDevice);
   e = cudaMemcpy(h->rowdesc_d, h->rowdesc.data(), 4 * h->rowdesc.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(h->scal, 0, d * SC_N);
+  if (e == cudaSuccess) e = cudaMemcpy(h->cosmo_d, &h->cosmo, sizeof(cov_cosmology), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     g_init_err = std::string("upload: ") + cudaGetErrorString(e);
     free_all(h);
@@ -372,6 +382,9 @@ extern "C" int cov_update(cov_handle* h, const cov_cosmology* cosmo, void* strea
   h->spectra_ready = false;
   h->ops_terms = -1;
   cudaStream_t s = (cudaStream_t)stream;
+  // the kernels read the cosmology from device memory; a captured batch step
+  // leaves this copy to its driver, which writes each cosmology before a replay
+  if (!h->deferred) WL_CHECK(h, cudaMemcpyAsync(h->cosmo_d, &h->cosmo, sizeof(cov_cosmology), cudaMemcpyHostToDevice, s));
   int tk = wl_stage_begin(h, ST_TABLES, s);
   int rc = wl_tables(h, s);
   wl_stage_end(h, tk, s);

@@ -177,26 +177,21 @@ static int chol_scratch(cov_handle* h, int64_t Ms, size_t* one_buf) {
 // Blocked right-looking Cholesky of the leading Ms x Ms block of the
 // workspace Wm (rows 0..Ms; row Ms carries D' along and ends up as
 // y = L^-1 D'), then (S/N)^2 for every cumulative selection as the prefix
-// sums of y^2 up to cnt[c] entries.
-static int factor_and_prefix(cov_handle* h, OutMap Wm, int64_t Ms, const std::vector<int64_t>& cnt, double* h_snr,
-                             cudaStream_t s) {
+// sums of y^2 up to cnt_d[c] entries, into out_d (device, n_ell).  Outside a
+// captured batch step the result is copied to h_snr and the status words are
+// checked; inside one (h->deferred) both stay on the device and the status
+// words accumulate over the replays.
+static int factor_and_prefix(cov_handle* h, OutMap Wm, int64_t Ms, const int64_t* cnt_d, double* out_d,
+                             double* h_snr, cudaStream_t s) {
   size_t one_buf = 0;
   int rc;
   if ((rc = chol_scratch(h, Ms, &one_buf))) return rc;
-  WL_CHECK(h, cudaMemsetAsync(h->chol_status, 0, sizeof(int), s));
-  int* st = nullptr;
-  int64_t* cnt_d = nullptr;
-  double* out_d = nullptr;
-  WL_CHECK(h, cudaMallocAsync(&st, sizeof(int), s));
-  WL_CHECK(h, cudaMallocAsync(&cnt_d, sizeof(int64_t) * h->nl, s));
-  WL_CHECK(h, cudaMallocAsync(&out_d, sizeof(double) * h->nl, s));
-  WL_CHECK(h, cudaMemsetAsync(st, 0, sizeof(int), s));
-  WL_CHECK(h, cudaMemcpyAsync(cnt_d, cnt.data(), sizeof(int64_t) * h->nl, cudaMemcpyHostToDevice, s));
+  if (!h->deferred) {
+    WL_CHECK(h, cudaMemsetAsync(h->chol_status, 0, sizeof(int), s));
+    WL_CHECK(h, cudaMemsetAsync(h->piv_status, 0, sizeof(int), s));
+  }
+  int* st = h->piv_status;
   int tk = wl_stage_begin(h, ST_SNR_CHOL, s);
-  // One panel of look-ahead: the trailing update of panel p first updates the
-  // 64 columns of panel p+1, then the FP64 diagonal block, panel solve and
-  // slicing of panel p+1 run on the side stream while the rest of the update
-  // of panel p runs here.
   uint8_t* bufs[2] = {(uint8_t*)h->chol_scratch, (uint8_t*)h->chol_scratch + one_buf};
   auto panel = [&](int64_t k0, cudaStream_t st_) -> int {
     int kb = (int)std::min<int64_t>(NB, Ms - k0);
@@ -212,7 +207,11 @@ static int factor_and_prefix(cov_handle* h, OutMap Wm, int64_t Ms, const std::ve
     int kb = (int)std::min<int64_t>(NB, Ms - k0);
     int64_t r0 = k0 + kb, r1 = Ms + 1;
     const void* buf = bufs[(k0 / NB) & 1];
-    if (r0 < Ms) {
+    if (r0 < Ms && h->chol_lookahead) {
+      // one panel of look-ahead: the trailing update of panel p first updates
+      // the 64 columns of panel p+1, then the FP64 diagonal block, panel solve
+      // and slicing of panel p+1 run on the side stream while the rest of the
+      // update of panel p runs here
       if ((rc = wl_chol_update(h, Wm, r0, r1, buf, 0, 1, h->chol_status, s))) return rc;
       WL_CHECK(h, cudaEventRecord(h->ev_cols, s));
       WL_CHECK(h, cudaStreamWaitEvent(h->side, h->ev_cols, 0));
@@ -220,6 +219,9 @@ static int factor_and_prefix(cov_handle* h, OutMap Wm, int64_t Ms, const std::ve
       WL_CHECK(h, cudaEventRecord(h->ev_panel, h->side));
       if ((rc = wl_chol_update(h, Wm, r0, r1, buf, 1, -1, h->chol_status, s))) return rc;
       WL_CHECK(h, cudaStreamWaitEvent(s, h->ev_panel, 0));
+    } else if (r0 < Ms) {
+      if ((rc = wl_chol_update(h, Wm, r0, r1, buf, 0, -1, h->chol_status, s))) return rc;
+      if ((rc = panel(r0, s))) return rc;
     } else if (r1 > r0) {
       // only the extra D row is left below this panel
       if ((rc = wl_chol_update(h, Wm, r0, r1, buf, 0, -1, h->chol_status, s))) return rc;
@@ -229,14 +231,13 @@ static int factor_and_prefix(cov_handle* h, OutMap Wm, int64_t Ms, const std::ve
   wl_stage_end(h, tk, s);
   tk = wl_stage_begin(h, ST_SNR_PREFIX, s);
   k_snr_prefix<<<h->nl, 256, 0, s>>>(Ms, Wm, cnt_d, h->nl, out_d);
+  WL_LAUNCH(h, "k_snr_prefix");
   wl_stage_end(h, tk, s);
+  if (h->deferred) return COV_OK;
   int status = 0, tstatus = 0;
   WL_CHECK(h, cudaMemcpyAsync(h_snr, out_d, sizeof(double) * h->nl, cudaMemcpyDeviceToHost, s));
   WL_CHECK(h, cudaMemcpyAsync(&status, st, sizeof(int), cudaMemcpyDeviceToHost, s));
   WL_CHECK(h, cudaMemcpyAsync(&tstatus, h->chol_status, sizeof(int), cudaMemcpyDeviceToHost, s));
-  WL_CHECK(h, cudaFreeAsync(st, s));
-  WL_CHECK(h, cudaFreeAsync(cnt_d, s));
-  WL_CHECK(h, cudaFreeAsync(out_d, s));
   WL_CHECK(h, cudaStreamSynchronize(s));
   if (tstatus) return wl_fail(h, COV_ERR_TIMEOUT, "Cholesky trailing update: a bounded mbarrier wait expired");
   if (status) return wl_fail(h, COV_ERR_NOT_PD, "Cholesky met a non-positive pivot");
@@ -247,23 +248,52 @@ static int maxbin_of(const cov_handle* h, int64_t a) {
   return h->rowdesc[8 * a] == 0 ? h->rowdesc[8 * a + 1] : h->rowdesc[8 * a + 3];
 }
 
-int wl_snr(cov_handle* h, const double* C, int64_t ldc, const double* D, int which, double* h_snr, cudaStream_t s) {
-  // host plan: selection ordered by largest ell bin (stable)
+// Device copies of a selection (slot 0..2: P, B, joint for the dense S/N;
+// slot 3: all rows, in their cumulative order, for the packed-tile S/N): the
+// reordering permutation and the prefix counts, built once per handle.
+static int selection(cov_handle* h, int slot, cudaStream_t s) {
+  if (h->sel[slot].ready) return COV_OK;
   std::vector<int> sel;
   for (int64_t a = 0; a < h->M; ++a) {
     int type = h->rowdesc[8 * a];
-    if (which == COV_WHICH_P && type != 0) continue;
-    if (which == COV_WHICH_B && type != 1) continue;
+    if (slot == COV_WHICH_P && type != 0) continue;
+    if (slot == COV_WHICH_B && type != 1) continue;
     sel.push_back((int)a);
   }
-  std::stable_sort(sel.begin(), sel.end(), [&](int x, int y) { return maxbin_of(h, x) < maxbin_of(h, y); });
+  if (slot < 3)
+    std::stable_sort(sel.begin(), sel.end(), [&](int x, int y) { return maxbin_of(h, x) < maxbin_of(h, y); });
   int64_t Ms = (int64_t)sel.size();
   std::vector<int64_t> cnt(h->nl, 0);
   for (int c = 0; c < h->nl; ++c)
     for (int64_t i = 0; i < Ms; ++i)
       if (maxbin_of(h, sel[i]) <= c) cnt[c] = i + 1;
+  auto& z = h->sel[slot];
+  if (!z.perm) {
+    WL_CHECK(h, cudaMalloc(&z.perm, sizeof(int) * (size_t)std::max<int64_t>(Ms, 1)));
+    WL_CHECK(h, cudaMalloc(&z.cnt, sizeof(int64_t) * h->nl));
+    WL_CHECK(h, cudaMalloc(&z.out, sizeof(double) * h->nl));
+    h->allocated += sizeof(int) * (size_t)std::max<int64_t>(Ms, 1) + sizeof(int64_t) * h->nl + sizeof(double) * h->nl;
+  }
+  if (!h->piv_status) {
+    WL_CHECK(h, cudaMalloc(&h->piv_status, sizeof(int)));
+    WL_CHECK(h, cudaMemsetAsync(h->piv_status, 0, sizeof(int), s));
+  }
+  if (Ms) WL_CHECK(h, cudaMemcpyAsync(z.perm, sel.data(), sizeof(int) * Ms, cudaMemcpyHostToDevice, s));
+  WL_CHECK(h, cudaMemcpyAsync(z.cnt, cnt.data(), sizeof(int64_t) * h->nl, cudaMemcpyHostToDevice, s));
+  WL_CHECK(h, cudaStreamSynchronize(s));  // sel and cnt are host memory read by the copies
+  z.Ms = Ms;
+  z.ready = true;
+  return COV_OK;
+}
+
+int wl_snr(cov_handle* h, const double* C, int64_t ldc, const double* D, int which, double* h_snr, cudaStream_t s) {
+  int rc;
+  if ((rc = selection(h, which, s))) return rc;
+  const auto& z = h->sel[which];
+  const int64_t Ms = z.Ms;
   if (Ms == 0) {
-    for (int c = 0; c < h->nl; ++c) h_snr[c] = nan("");
+    if (h_snr)
+      for (int c = 0; c < h->nl; ++c) h_snr[c] = nan("");
     return COV_OK;
   }
   int64_t ldw = Ms + 1;
@@ -281,19 +311,12 @@ int wl_snr(cov_handle* h, const double* C, int64_t ldc, const double* D, int whi
     h->work_n = need;
     h->allocated += sizeof(double) * need;
   }
-  if (!h->perm) {
-    WL_CHECK(h, cudaMalloc(&h->perm, sizeof(int) * h->M));
-    h->allocated += sizeof(int) * h->M;
-  }
-  WL_CHECK(h, cudaMemcpyAsync(h->perm, sel.data(), sizeof(int) * Ms, cudaMemcpyHostToDevice, s));
   dim3 gp((unsigned)(Ms + 1), (unsigned)((Ms + 1 + 255) / 256));
   int tk = wl_stage_begin(h, ST_SNR_PACK, s);
-  k_snr_pack<<<gp, 256, 0, s>>>(Ms, h->perm, C, ldc, D, h->work, ldw);
+  k_snr_pack<<<gp, 256, 0, s>>>(Ms, z.perm, C, ldc, D, h->work, ldw);
   WL_LAUNCH(h, "k_snr_pack");
   wl_stage_end(h, tk, s);
-  int rc = factor_and_prefix(h, out_rows(h->work, ldw), Ms, cnt, h_snr, s);
-  WL_CHECK(h, cudaStreamSynchronize(s));  // sel is host memory read by an async copy
-  return rc;
+  return factor_and_prefix(h, out_rows(h->work, ldw), Ms, z.cnt, z.out, h_snr, s);
 }
 
 // In place on the lower-packed tiles (rows in cumulative order): Jacobi
@@ -326,10 +349,8 @@ __global__ void k_tiles_scale(int64_t M, OutMap W, const double* dg, const doubl
 
 int wl_snr_tiles(cov_handle* h, double* Ct, const double* D, double* h_snr, cudaStream_t s) {
   const int64_t M = h->M;
-  std::vector<int64_t> cnt(h->nl, 0);
-  for (int c = 0; c < h->nl; ++c)
-    for (int64_t a = 0; a < M; ++a)
-      if (maxbin_of(h, a) <= c) cnt[c] = a + 1;
+  int rc;
+  if ((rc = selection(h, 3, s))) return rc;
   OutMap Wm = out_tiles(Ct, 0);
   double* dg = nullptr;
   WL_CHECK(h, cudaMallocAsync(&dg, sizeof(double) * M, s));
@@ -340,6 +361,5 @@ int wl_snr_tiles(cov_handle* h, double* Ct, const double* D, double* h_snr, cuda
   WL_LAUNCH(h, "k_tiles_scale");
   wl_stage_end(h, tk, s);
   WL_CHECK(h, cudaFreeAsync(dg, s));
-  int rc = factor_and_prefix(h, Wm, M, cnt, h_snr, s);
-  return rc;
+  return factor_and_prefix(h, Wm, M, h->sel[3].cnt, h->sel[3].out, h_snr, s);
 }

@@ -17,7 +17,8 @@
 //     FP64 and subtracts v from the FP64 trailing matrix (coalesced stores; the
 //     tile was copied to shared memory during the MMAs).
 //
-// One CTA (128 threads) per tile: warp 0 / lane 0 loads the 6 I-slices
+// One CTA (128 threads) per lower tile (no blocks for tiles above the
+// diagonal): warp 0 / lane 0 loads the 6 I-slices
 // (128 x 64) and 6 J-slices (64 x 64) with TMA (128B swizzle) in one stage,
 // warp 1 / lane 0 issues the MMAs, all four warps run the epilogue.  Waits are
 // bounded (status word, COV_ERR_TIMEOUT).
@@ -111,14 +112,66 @@ __device__ __forceinline__ void cs_tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// grid.x = tile row (128 rows), grid.y = tile column (64 columns) - tj0
+// RN(a) 2^ex as an FP64 value, for |a| < 2^63, by integer operations: the
+// leading bit sets the exponent, the 53 leading bits (rounded to nearest,
+// ties to even, as the FP64 conversion rounds) the significand.  Results
+// outside the normal range take the FP64 path.
+__device__ __forceinline__ double scaled_to_double(long long a, int ex) {
+  if (a == 0) return 0.0;
+  unsigned long long sign = a < 0 ? (1ull << 63) : 0ull;
+  unsigned long long u = a < 0 ? (unsigned long long)(-a) : (unsigned long long)a;
+  int msb = 63 - __clzll((long long)u);
+  unsigned long long m;
+  if (msb <= 52) {
+    m = u << (52 - msb);
+  } else {
+    int sh = msb - 52;
+    m = u >> sh;
+    unsigned long long rem = u & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (m & 1ull))) ++m;
+    if (m >> 53) {
+      m >>= 1;
+      ++msb;
+    }
+  }
+  int e = msb + ex + 1023;
+  if (e <= 0 || e >= 2047) return ldexp((double)a, ex);
+  return __longlong_as_double((long long)(sign | ((unsigned long long)e << 52) | (m & ((1ull << 52) - 1))));
+}
+
+// Lower tiles of one update launch, row by row: tile row ti (128 rows, from
+// ti0 = tj0 * 64 / 128) holds the column tiles tj0 .. min(tj0 + ntj - 1,
+// 2 ti + 1) (64 columns each).  cum(ti) counts the tiles of rows ti0 .. ti-1.
+struct TileRows {
+  int tj0, ntj, ti0, nti;
+  __host__ __device__ int64_t cnt(int64_t i) const {
+    int64_t c = 2 * i + 2 - tj0;
+    return c < ntj ? c : ntj;
+  }
+  __host__ __device__ int64_t cum(int64_t ti) const {
+    // rows below i_star = ceil((ntj + tj0 - 2) / 2) grow by two tiles per row; the rest hold ntj
+    int64_t istar = (ntj + tj0 - 2 + 1) / 2;
+    if (istar < ti0) istar = ti0;
+    int64_t b = ti < istar ? ti : istar, a = ti0;
+    int64_t tri = b > a ? (b - a) * (2 - tj0) + (b * (b - 1) - a * (a - 1)) : 0;
+    int64_t rect = ti > istar ? (ti - istar) * (int64_t)ntj : 0;
+    return tri + rect;
+  }
+};
+
 __global__ void __launch_bounds__(128, 1)
     k_chol_update(const __grid_constant__ CUtensorMap map_i, const __grid_constant__ CUtensorMap map_j,
                   int64_t nrows, int64_t nrows_pad, const int* __restrict__ rexp, OutMap W, int64_t r0, int* status,
-                  int tj0) {
-  int tj = blockIdx.y + tj0;
-  int ti = blockIdx.x + (tj0 * CS_BJ) / CS_BI;
-  if ((int64_t)tj * CS_BJ > (int64_t)ti * CS_BI + CS_BI - 1) return;  // tile above the diagonal
+                  TileRows tr) {
+  // the launch holds only lower tiles: find the row of this block by bisection
+  const int64_t id = blockIdx.x;
+  int64_t lo = tr.ti0, hi = tr.ti0 + tr.nti;  // cum(lo) <= id < cum(hi)
+  while (hi - lo > 1) {
+    int64_t mid = (lo + hi) >> 1;
+    if (tr.cum(mid) <= id) lo = mid; else hi = mid;
+  }
+  const int ti = (int)lo;
+  const int tj = tr.tj0 + (int)(id - tr.cum(lo));
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar;
   __shared__ __align__(8) uint64_t acc_bar;
@@ -235,9 +288,10 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
         for (int jj = 0; jj < 32; ++jj) acc[jj] = (acc[jj] << 8) + (long long)__float2int_rn(v[jj]);
       }
-      // value = acc 2^(e_i + e_j - 14 - 8 (S - 1)); the e_j part is applied per column below
+      // value = acc 2^(e_i + e_j - 14 - 8 (S - 1)), applied per element below
+      long long* stg_i = (long long*)stg;
 #pragma unroll
-      for (int jj = 0; jj < 32; ++jj) stg[lane * 33 + jj] = (double)acc[jj];
+      for (int jj = 0; jj < 32; ++jj) stg_i[lane * 33 + jj] = acc[jj];
       __syncwarp();
       int64_t gj = (int64_t)row_j + c * 32 + lane;
       int ej = (gj < nrows) ? rexp[gj] : 0;
@@ -246,11 +300,13 @@ __global__ void __launch_bounds__(128, 1)
         int lr = warp * 32 + rr;
         int64_t gr = (int64_t)row_i + lr;
         if (gr < nrows && gj < nrows && gj <= gr) {
-          int er = rexp_sh[lr];
-          // exact power of two 2^(e_r + e_j - 14 - 40) built from its exponent bits
-          int ex = er + ej - 54;
-          double sc = (ex > -1000 && ex < 1000) ? __longlong_as_double((long long)(ex + 1023) << 52) : ldexp(1.0, ex);
-          *W.at(r0 + gr, r0 + gj) = ctile[lr * CS_BJ + c * 32 + lane] - stg[rr * 33 + lane] * sc;
+          int ex = rexp_sh[lr] + ej - 54;
+          // the FP64 pipe is scarce on this part: the rounded conversion of the
+          // integer and the power-of-two scaling are done with integer ops, so
+          // only the subtraction runs on it
+          double v = scaled_to_double(stg_i[rr * 33 + lane], ex);
+          double* p = W.at(r0 + gr, r0 + gj);
+          *p = ctile[lr * CS_BJ + c * 32 + lane] - v;
         }
       }
       __syncwarp();
@@ -318,10 +374,15 @@ int wl_chol_update(cov_handle* h, OutMap W, int64_t r0, int64_t r1, const void* 
         return (int)cudaFuncSetAttribute(k_chol_update, cudaFuncAttributeMaxDynamicSharedMemorySize, CS_SMEM);
       }) != 0)
     return wl_fail(h, COV_ERR_CUDA, "cudaFuncSetAttribute(k_chol_update) failed");
-  // only tile rows that reach the requested columns
-  int ti0 = (int)(((int64_t)tj0 * CS_BJ) / CS_BI);
-  dim3 grid((unsigned)(pad / CS_BI - ti0), (unsigned)ntj);
-  k_chol_update<<<grid, 128, CS_SMEM, s>>>(mi, mj, n, pad, rexp, W, r0, status, tj0);
+  // only the lower tiles of the tile rows that reach the requested columns
+  TileRows tr;
+  tr.tj0 = tj0;
+  tr.ntj = ntj;
+  tr.ti0 = (int)(((int64_t)tj0 * CS_BJ) / CS_BI);
+  tr.nti = (int)(pad / CS_BI) - tr.ti0;
+  if (tr.nti <= 0) return COV_OK;
+  int64_t nblk = tr.cum(tr.ti0 + tr.nti);
+  k_chol_update<<<(unsigned)nblk, 128, CS_SMEM, s>>>(mi, mj, n, pad, rexp, W, r0, status, tr);
   WL_LAUNCH(h, "k_chol_update");
   return COV_OK;
 }

@@ -162,6 +162,19 @@ struct cov_handle {
   int* chol_status = nullptr;
   bool spectra_ready = false;
   int row_set = 0, row_order = 0;  // COV_ROWS_*, COV_ORDER_*
+  cov_cosmology* cosmo_d = nullptr;  // the cosmology the kernels read (device copy of cosmo)
+  bool deferred = false;  // inside a captured batch step: no host synchronisation, no host-side copies
+  bool chol_lookahead = true;  // Cholesky panel look-ahead on the side stream
+  int tc_kernel = -1;          // contraction kernel: -1 automatic, 0 one CTA per tile, 1 2 x 2 clusters
+  struct Selection {           // cumulative S/N selections (P, B, joint; all rows in place)
+    bool ready = false;
+    int64_t Ms = 0;
+    int* perm = nullptr;
+    int64_t* cnt = nullptr;
+    double* out = nullptr;
+  } sel[4];
+  int* piv_status = nullptr;  // non-positive pivot seen (sticky inside a batch)
+  double *batch_C = nullptr, *batch_D = nullptr;  // covariance and data vector of cov_batch_snr
   int ops_terms = -1, ops_precision = -1;  // operands prepared for the band assembly (-1: none)
   bool prof = false;
   std::vector<StageEvent> pending;

@@ -12,9 +12,10 @@
 
 // One warp per (ell bin, node): I_2^0(k,k), I_1^1(k), I_2^1(k,k) -> P^HM and
 // its response; the k_max rule zeroes everything beyond k_max.
-__global__ void k_pspec(cov_cosmology c, int nl, int nchi, int nm, double kmax, const double* ell, const double* chi,
+__global__ void k_pspec(const cov_cosmology* __restrict__ cosmo_p, int nl, int nchi, int nm, double kmax, const double* ell, const double* chi,
                         const double* m, const double* om, const double* f, const double* b1, const double* U,
                         const double* Pl, const double* dPl, double* P3, double* RP3) {
+  const cov_cosmology c = *cosmo_p;
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= nl * nchi) return;
   int b = warp / nchi, n = warp % nchi;
@@ -66,11 +67,12 @@ __device__ __forceinline__ double bpt_shift(const double* k, const double* P, in
 }
 
 // One warp per (triple, node): B^HM, its response and the 1-halo B.
-__global__ void k_bspec(cov_cosmology c, int ntri, int nchi, int nm, double kmax, const int32_t* tris,
+__global__ void k_bspec(const cov_cosmology* __restrict__ cosmo_p, int ntri, int nchi, int nm, double kmax, const int32_t* tris,
                         const double* ell, const double* chi, const double* D, const double* m, const double* om,
                         const double* f, const double* b1, const double* b2, const double* U, const double* Pl,
                         const double* dPl, const double* Psh, const double* scal, double* B3, double* RB3,
                         double* B1h3) {
+  const cov_cosmology c = *cosmo_p;
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= ntri * nchi) return;
   int t = warp / nchi, n = warp % nchi;
@@ -206,9 +208,10 @@ __global__ void k_datavec(int64_t M, int nchi, const int32_t* rd, const double* 
 
 // 1-halo factor rows A[a][(n,q)] = sqrt(w_n omega_q f_nq / Omega) chi^(1-2mu)
 // prod W (m_q/rho)^mu prod U; grid (row blocks of K), coalesced along K.
-__global__ void k_rows_a(int64_t M, int nchi, int nm, double inv_omega, double rho, const int32_t* rd,
+__global__ void k_rows_a(int64_t M, int nchi, int nm, double inv_omega, const cov_cosmology* __restrict__ cosmo_p, const int32_t* rd,
                          const double* chi, const double* wchi, const double* W, const double* m, const double* om,
                          const double* f, const double* U, double* A) {
+  const double rho = WL_RHO_CRIT0 * cosmo_p->Om;
   int64_t a = blockIdx.x;
   int K = nchi * nm;
   int kk = blockIdx.y * blockDim.x + threadIdx.x;
@@ -228,9 +231,10 @@ __global__ void k_rows_a(int64_t M, int nchi, int nm, double inv_omega, double r
 }
 
 // trispectrum rows for leg pairs (L1 <= L2), L = bin * nt + tomo
-__global__ void k_rows_t(int nleg, int nt, int nchi, int nm, double rho, const double* chi, const double* wchi,
+__global__ void k_rows_t(int nleg, int nt, int nchi, int nm, const cov_cosmology* __restrict__ cosmo_p, const double* chi, const double* wchi,
                          const double* W, const double* m, const double* om, const double* f, const double* U,
                          double* Tr) {
+  const double rho = WL_RHO_CRIT0 * cosmo_p->Om;
   int64_t r = blockIdx.x;
   int K = nchi * nm;
   int kk = blockIdx.y * blockDim.x + threadIdx.x;
@@ -271,7 +275,7 @@ __global__ void k_rows_s(int64_t M, int nchi, const int32_t* rd, const double* c
 }
 
 int wl_spectra(cov_handle* h, double* d_D, cudaStream_t s) {
-  const cov_cosmology c = h->cosmo;
+  const cov_cosmology* c = h->cosmo_d;
   int nl = h->nl, nchi = h->nchi, nm = h->nm, nt = h->nt;
   double kmax = h->bins.k_max;
   int warps = nl * nchi;
@@ -296,18 +300,16 @@ int wl_spectra(cov_handle* h, double* d_D, cudaStream_t s) {
 }
 
 int wl_rows_a(cov_handle* h, cudaStream_t s) {
-  double rho = WL_RHO_CRIT0 * h->cosmo.Om;
   dim3 g((unsigned)h->M, (h->K + 255) / 256);
-  k_rows_a<<<g, 256, 0, s>>>(h->M, h->nchi, h->nm, 1.0 / h->omega, rho, h->rowdesc_d, h->chi, h->wchi, h->W, h->m,
+  k_rows_a<<<g, 256, 0, s>>>(h->M, h->nchi, h->nm, 1.0 / h->omega, h->cosmo_d, h->rowdesc_d, h->chi, h->wchi, h->W, h->m,
                              h->om, h->f, h->U, h->A);
   WL_LAUNCH(h, "k_rows_a");
   return COV_OK;
 }
 
 int wl_rows_t(cov_handle* h, cudaStream_t s) {
-  double rho = WL_RHO_CRIT0 * h->cosmo.Om;
   dim3 g((unsigned)h->ntrow, (h->K + 255) / 256);
-  k_rows_t<<<g, 256, 0, s>>>(h->nleg, h->nt, h->nchi, h->nm, rho, h->chi, h->wchi, h->W, h->m, h->om, h->f, h->U,
+  k_rows_t<<<g, 256, 0, s>>>(h->nleg, h->nt, h->nchi, h->nm, h->cosmo_d, h->chi, h->wchi, h->W, h->m, h->om, h->f, h->U,
                              h->Trows);
   WL_LAUNCH(h, "k_rows_t");
   return COV_OK;

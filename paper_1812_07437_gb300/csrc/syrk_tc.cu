@@ -40,9 +40,10 @@ __device__ __forceinline__ int64_t blk_off(int64_t r, int k, int nk) {
 // Per-(n, q) and per-n factors of the 1-halo rows, so that the row builder
 // needs only products: g_mu[n][q] = sqrt(w_n omega_q f_nq / Omega) (m_q/rho)^mu
 // and c_mu[n] = chi_n^(1 - 2 mu), for mu = 2 (P rows) and 3 (B rows).
-__global__ void k_rows_prep(int nchi, int nm, double inv_omega, double rho, const double* chi, const double* wchi,
+__global__ void k_rows_prep(int nchi, int nm, double inv_omega, const cov_cosmology* __restrict__ cosmo_p, const double* chi, const double* wchi,
                             const double* m, const double* om, const double* f, double* g2, double* g3, double* c2,
                             double* c3) {
+  const double rho = WL_RHO_CRIT0 * cosmo_p->Om;
   int kk = blockIdx.x * blockDim.x + threadIdx.x;
   if (kk >= nchi * nm) return;
   int n = kk / nm, q = kk % nm;
@@ -350,7 +351,7 @@ __device__ __forceinline__ void tri_tile_tc(int64_t id, int64_t* ti, int64_t* tj
 #define TW_STAGE_BYTES (4 * TW_OP_BYTES)             // 64 KB
 #define TW_SMEM (TW_STAGES * TW_STAGE_BYTES + 1024)
 
-#define TW_PREFETCH 16
+#define TW_PREFETCH 4
 
 // TMA prefetch of one box into L2 (no shared memory, no completion signal)
 __device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int c0, int c1) {
@@ -764,7 +765,6 @@ static int zero_last_tile(cov_handle* h, void* base, int64_t rows, int K, cudaSt
 }
 
 int wl_rows_split(cov_handle* h, int nssc, cudaStream_t s) {
-  double rho = WL_RHO_CRIT0 * h->cosmo.Om;
   int Kt = h->K + nssc;
   int nsig = h->nl + h->ntri;
   int rc;
@@ -775,7 +775,7 @@ int wl_rows_split(cov_handle* h, int nssc, cudaStream_t s) {
     return rc;
   if ((rc = zero_last_tile(h, h->Ahi, h->M, Kt, s))) return rc;
   if ((rc = zero_last_tile(h, h->Alo, h->M, Kt, s))) return rc;
-  k_rows_prep<<<(h->K + 255) / 256, 256, 0, s>>>(h->nchi, h->nm, 1.0 / h->omega, rho, h->chi, h->wchi, h->m, h->om,
+  k_rows_prep<<<(h->K + 255) / 256, 256, 0, s>>>(h->nchi, h->nm, 1.0 / h->omega, h->cosmo_d, h->chi, h->wchi, h->m, h->om,
                                                    h->f, h->G2, h->G3, h->C2, h->C3);
   WL_LAUNCH(h, "k_rows_prep");
   k_rows_sig<<<dim3((unsigned)nsig, (unsigned)h->nchi), 128, 0, s>>>(h->nl, h->ntri, h->nchi, h->nm, h->tris_d, h->U,
@@ -801,7 +801,6 @@ int wl_rows_split(cov_handle* h, int nssc, cudaStream_t s) {
 // BF16 hi/lo trispectrum rows straight from the pair signatures (no FP64
 // row array): the PT term's table T = rows rows^T in the split form.
 int wl_trows_split(cov_handle* h, cudaStream_t s) {
-  double rho = WL_RHO_CRIT0 * h->cosmo.Om;
   int npair = h->nl * (h->nl + 1) / 2;
   int rc;
   if ((rc = wl_ensure(h, (void**)&h->FsigT, sizeof(float) * (size_t)npair * h->K, "pair signature table")))
@@ -816,7 +815,7 @@ int wl_trows_split(cov_handle* h, cudaStream_t s) {
   if ((rc = wl_ensure(h, (void**)&h->C3, sizeof(double) * h->nchi, "row factor table"))) return rc;
   if ((rc = zero_last_tile(h, h->Thi, h->ntrow, h->K, s))) return rc;
   if ((rc = zero_last_tile(h, h->Tlo, h->ntrow, h->K, s))) return rc;
-  k_rows_prep<<<(h->K + 255) / 256, 256, 0, s>>>(h->nchi, h->nm, 1.0 / h->omega, rho, h->chi, h->wchi, h->m, h->om,
+  k_rows_prep<<<(h->K + 255) / 256, 256, 0, s>>>(h->nchi, h->nm, 1.0 / h->omega, h->cosmo_d, h->chi, h->wchi, h->m, h->om,
                                                    h->f, h->G2, h->G3, h->C2, h->C3);
   WL_LAUNCH(h, "k_rows_prep");
   k_rows_sig<<<dim3((unsigned)npair, (unsigned)h->nchi), 128, 0, s>>>(h->nl, h->ntri, h->nchi, h->nm, h->tris_d, h->U,
@@ -923,7 +922,7 @@ static int launch_tc(cov_handle* h, const void* hi, const void* lo, const double
   if (t1 <= t0) return COV_OK;
   const int2* tiles = nullptr;
   int64_t nblk = 0;
-  if (mc_clusters_ok()) {
+  if (h->tc_kernel != 0 && mc_clusters_ok()) {
     CUtensorMap chi, clo;
     if ((rc = make_map(h, &chi, (void*)hi, rows, Kp, MC_BOX_ROWS))) return rc;
     if ((rc = make_map(h, &clo, (void*)lo, rows, Kp, MC_BOX_ROWS))) return rc;
@@ -951,6 +950,7 @@ static int launch_tc(cov_handle* h, const void* hi, const void* lo, const double
 // The contraction kernels raise a device status word when a bounded wait
 // expires; it is cleared before a group of launches and read after them.
 int wl_tc_status_reset(cov_handle* h, cudaStream_t s) {
+  if (h->deferred) return COV_OK;  // inside a captured batch step the word accumulates over replays
   if (!h->tc_status) {
     WL_CHECK(h, cudaMalloc(&h->tc_status, sizeof(int)));
     h->allocated += sizeof(int);
@@ -960,6 +960,7 @@ int wl_tc_status_reset(cov_handle* h, cudaStream_t s) {
 }
 
 int wl_tc_status_check(cov_handle* h, cudaStream_t s) {
+  if (h->deferred) return COV_OK;  // read by the batch driver after the replays
   int st = 0;
   WL_CHECK(h, cudaMemcpyAsync(&st, h->tc_status, sizeof(int), cudaMemcpyDeviceToHost, s));
   WL_CHECK(h, cudaStreamSynchronize(s));

@@ -112,6 +112,24 @@ class Handle:
                                      out.ctypes.data_as(C.c_void_p), _stream_ptr(stream)), self.h)
         return out
 
+    def batch_snr(self, cosmologies, terms=N.COV_TERMS_ALL, precision=N.COV_SPLIT_BF16, with_D=False, tune=False,
+                  stream=None):
+        """Cumulative S/N (and optionally D) for a list of cosmology dicts.
+
+        Returns (snr [n, 3, n_ell] in the order P, B, joint; D [n, M] or None; tuning/timing dict)."""
+        n = len(cosmologies)
+        arr = (N.cov_cosmology * n)(*[N.cov_cosmology(*(float(c[k]) for k in ("Om", "Ob", "h", "ns", "sigma8", "w0",
+                                                                           "Tcmb"))) for c in cosmologies])
+        snr = np.zeros((n, 3, self.n_ell), dtype=np.float64)
+        D = np.zeros((n, self.M), dtype=np.float64) if with_D else None
+        info = N.cov_batch_info()
+        N.check(self.L.cov_batch_snr(self.h, arr, n, terms, precision,
+                                     D.ctypes.data_as(C.c_void_p) if with_D else None, snr.ctypes.data_as(C.c_void_p),
+                                     N.COV_BATCH_TUNE if tune else 0, C.byref(info), _stream_ptr(stream)), self.h)
+        d = {f: getattr(info, f) for f, _ in N.cov_batch_info._fields_}
+        d["candidate_ms"] = list(info.candidate_ms)
+        return snr, D, d
+
 
 def packed_tiles(rows):
     """Number of 256 x 256 lower tiles holding rows 0..rows-1."""

@@ -43,7 +43,7 @@ COV_ORDER_CUMULATIVE = 1
 
 EXPORTED = ["cov_init", "cov_update", "cov_layout", "cov_counts", "cov_spectra", "cov_assemble", "cov_snr",
             "cov_assemble_band", "cov_table", "cov_profile", "cov_stage_times", "cov_stage_name", "cov_snr_noalloc",
-            "cov_last_error", "cov_free", "cov_snr_tiles", "cov_server_create", "cov_server_submit", "cov_server_wait",
+            "cov_last_error", "cov_free", "cov_snr_tiles", "cov_batch_snr", "cov_server_create", "cov_server_submit", "cov_server_wait",
             "cov_server_error", "cov_server_stats_get", "cov_server_clock", "cov_request_footprint",
             "cov_server_free"]
 
@@ -74,6 +74,14 @@ class cov_bins(C.Structure):
 
 class cov_opts(C.Structure):
     _fields_ = [("device", C.c_int), ("hbm_budget", C.c_size_t), ("rows", C.c_int), ("order", C.c_int)]
+
+
+COV_BATCH_TUNE = 1
+
+
+class cov_batch_info(C.Structure):
+    _fields_ = [("tc_kernel", C.c_int), ("chol_lookahead", C.c_int), ("candidate_ms", C.c_double * 4),
+                ("first_ms", C.c_double), ("capture_ms", C.c_double), ("replay_ms", C.c_double)]
 
 
 class cov_server_opts(C.Structure):
@@ -119,6 +127,8 @@ def lib():
         L.cov_snr.argtypes = [P, P, i64, P, C.c_int, P, P]
         L.cov_assemble_band.argtypes = [P, i64, i64, P, i64, C.c_int, C.c_uint, C.c_int, P]
         L.cov_snr_tiles.argtypes = [P, P, P, P, P]
+        L.cov_batch_snr.argtypes = [P, C.POINTER(cov_cosmology), C.c_int, C.c_uint, C.c_int, P, P, C.c_uint,
+                                    C.POINTER(cov_batch_info), P]
         L.cov_table.argtypes = [P, C.c_char_p, P, C.POINTER(i64), P]
         L.cov_profile.argtypes = [P, C.c_int]
         L.cov_stage_times.argtypes = [P, P, P, C.c_int]

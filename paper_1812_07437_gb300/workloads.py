@@ -91,3 +91,30 @@ def serving_requests(n, rate_hz, seed=2024, n_chi=128, n_mass=96):
         wl["cosmology"] = cos
         out.append((float(t[k]), wl))
     return out
+
+
+def fisher_workload(n_tomo, n_ell=16, n_chi=256, n_mass=128):
+    """The batched Fisher set-up: 16 log ell bins on [10, 5000], N_chi = 256,
+    N_M = 128, photo-z scatter 0.05 (1+z), every covariance term."""
+    return _wl(f"fisher_{n_tomo}bin", n_tomo, 0.05, n_ell, 10.0, 5000.0, n_chi, n_mass, TERMS_ALL)
+
+
+def fisher_cosmologies(seed=12345, n=64):
+    """The fiducial cosmology, +-1% and +-2% steps in each of Omega_m, sigma_8,
+    w0, h, n_s and Omega_b (24 points), then uniform draws within +-5% of the
+    fiducial in all six (seeded) up to n cosmologies."""
+    import numpy as np
+    keys = ["Om", "sigma8", "w0", "h", "ns", "Ob"]
+    out = [dict(FIDUCIAL)]
+    for k in keys:
+        for step in (0.01, -0.01, 0.02, -0.02):
+            c = dict(FIDUCIAL)
+            c[k] *= 1.0 + step
+            out.append(c)
+    rng = np.random.default_rng(seed)
+    while len(out) < n:
+        c = dict(FIDUCIAL)
+        for k in keys:
+            c[k] *= 1.0 + rng.uniform(-0.05, 0.05)
+        out.append(c)
+    return out[:n]

@@ -54,6 +54,9 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.cov_snr(None, None, 0, None, 0, None, None) == N.COV_ERR_INVALID
     assert lib.cov_assemble_band(None, 0, 256, None, 0, N.COV_LAYOUT_TILES, N.COV_TERMS_ALL, N.COV_SPLIT_BF16,
                                  None) == N.COV_ERR_INVALID
+    assert lib.cov_batch_snr(None, None, 0, N.COV_TERMS_ALL, N.COV_SPLIT_BF16, None, None, 0, None,
+                             None) == N.COV_ERR_INVALID
+    assert lib.cov_snr_tiles(None, None, None, None, None) == N.COV_ERR_INVALID
 
 
 def test_tile_layout_addressing_covers_the_lower_triangle():
