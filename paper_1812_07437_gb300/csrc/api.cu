@@ -207,6 +207,8 @@ static void free_all(cov_handle* h) {
   if (h->ev_cols) cudaEventDestroy(h->ev_cols);
   if (h->ev_panel) cudaEventDestroy(h->ev_panel);
   if (h->side) cudaStreamDestroy(h->side);
+  if (h->batch_stream) cudaStreamDestroy(h->batch_stream);
+  if (h->batch_ev) cudaEventDestroy(h->batch_ev);
   h->pending.clear();
   h->pool.clear();
   void* ptrs[] = {h->gl64x, h->gl64w, h->glkx, h->glkw, h->glcx, h->glcw, h->scal, h->chi, h->wchi, h->z, h->D,

@@ -46,7 +46,15 @@ extern "C" int cov_batch_snr(cov_handle* h, const cov_cosmology* cosmos, int n, 
     return wl_fail(h, COV_ERR_INVALID, "cov_batch_snr: bad cosmologies, outputs, terms, precision or flags");
   if ((terms & COV_TERM_SSC) && !(terms & COV_TERM_1H) && precision != COV_FP64)
     return wl_fail(h, COV_ERR_INVALID, "cov_batch_snr: COV_TERM_SSC needs COV_TERM_1H in the split form");
-  cudaStream_t s = (cudaStream_t)stream;
+  // The batch runs on a stream of its own (a capture cannot record the legacy
+  // default stream), ordered after the caller's stream; it returns when done.
+  if (!h->batch_stream) {
+    WL_CHECK(h, cudaStreamCreateWithFlags(&h->batch_stream, cudaStreamNonBlocking));
+    WL_CHECK(h, cudaEventCreateWithFlags(&h->batch_ev, cudaEventDisableTiming));
+  }
+  WL_CHECK(h, cudaEventRecord(h->batch_ev, (cudaStream_t)stream));
+  WL_CHECK(h, cudaStreamWaitEvent(h->batch_stream, h->batch_ev, 0));
+  cudaStream_t s = h->batch_stream;
   const int64_t M = h->M;
   const int nl = h->nl;
   int rc;

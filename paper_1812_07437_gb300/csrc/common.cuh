@@ -175,6 +175,8 @@ struct cov_handle {
   } sel[4];
   int* piv_status = nullptr;  // non-positive pivot seen (sticky inside a batch)
   double *batch_C = nullptr, *batch_D = nullptr;  // covariance and data vector of cov_batch_snr
+  cudaStream_t batch_stream = nullptr;             // cov_batch_snr runs (and captures) on this stream
+  cudaEvent_t batch_ev = nullptr;
   int ops_terms = -1, ops_precision = -1;  // operands prepared for the band assembly (-1: none)
   bool prof = false;
   std::vector<StageEvent> pending;
