@@ -97,19 +97,16 @@ __device__ __forceinline__ uint64_t cs_desc_sw128(uint32_t saddr) {
   return d;
 }
 
-__device__ __forceinline__ void cs_tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
+__device__ __forceinline__ void cs_tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
-      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // RN(a) 2^ex as an FP64 value, for |a| < 2^63, by integer operations: the
@@ -200,16 +197,21 @@ __global__ void __launch_bounds__(128, 1)
   double* ctile = (double*)(smem + CS_STAGE);  // [128][64] FP64 copy of the trailing tile
   if (warp >= 2) {
     // warps 2-3 stream the FP64 tile into shared memory while the slices load
-    // and the MMAs run (8-byte cp.async, coalesced along each row)
-    int t = threadIdx.x - 64;
-    for (int e = t; e < CS_BI * CS_BJ; e += 64) {
-      int rr = e / CS_BJ, cc = e % CS_BJ;
-      int64_t gr = (int64_t)row_i + rr, gc = (int64_t)row_j + cc;
+    // and the MMAs run: thread t copies column t down the 128 rows (8-byte
+    // cp.async, coalesced across the threads), stepping its source address
+    // by the row stride and recomputing it only where a new tile row begins
+    const int t = threadIdx.x - 64;
+    const int64_t gc = (int64_t)row_j + t, ac = r0 + gc;
+    const int64_t stride = W.tiled ? 256 : W.ldc;
+    const double* src = nullptr;
+    for (int rr = 0; rr < CS_BI; ++rr) {
+      const int64_t gr = (int64_t)row_i + rr, ar = r0 + gr;
       if (gr < nrows && gc < nrows && gc <= gr) {
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(cs_smem_u32(ctile + e)),
-                     "l"(W.at(r0 + gr, r0 + gc))
+        if (!src || (W.tiled && (ar & 255) == 0)) src = W.at(ar, ac);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(cs_smem_u32(ctile + rr * CS_BJ + t)), "l"(src)
                      : "memory");
       }
+      if (src) src += stride;
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   } else if (warp == 0 && lane == 0) {
@@ -272,42 +274,54 @@ __global__ void __launch_bounds__(128, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncthreads();
   if (have && *(volatile int*)status == 0) {
-    double* stg = (double*)smem + warp * (32 * 33);
+    // 16 columns at a time: each thread first owns one row (TMEM lane) and
+    // combines the six exact group sums a_g (|a_g| < 2^23) into
+    // v = sum_g a_g 2^(8 (5 - g)) = ((p0 2^16) + p1) 2^16 + p2 with the int32
+    // pairs p = a_(2k) 2^8 + a_(2k+1) (|p| < 2^31); the values are then
+    // staged so that each thread owns one column and 16 consecutive rows for
+    // the coalesced read-modify-write of the FP64 tile.
+    long long* stg = (long long*)smem + warp * (32 * 17);
+    const int jc = lane & 15, rh = lane >> 4;
+    const int64_t stride = W.tiled ? 256 : W.ldc;
 #pragma unroll 1
-    for (int c = 0; c < CS_BJ / 32; ++c) {
-      // the six group sums are exact integers (< 2^23, so int32 conversions
-      // are exact and stay off the FP64 pipe): combine them exactly in int64,
-      // v = sum_g acc_g 2^(8 (5 - g)), then one conversion to FP64
-      long long acc[32];
+    for (int c = 0; c < CS_BJ / 16; ++c) {
+      long long acc[16];
+      int half[16];
 #pragma unroll
-      for (int jj = 0; jj < 32; ++jj) acc[jj] = 0;
+      for (int jj = 0; jj < 16; ++jj) acc[jj] = 0;
 #pragma unroll 1
       for (int g = 0; g < CS_S; ++g) {
-        float v[32];
-        cs_tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * CS_BJ + c * 32), v);
+        float v[16];
+        cs_tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * CS_BJ + c * 16), v);
+        if ((g & 1) == 0) {
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) acc[jj] = (acc[jj] << 8) + (long long)__float2int_rn(v[jj]);
-      }
-      // value = acc 2^(e_i + e_j - 14 - 8 (S - 1)), applied per element below
-      long long* stg_i = (long long*)stg;
+          for (int jj = 0; jj < 16; ++jj) half[jj] = __float2int_rn(v[jj]) * 256;
+        } else {
 #pragma unroll
-      for (int jj = 0; jj < 32; ++jj) stg_i[lane * 33 + jj] = acc[jj];
-      __syncwarp();
-      int64_t gj = (int64_t)row_j + c * 32 + lane;
-      int ej = (gj < nrows) ? rexp[gj] : 0;
-#pragma unroll 4
-      for (int rr = 0; rr < 32; ++rr) {
-        int lr = warp * 32 + rr;
-        int64_t gr = (int64_t)row_i + lr;
-        if (gr < nrows && gj < nrows && gj <= gr) {
-          int ex = rexp_sh[lr] + ej - 54;
-          // the FP64 pipe is scarce on this part: the rounded conversion of the
-          // integer and the power-of-two scaling are done with integer ops, so
-          // only the subtraction runs on it
-          double v = scaled_to_double(stg_i[rr * 33 + lane], ex);
-          double* p = W.at(r0 + gr, r0 + gj);
-          *p = ctile[lr * CS_BJ + c * 32 + lane] - v;
+          for (int jj = 0; jj < 16; ++jj) acc[jj] = acc[jj] * 65536 + (long long)(half[jj] + __float2int_rn(v[jj]));
         }
+      }
+#pragma unroll
+      for (int jj = 0; jj < 16; ++jj) stg[lane * 17 + jj] = acc[jj];
+      __syncwarp();
+      // value = acc 2^(e_i + e_j - 14 - 8 (S - 1)); this thread: column jc,
+      // rows 16 rh .. 16 rh + 15 of the warp's 32
+      const int64_t gj = (int64_t)row_j + c * 16 + jc, aj = r0 + gj;
+      const int ej = (gj < nrows) ? rexp[gj] : 0;
+      double* dst = nullptr;
+#pragma unroll 4
+      for (int k = 0; k < 16; ++k) {
+        const int rr = rh * 16 + k, lr = warp * 32 + rr;
+        const int64_t gr = (int64_t)row_i + lr, ar = r0 + gr;
+        if (gr < nrows && gj < nrows && gj <= gr) {
+          if (!dst || (W.tiled && (ar & 255) == 0)) dst = W.at(ar, aj);
+          // the FP64 pipe is scarce on this part: the rounded conversion and
+          // the power-of-two scaling are integer operations, so only the
+          // subtraction runs on it
+          const double v = scaled_to_double(stg[rr * 17 + jc], rexp_sh[lr] + ej - 54);
+          *dst = ctile[lr * CS_BJ + c * 16 + jc] - v;
+        }
+        if (dst) dst += stride;
       }
       __syncwarp();
     }
