@@ -136,6 +136,48 @@ __global__ void k_trsm_rows(OutMap W, int64_t k0, int kb, int64_t r0, int64_t r1
     if (j < kb) row[j] = x[j];
 }
 
+// The same solve with four lanes per row (eight rows per warp): lane q owns
+// the right-hand-side entries j = q (mod 4).  Column by column, the owner of
+// column l scales its entry into x_l, shuffles it to the other three lanes,
+// and each lane subtracts x_l L[j][l] from its entries j > l.  Four times the
+// warps of k_trsm_rows, so the FP64 latency of a row's 64-step chain is hidden
+// across more rows in flight.
+#define TR4_THREADS 128
+__global__ void __launch_bounds__(TR4_THREADS) k_trsm_rows4(OutMap W, int64_t k0, int kb, int64_t r0, int64_t r1) {
+  __shared__ double L[NB][NB + 1];
+  __shared__ double invd[NB];
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    int i = e >> 6, l = e & 63;
+    L[i][l] = (i < kb && l <= i) ? *W.at(k0 + i, k0 + l) : 0.0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kb; i += blockDim.x) invd[i] = 1.0 / L[i][i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, q = lane & 3, g4 = lane & ~3;
+  const int64_t r = r0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 4;
+  const bool valid = r < r1;
+  double* row = valid ? W.at(r, k0) : nullptr;
+  double a[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) a[m] = (valid && q + 4 * m < kb) ? row[q + 4 * m] : 0.0;
+#pragma unroll
+  for (int l = 0; l < NB; ++l) {
+    if (l >= kb) break;
+    if (q == (l & 3)) a[l >> 2] *= invd[l];
+    const double xl = __shfl_sync(0xffffffffu, a[l >> 2], g4 + (l & 3));
+#pragma unroll
+    for (int m = (l + 1) / 4; m < 16; ++m) {
+      const int j = q + 4 * m;
+      if (j > l) a[m] = fma(-xl, L[j][l], a[m]);
+    }
+  }
+  if (valid) {
+#pragma unroll
+    for (int m = 0; m < 16; ++m)
+      if (q + 4 * m < kb) row[q + 4 * m] = a[m];
+  }
+}
+
 __global__ void k_snr_prefix(int64_t Ms, OutMap W, const int64_t* cnt, int nl, double* out) {
   __shared__ double sh[32];
   int c = blockIdx.x;
@@ -198,7 +240,8 @@ static int factor_and_prefix(cov_handle* h, OutMap Wm, int64_t Ms, const int64_t
     k_potrf_diag<<<1, 256, 0, st_>>>(Wm, k0, kb, st);
     int64_t r0 = k0 + kb, r1 = Ms + 1;
     if (r1 > r0)
-      k_trsm_rows<<<(unsigned)((r1 - r0 + TRSM_ROWS - 1) / TRSM_ROWS), TRSM_ROWS, 0, st_>>>(Wm, k0, kb, r0, r1);
+      k_trsm_rows4<<<(unsigned)(((r1 - r0) * 4 + TR4_THREADS - 1) / TR4_THREADS), TR4_THREADS, 0, st_>>>(Wm, k0, kb,
+                                                                                                     r0, r1);
     WL_LAUNCH(h, "Cholesky panel kernels");
     return wl_chol_slice(h, Wm, k0, kb, r0, r1, bufs[(k0 / NB) & 1], st_);
   };

@@ -97,16 +97,24 @@ __device__ __forceinline__ uint64_t cs_desc_sw128(uint32_t saddr) {
   return d;
 }
 
-__device__ __forceinline__ void cs_tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
+// 32 lanes x 16 columns of TMEM into registers; the caller issues
+// tcgen05.wait::ld before using them
+__device__ __forceinline__ void cs_tmem_ld16_nowait(uint32_t taddr, uint32_t* r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// The integer held exactly by an FP32 value of magnitude below 2^24 (its
+// bits b), by integer operations: the conversion instruction goes through a
+// narrow unit on this part and dominated the epilogue.
+__device__ __forceinline__ int exact_f2i(uint32_t b) {
+  const int e = (int)((b >> 23) & 0xFFu);
+  const uint32_t m = (b & 0x7FFFFFu) | 0x800000u;
+  const int v = e < 127 ? 0 : (int)(m >> (150 - e));
+  return (b >> 31) ? -v : v;
 }
 
 // RN(a) 2^ex as an FP64 value, for |a| < 2^63, by integer operations: the
@@ -285,21 +293,24 @@ __global__ void __launch_bounds__(128, 1)
     const int64_t stride = W.tiled ? 256 : W.ldc;
 #pragma unroll 1
     for (int c = 0; c < CS_BJ / 16; ++c) {
+      // all six TMEM loads in flight before one wait: the load latency is paid
+      // once per chunk instead of once per group
+      uint32_t r[CS_S][16];
+#pragma unroll
+      for (int g = 0; g < CS_S; ++g)
+        cs_tmem_ld16_nowait(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * CS_BJ + c * 16), r[g]);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int g = 0; g < CS_S; ++g)
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) asm volatile("" : "+r"(r[g][jj]));  // uses stay after the wait
       long long acc[16];
-      int half[16];
 #pragma unroll
-      for (int jj = 0; jj < 16; ++jj) acc[jj] = 0;
-#pragma unroll 1
-      for (int g = 0; g < CS_S; ++g) {
-        float v[16];
-        cs_tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * CS_BJ + c * 16), v);
-        if ((g & 1) == 0) {
+      for (int jj = 0; jj < 16; ++jj) {
+        long long a = 0;
 #pragma unroll
-          for (int jj = 0; jj < 16; ++jj) half[jj] = __float2int_rn(v[jj]) * 256;
-        } else {
-#pragma unroll
-          for (int jj = 0; jj < 16; ++jj) acc[jj] = acc[jj] * 65536 + (long long)(half[jj] + __float2int_rn(v[jj]));
-        }
+        for (int k = 0; k < CS_S; k += 2) a = a * 65536 + (long long)(exact_f2i(r[k][jj]) * 256 + exact_f2i(r[k + 1][jj]));
+        acc[jj] = a;
       }
 #pragma unroll
       for (int jj = 0; jj < 16; ++jj) stg[lane * 17 + jj] = acc[jj];
