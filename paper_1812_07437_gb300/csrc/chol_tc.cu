@@ -247,25 +247,25 @@ __global__ void __launch_bounds__(128, 1)
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CS_BJ >> 3) << 17) |
                              ((uint32_t)(CS_BI >> 4) << 24);
       uint32_t base_i = cs_smem_u32(smem), base_j = cs_smem_u32(smem + CS_S * CS_IBYTES);
-      for (int g = 0; g < CS_S; ++g) {
-        uint32_t dt = tmem + (uint32_t)(g * CS_BJ);
-        int first = 1;
-        for (int t = 0; t <= g; ++t) {
-          int u = g - t;
+      // consecutive MMAs go to different accumulators (round r pairs slice
+      // t = r with u = g - r for g = r .. 5), so no MMA waits on the one
+      // before it; the first round of the first K step initialises all six
+#pragma unroll 1
+      for (int k = 0; k < CS_K / 16; ++k)
 #pragma unroll
-          for (int k = 0; k < CS_K / 16; ++k) {
-            uint64_t ad = cs_desc_sw128(base_i + t * CS_IBYTES + k * 32);
-            uint64_t bd = cs_desc_sw128(base_j + u * CS_JBYTES + k * 32);
-            uint32_t acc = first ? 0u : 1u;
+        for (int r = 0; r < CS_S; ++r)
+#pragma unroll
+          for (int g = r; g < CS_S; ++g) {
+            uint32_t dt = tmem + (uint32_t)(g * CS_BJ);
+            uint64_t ad = cs_desc_sw128(base_i + r * CS_IBYTES + k * 32);
+            uint64_t bd = cs_desc_sw128(base_j + (g - r) * CS_JBYTES + k * 32);
+            uint32_t acc = (k == 0 && r == 0) ? 0u : 1u;
             asm volatile(
                 "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, "
                 "p;\n}\n" ::"r"(dt),
                 "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
                 : "memory");
-            first = 0;
           }
-        }
-      }
     }
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      cs_smem_u32(&acc_bar))
@@ -316,23 +316,23 @@ __global__ void __launch_bounds__(128, 1)
       for (int jj = 0; jj < 16; ++jj) stg[lane * 17 + jj] = acc[jj];
       __syncwarp();
       // value = acc 2^(e_i + e_j - 14 - 8 (S - 1)); this thread: column jc,
-      // rows 16 rh .. 16 rh + 15 of the warp's 32
+      // rows 16 rh .. 16 rh + 15 of the warp's 32.  The 16 rows never cross a
+      // 256-row tile row, so one base address serves them all, and the 16
+      // values are independent (all in flight before the stores).
       const int64_t gj = (int64_t)row_j + c * 16 + jc, aj = r0 + gj;
       const int ej = (gj < nrows) ? rexp[gj] : 0;
-      double* dst = nullptr;
-#pragma unroll 4
-      for (int k = 0; k < 16; ++k) {
-        const int rr = rh * 16 + k, lr = warp * 32 + rr;
-        const int64_t gr = (int64_t)row_i + lr, ar = r0 + gr;
-        if (gr < nrows && gj < nrows && gj <= gr) {
-          if (!dst || (W.tiled && (ar & 255) == 0)) dst = W.at(ar, aj);
-          // the FP64 pipe is scarce on this part: the rounded conversion and
-          // the power-of-two scaling are integer operations, so only the
-          // subtraction runs on it
-          const double v = scaled_to_double(stg[rr * 17 + jc], rexp_sh[lr] + ej - 54);
-          *dst = ctile[lr * CS_BJ + c * 16 + jc] - v;
-        }
-        if (dst) dst += stride;
+      const int lr0 = warp * 32 + rh * 16;
+      const int64_t gr0 = (int64_t)row_i + lr0, ar0 = r0 + gr0;
+      if (gj < nrows && gr0 + 15 >= gj && (!W.tiled || (aj >> 8) <= (ar0 >> 8))) {
+        double* base = W.at(ar0, aj);
+        double nv[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+          nv[k] = ctile[(lr0 + k) * CS_BJ + c * 16 + jc] -
+                  scaled_to_double(stg[(rh * 16 + k) * 17 + jc], rexp_sh[lr0 + k] + ej - 54);
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+          if (gr0 + k < nrows && gj <= gr0 + k) base[k * stride] = nv[k];
       }
       __syncwarp();
     }

@@ -381,6 +381,56 @@ __device__ __forceinline__ uint32_t idesc_bf16_128x256() {
   return d;
 }
 
+// v 2^s as FP64 for the bits b of an FP32 value: FP32 to FP64 is exact and
+// the row scales are exact powers of two, so the product is an exponent sum,
+// done with integer operations (the FP64 pipe is narrow on this part).  Zero,
+// FP32 subnormals and results outside the FP64 normal range take the FP64
+// path; the value is the same either way.
+__device__ __forceinline__ double f32_scaled(uint32_t b, int s) {
+  const int e = (int)((b >> 23) & 0xFFu);
+  const int E = e - 127 + 1023 + s;
+  if (e == 0 || e == 255 || E <= 0 || E >= 2047) return ldexp((double)__uint_as_float(b), s);
+  return __longlong_as_double((long long)(((unsigned long long)(b >> 31) << 63) | ((unsigned long long)E << 52) |
+                                          ((unsigned long long)(b & 0x7FFFFFu) << 29)));
+}
+
+// exponent of an exact power of two (a row scale); rows past M have scale 0
+__device__ __forceinline__ int pow2_exp(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7FF) - 1023;
+}
+
+// Epilogue of one 256 x 256 tile: C = s_i s_j acc, plain stores (the
+// contraction is the first writer of the tile).  Each warp stages a 32 x 32
+// block of FP32 bits through the idle shared-memory ring (transpose) so that
+// every store instruction writes 32 consecutive doubles of one row.
+__device__ __forceinline__ void tile_epilogue(uint8_t* smem, uint32_t tmem, int warp, int lane, int row_i, int row_j,
+                                              int64_t M, const double* __restrict__ rscale, const OutMap& out) {
+  uint32_t* stg = (uint32_t*)smem + warp * (32 * 33 + 32);
+  int* erow = (int*)(stg + 32 * 33);
+#pragma unroll 1
+  for (int h = 0; h < 2; ++h) {
+    const int64_t r0 = (int64_t)row_i + 128 * h + warp * 32;
+    const int64_t gi = r0 + lane;
+    erow[lane] = (gi < M) ? pow2_exp(rscale[gi]) : 0;
+#pragma unroll 1
+    for (int c = 0; c < 8; ++c) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(256 * h + c * 32), v);
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) stg[lane * 33 + jj] = __float_as_uint(v[jj]);
+      __syncwarp();
+      const int64_t gj = (int64_t)row_j + c * 32 + lane;
+      const int ej = (gj < M) ? pow2_exp(rscale[gj]) : 0;
+#pragma unroll 4
+      for (int rr = 0; rr < 32; ++rr) {
+        const int64_t gr = r0 + rr;
+        if (gr < M && gj < M && gj <= gr) *out.at(gr, gj) = f32_scaled(stg[rr * 33 + lane], erow[rr] + ej);
+      }
+      __syncwarp();
+    }
+  }
+}
+
 __global__ void __launch_bounds__(128, 1)
     k_syrk_tc256(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, int64_t M,
                  int nk, const double* __restrict__ rscale, OutMap out, int* status, const int2* __restrict__ tiles) {
@@ -494,29 +544,7 @@ __global__ void __launch_bounds__(128, 1)
     // writer of the tile).  Each warp stages a 32 x 32 block through the idle
     // shared-memory ring (transpose) so that every store instruction writes 32
     // consecutive doubles of one row.
-    double* stg = (double*)smem + warp * (32 * 33);
-#pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-      int64_t r0 = (int64_t)row_i + 128 * h + warp * 32;
-      int64_t gi = r0 + lane;
-      double si = (gi < M) ? rscale[gi] : 0.0;
-#pragma unroll 1
-      for (int c = 0; c < 8; ++c) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(256 * h + c * 32), v);
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj) stg[lane * 33 + jj] = (double)v[jj] * si;
-        __syncwarp();
-        int64_t gj = (int64_t)row_j + c * 32 + lane;
-        double sj = (gj < M) ? rscale[gj] : 0.0;
-#pragma unroll 4
-        for (int rr = 0; rr < 32; ++rr) {
-          int64_t gr = r0 + rr;
-          if (gr < M && gj < M && gj <= gr) *out.at(gr, gj) = stg[rr * 33 + lane] * sj;
-        }
-        __syncwarp();
-      }
-    }
+    tile_epilogue(smem, tmem, warp, lane, row_i, row_j, M, rscale, out);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -684,29 +712,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128, 1)
   bool have = mbar_wait(&acc_bar, 0u, &abort_flag, status);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (have && !abort_flag && store) {
-    double* stg = (double*)smem + warp * (32 * 33);
-#pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-      int64_t r0 = (int64_t)row_i + 128 * h + warp * 32;
-      int64_t gi = r0 + lane;
-      double si = (gi < M) ? rscale[gi] : 0.0;
-#pragma unroll 1
-      for (int c = 0; c < 8; ++c) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(256 * h + c * 32), v);
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj) stg[lane * 33 + jj] = (double)v[jj] * si;
-        __syncwarp();
-        int64_t gj = (int64_t)row_j + c * 32 + lane;
-        double sj = (gj < M) ? rscale[gj] : 0.0;
-#pragma unroll 4
-        for (int r2 = 0; r2 < 32; ++r2) {
-          int64_t gr = r0 + r2;
-          if (gr < M && gj < M && gj <= gr) *out.at(gr, gj) = stg[r2 * 33 + lane] * sj;
-        }
-        __syncwarp();
-      }
-    }
+    tile_epilogue(smem, tmem, warp, lane, row_i, row_j, M, rscale, out);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
