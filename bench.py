@@ -51,6 +51,9 @@ def parse():
     p.add_argument("--snr-10bin", action="store_true",
                    help="also time the cumulative S/N of the workload itself, in place on its packed tiles "
                         "(one extra assembly and FP64-accurate Cholesky per row set; minutes at 10 bins)")
+    p.add_argument("--snr-rows", default="joint,B,P", help="row sets of --snr-10bin")
+    p.add_argument("--snr-precision", default="auto", choices=["auto", "fp64", "split_bf16"],
+                   help="covariance form of --snr-10bin (auto: the bench's own)")
     p.add_argument("--serve-requests", type=int, default=24)
     p.add_argument("--serve-rate", type=float, default=200.0)
     p.add_argument("--serve-budget-gb", type=float, default=64.0)
@@ -676,8 +679,12 @@ def run_ours(args):
     if not args.no_batch and packed and rank == 0 and world == 1:
         out["fisher_batch"] = batch_run(prec, local, [int(x) for x in args.batch_bins.split(",") if x])
     if args.snr_10bin and rank == 0 and world == 1:
-        out["snr_tiles"] = snr_tiles_run(workloads.get(args.workload), prec, local,
-                                         [("joint", N.COV_ROWS_JOINT), ("B", N.COV_ROWS_B), ("P", N.COV_ROWS_P)])
+        sets = {"joint": N.COV_ROWS_JOINT, "B": N.COV_ROWS_B, "P": N.COV_ROWS_P}
+        sp = prec if args.snr_precision == "auto" else (N.COV_FP64 if args.snr_precision == "fp64" else
+                                                         N.COV_SPLIT_BF16)
+        out["snr_tiles"] = snr_tiles_run(workloads.get(args.workload), sp, local,
+                                         [(r, sets[r]) for r in args.snr_rows.split(",") if r])
+        out["snr_tiles"]["precision"] = "fp64" if sp == N.COV_FP64 else "split_bf16"
     if not args.no_serve and packed and rank == 0 and world == 1:
         sv = serving_run(prec, args.serve_requests, args.serve_rate, args.serve_budget_gb, args.serve_slots, local)
         # the same mix offered at about half the rate the first run achieved
