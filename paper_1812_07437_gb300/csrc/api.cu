@@ -211,11 +211,15 @@ static void free_all(cov_handle* h) {
   if (h->batch_ev) cudaEventDestroy(h->batch_ev);
   h->pending.clear();
   h->pool.clear();
-  void* ptrs[] = {h->gl64x, h->gl64w, h->glkx, h->glkw, h->glcx, h->glcw, h->scal, h->chi, h->wchi, h->z, h->D,
-                  h->ell_d, h->m, h->om, h->sig0, h->dlns, h->f, h->b1, h->b2, h->U, h->Pl, h->dPl, h->Psh, h->zedges,
-                  h->norms, h->W, h->sigw2, h->slo_d, h->shi_d, h->Nmodes, h->Ntri, h->rowtab, h->tris_d,
-                  h->rowdesc_d, h->P3, h->RP3, h->B3, h->RB3, h->B1h3, h->Ps, h->B1hp, h->Bp, h->A, h->Ahi,
-                  h->Alo, h->Ascale, h->G2, h->G3, h->C2, h->C3, h->tc_status, h->Thi, h->Tlo, h->Tscale, h->Trows, h->Tmat, h->Srows, h->cosmo_d, h->Fsig, h->Esig, h->Msig, h->FsigT, h->EsigT, h->MsigT, h->invN, h->omN, h->work, h->perm, h->chol_scratch, h->chol_status};
+  void* ptrs[] = {h->gl64x, h->gl64w, h->glkx,    h->glkw,    h->glcx,   h->glcw,   h->scal,      h->chi,
+                  h->wchi,  h->z,     h->D,       h->ell_d,   h->m,      h->om,     h->sig0,      h->dlns,
+                  h->f,     h->b1,    h->b2,      h->U,       h->Pl,     h->dPl,    h->Psh,       h->zedges,
+                  h->norms, h->W,     h->sigw2,   h->slo_d,   h->shi_d,  h->Nmodes, h->Ntri,      h->rowtab,
+                  h->tris_d, h->rowdesc_d, h->P3, h->RP3,     h->B3,     h->RB3,    h->B1h3,      h->Ps,
+                  h->B1hp,  h->Bp,    h->A,       h->Ahi,     h->Alo,    h->Ascale, h->G2,        h->G3,
+                  h->C2,    h->C3,    h->tc_status, h->Thi,   h->Tlo,    h->Tscale, h->Trows,     h->Tmat,
+                  h->Srows, h->cosmo_d, h->Fsig,  h->Esig,    h->Msig,   h->FsigT,  h->EsigT,     h->MsigT,
+                  h->invN,  h->omN,   h->work,    h->chol_scratch, h->chol_status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->tile_ring) cudaFree(h->tile_ring);
@@ -386,7 +390,8 @@ extern "C" int cov_update(cov_handle* h, const cov_cosmology* cosmo, void* strea
   cudaStream_t s = (cudaStream_t)stream;
   // the kernels read the cosmology from device memory; a captured batch step
   // leaves this copy to its driver, which writes each cosmology before a replay
-  if (!h->deferred) WL_CHECK(h, cudaMemcpyAsync(h->cosmo_d, &h->cosmo, sizeof(cov_cosmology), cudaMemcpyHostToDevice, s));
+  if (!h->deferred)
+    WL_CHECK(h, cudaMemcpyAsync(h->cosmo_d, &h->cosmo, sizeof(cov_cosmology), cudaMemcpyHostToDevice, s));
   int tk = wl_stage_begin(h, ST_TABLES, s);
   int rc = wl_tables(h, s);
   wl_stage_end(h, tk, s);
@@ -540,7 +545,9 @@ extern "C" int cov_stage_times(cov_handle* h, double* ms, int64_t* calls, int n_
   return COV_OK;
 }
 
-extern "C" const char* cov_stage_name(int stage) { return (stage >= 0 && stage < ST_COUNT) ? kStageNames[stage] : nullptr; }
+extern "C" const char* cov_stage_name(int stage) {
+  return (stage >= 0 && stage < ST_COUNT) ? kStageNames[stage] : nullptr;
+}
 
 extern "C" const char* cov_last_error(const cov_handle* h) {
   return h ? h->err.c_str() : g_init_err.c_str();

@@ -7,9 +7,10 @@
 // M_s x M_s block carries the extra row along, so that row ends up holding
 // y = L^-1 D'.  Diagonal blocks and panel solves run in FP64 on the CUDA cores;
 // the trailing updates run on the tensor cores with exact integer slicing
-// (chol_tc.cu), accurate to ~2^-48 of each row's largest entry.  Because the leading principal block of a Cholesky factor is
-// the factor of the leading principal block, (S/N)^2 for every cumulative
-// ell_max is a prefix sum of y^2 over the reordered entries.
+// (chol_tc.cu), accurate to ~2^-48 of each row's largest entry.  Because the
+// leading principal block of a Cholesky factor is the factor of the leading
+// principal block, (S/N)^2 for every cumulative ell_max is a prefix sum of y^2
+// over the reordered entries.
 #include <algorithm>
 
 #include "common.cuh"

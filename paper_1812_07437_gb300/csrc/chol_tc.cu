@@ -309,7 +309,8 @@ __global__ void __launch_bounds__(128, 1)
       for (int jj = 0; jj < 16; ++jj) {
         long long a = 0;
 #pragma unroll
-        for (int k = 0; k < CS_S; k += 2) a = a * 65536 + (long long)(exact_f2i(r[k][jj]) * 256 + exact_f2i(r[k + 1][jj]));
+        for (int k = 0; k < CS_S; k += 2)
+          a = a * 65536 + (long long)(exact_f2i(r[k][jj]) * 256 + exact_f2i(r[k + 1][jj]));
         acc[jj] = a;
       }
 #pragma unroll

@@ -154,7 +154,6 @@ struct cov_handle {
   double* Srows = nullptr;  // [M][nchi]
   double* work = nullptr;   // Cholesky workspace (M+1)^2
   int64_t work_n = 0;
-  int* perm = nullptr;      // [M] reorder for the cumulative S/N
   void* chol_scratch = nullptr;  // two slice buffers of the tensor-core trailing update
   size_t chol_scratch_n = 0;
   cudaStream_t side = nullptr;   // look-ahead stream of the Cholesky panel kernels

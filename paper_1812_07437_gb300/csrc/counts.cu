@@ -147,7 +147,8 @@ int wl_counts(cov_handle* h, cudaStream_t s) {
   if (h->ntri > 0) {
     dim3 g2(rmax + 1, h->ntri);
     size_t shb = sizeof(int2) * 2 * (size_t)(rmax + 1);
-    if (shb > 48 * 1024) WL_CHECK(h, cudaFuncSetAttribute(k_ntri, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
+    if (shb > 48 * 1024)
+      WL_CHECK(h, cudaFuncSetAttribute(k_ntri, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
     k_ntri<<<g2, 128, shb, s>>>(rmax, h->tris_d, h->slo_d, h->shi_d, h->rowtab, (unsigned long long*)h->Ntri);
   }
   WL_LAUNCH(h, "count kernels");

@@ -12,7 +12,8 @@
 
 // One warp per (ell bin, node): I_2^0(k,k), I_1^1(k), I_2^1(k,k) -> P^HM and
 // its response; the k_max rule zeroes everything beyond k_max.
-__global__ void k_pspec(const cov_cosmology* __restrict__ cosmo_p, int nl, int nchi, int nm, double kmax, const double* ell, const double* chi,
+__global__ void k_pspec(const cov_cosmology* __restrict__ cosmo_p, int nl, int nchi, int nm, double kmax,
+                        const double* ell, const double* chi,
                         const double* m, const double* om, const double* f, const double* b1, const double* U,
                         const double* Pl, const double* dPl, double* P3, double* RP3) {
   const cov_cosmology c = *cosmo_p;
@@ -67,7 +68,8 @@ __device__ __forceinline__ double bpt_shift(const double* k, const double* P, in
 }
 
 // One warp per (triple, node): B^HM, its response and the 1-halo B.
-__global__ void k_bspec(const cov_cosmology* __restrict__ cosmo_p, int ntri, int nchi, int nm, double kmax, const int32_t* tris,
+__global__ void k_bspec(const cov_cosmology* __restrict__ cosmo_p, int ntri, int nchi, int nm, double kmax,
+                        const int32_t* tris,
                         const double* ell, const double* chi, const double* D, const double* m, const double* om,
                         const double* f, const double* b1, const double* b2, const double* U, const double* Pl,
                         const double* dPl, const double* Psh, const double* scal, double* B3, double* RB3,
@@ -208,7 +210,8 @@ __global__ void k_datavec(int64_t M, int nchi, const int32_t* rd, const double* 
 
 // 1-halo factor rows A[a][(n,q)] = sqrt(w_n omega_q f_nq / Omega) chi^(1-2mu)
 // prod W (m_q/rho)^mu prod U; grid (row blocks of K), coalesced along K.
-__global__ void k_rows_a(int64_t M, int nchi, int nm, double inv_omega, const cov_cosmology* __restrict__ cosmo_p, const int32_t* rd,
+__global__ void k_rows_a(int64_t M, int nchi, int nm, double inv_omega, const cov_cosmology* __restrict__ cosmo_p,
+                         const int32_t* rd,
                          const double* chi, const double* wchi, const double* W, const double* m, const double* om,
                          const double* f, const double* U, double* A) {
   const double rho = WL_RHO_CRIT0 * cosmo_p->Om;
@@ -231,7 +234,8 @@ __global__ void k_rows_a(int64_t M, int nchi, int nm, double inv_omega, const co
 }
 
 // trispectrum rows for leg pairs (L1 <= L2), L = bin * nt + tomo
-__global__ void k_rows_t(int nleg, int nt, int nchi, int nm, const cov_cosmology* __restrict__ cosmo_p, const double* chi, const double* wchi,
+__global__ void k_rows_t(int nleg, int nt, int nchi, int nm, const cov_cosmology* __restrict__ cosmo_p,
+                         const double* chi, const double* wchi,
                          const double* W, const double* m, const double* om, const double* f, const double* U,
                          double* Tr) {
   const double rho = WL_RHO_CRIT0 * cosmo_p->Om;
@@ -301,7 +305,8 @@ int wl_spectra(cov_handle* h, double* d_D, cudaStream_t s) {
 
 int wl_rows_a(cov_handle* h, cudaStream_t s) {
   dim3 g((unsigned)h->M, (h->K + 255) / 256);
-  k_rows_a<<<g, 256, 0, s>>>(h->M, h->nchi, h->nm, 1.0 / h->omega, h->cosmo_d, h->rowdesc_d, h->chi, h->wchi, h->W, h->m,
+  k_rows_a<<<g, 256, 0, s>>>(h->M, h->nchi, h->nm, 1.0 / h->omega, h->cosmo_d, h->rowdesc_d, h->chi, h->wchi, h->W,
+                             h->m,
                              h->om, h->f, h->U, h->A);
   WL_LAUNCH(h, "k_rows_a");
   return COV_OK;

@@ -40,7 +40,8 @@ __device__ __forceinline__ int64_t blk_off(int64_t r, int k, int nk) {
 // Per-(n, q) and per-n factors of the 1-halo rows, so that the row builder
 // needs only products: g_mu[n][q] = sqrt(w_n omega_q f_nq / Omega) (m_q/rho)^mu
 // and c_mu[n] = chi_n^(1 - 2 mu), for mu = 2 (P rows) and 3 (B rows).
-__global__ void k_rows_prep(int nchi, int nm, double inv_omega, const cov_cosmology* __restrict__ cosmo_p, const double* chi, const double* wchi,
+__global__ void k_rows_prep(int nchi, int nm, double inv_omega, const cov_cosmology* __restrict__ cosmo_p,
+                            const double* chi, const double* wchi,
                             const double* m, const double* om, const double* f, double* g2, double* g3, double* c2,
                             double* c3) {
   const double rho = WL_RHO_CRIT0 * cosmo_p->Om;
@@ -781,8 +782,8 @@ int wl_rows_split(cov_handle* h, int nssc, cudaStream_t s) {
     return rc;
   if ((rc = zero_last_tile(h, h->Ahi, h->M, Kt, s))) return rc;
   if ((rc = zero_last_tile(h, h->Alo, h->M, Kt, s))) return rc;
-  k_rows_prep<<<(h->K + 255) / 256, 256, 0, s>>>(h->nchi, h->nm, 1.0 / h->omega, h->cosmo_d, h->chi, h->wchi, h->m, h->om,
-                                                   h->f, h->G2, h->G3, h->C2, h->C3);
+  k_rows_prep<<<(h->K + 255) / 256, 256, 0, s>>>(h->nchi, h->nm, 1.0 / h->omega, h->cosmo_d, h->chi, h->wchi,
+                                                 h->m, h->om, h->f, h->G2, h->G3, h->C2, h->C3);
   WL_LAUNCH(h, "k_rows_prep");
   k_rows_sig<<<dim3((unsigned)nsig, (unsigned)h->nchi), 128, 0, s>>>(h->nl, h->ntri, h->nchi, h->nm, h->tris_d, h->U,
                                                                      h->G2, h->G3, h->C2, h->C3, h->Fsig, h->Esig,
@@ -821,8 +822,8 @@ int wl_trows_split(cov_handle* h, cudaStream_t s) {
   if ((rc = wl_ensure(h, (void**)&h->C3, sizeof(double) * h->nchi, "row factor table"))) return rc;
   if ((rc = zero_last_tile(h, h->Thi, h->ntrow, h->K, s))) return rc;
   if ((rc = zero_last_tile(h, h->Tlo, h->ntrow, h->K, s))) return rc;
-  k_rows_prep<<<(h->K + 255) / 256, 256, 0, s>>>(h->nchi, h->nm, 1.0 / h->omega, h->cosmo_d, h->chi, h->wchi, h->m, h->om,
-                                                   h->f, h->G2, h->G3, h->C2, h->C3);
+  k_rows_prep<<<(h->K + 255) / 256, 256, 0, s>>>(h->nchi, h->nm, 1.0 / h->omega, h->cosmo_d, h->chi, h->wchi,
+                                                 h->m, h->om, h->f, h->G2, h->G3, h->C2, h->C3);
   WL_LAUNCH(h, "k_rows_prep");
   k_rows_sig<<<dim3((unsigned)npair, (unsigned)h->nchi), 128, 0, s>>>(h->nl, h->ntri, h->nchi, h->nm, h->tris_d, h->U,
                                                                       h->G2, h->G3, h->C2, h->C3, h->FsigT, h->EsigT,

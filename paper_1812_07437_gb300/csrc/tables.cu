@@ -37,7 +37,8 @@ __global__ void k_gauss_legendre(int n, double* x, double* w) {
   w[i] = 2.0 / ((1.0 - zz * zz) * pp * pp);
 }
 
-__global__ void k_chimax(const cov_cosmology* __restrict__ cosmo_p, double zmax, const double* glx, const double* glw, double* scal);
+__global__ void k_chimax(const cov_cosmology* __restrict__ cosmo_p, double zmax, const double* glx,
+                         const double* glw, double* scal);
 
 // RK4 integration of the linear growth ODE in ln a from a = 1e-3 to a_t
 __device__ double dev_growth_raw(double at, const cov_cosmology& c) {
@@ -74,7 +75,8 @@ __device__ double dev_growth_raw(double at, const cov_cosmology& c) {
 }
 
 // chi(z_max)
-__global__ void k_chimax(const cov_cosmology* __restrict__ cosmo_p, double zmax, const double* glx, const double* glw, double* scal) {
+__global__ void k_chimax(const cov_cosmology* __restrict__ cosmo_p, double zmax, const double* glx,
+                         const double* glw, double* scal) {
   const cov_cosmology c = *cosmo_p;
   if (threadIdx.x == 0 && blockIdx.x == 0) scal[SC_CHIMAX] = dev_chi_of_z(zmax, c, glx, glw);
 }
@@ -87,7 +89,8 @@ __global__ void k_growth_norm(int nchi, const double* scal, double* D) {
 
 // line-of-sight nodes: chi_n (GL on [0, chi_max]), weights, z(chi_n), D(z_n);
 // one node per block so that the sequential RK4 runs spread over the SMs
-__global__ void k_los(const cov_cosmology* __restrict__ cosmo_p, int nchi, const double* glcx, const double* glcw, const double* gl64x,
+__global__ void k_los(const cov_cosmology* __restrict__ cosmo_p, int nchi, const double* glcx, const double* glcw,
+                      const double* gl64x,
                       const double* gl64w, const double* scal, double* chi, double* wchi, double* z, double* D) {
   const cov_cosmology c = *cosmo_p;
   int n = blockIdx.x;
@@ -113,7 +116,8 @@ __global__ void k_los(const cov_cosmology* __restrict__ cosmo_p, int nchi, const
 }
 
 // sigma_8 normalisation: amplitude A of P_lin(k,0) = A k^ns T^2
-__global__ void k_amplitude(const cov_cosmology* __restrict__ cosmo_p, const double* glkx, const double* glkw, double* scal) {
+__global__ void k_amplitude(const cov_cosmology* __restrict__ cosmo_p, const double* glkx, const double* glkw,
+                            double* scal) {
   const cov_cosmology c = *cosmo_p;
   __shared__ double sh[32];
   double half = 0.5 * (WL_LNK_MAX - WL_LNK_MIN), s = 0.0;
@@ -127,7 +131,8 @@ __global__ void k_amplitude(const cov_cosmology* __restrict__ cosmo_p, const dou
 }
 
 // mass nodes, sigma(m, 0) and d ln sigma / d ln m (one block per mass node)
-__global__ void k_sigma(const cov_cosmology* __restrict__ cosmo_p, cov_bins b, const double* glkx, const double* glkw, const double* scal,
+__global__ void k_sigma(const cov_cosmology* __restrict__ cosmo_p, cov_bins b, const double* glkx,
+                        const double* glkw, const double* scal,
                         double* m, double* om, double* sig0, double* dlns) {
   const cov_cosmology c = *cosmo_p;
   __shared__ double sh[32];
@@ -163,7 +168,8 @@ __device__ __forceinline__ double st_amp() {
 }
 
 // Sheth-Tormen f_m, PBS biases and the m_min regularisation; one block per node
-__global__ void k_halo(const cov_cosmology* __restrict__ cosmo_p, int nm, const double* D, const double* m, const double* om,
+__global__ void k_halo(const cov_cosmology* __restrict__ cosmo_p, int nm, const double* D, const double* m,
+                       const double* om,
                        const double* sig0, const double* dlns, double* f, double* b1, double* b2) {
   const cov_cosmology c = *cosmo_p;
   __shared__ double sh[32];
@@ -208,7 +214,8 @@ __global__ void k_halo(const cov_cosmology* __restrict__ cosmo_p, int nm, const 
 }
 
 // NFW profiles on the Limber grid and P_lin, dP_lin/dln k at k = l_b/chi_n
-__global__ void k_profiles(const cov_cosmology* __restrict__ cosmo_p, cov_bins b, const double* ell, const double* chi, const double* z,
+__global__ void k_profiles(const cov_cosmology* __restrict__ cosmo_p, cov_bins b, const double* ell,
+                           const double* chi, const double* z,
                            const double* D, const double* m, const double* scal, double* U, double* Pl,
                            double* dPl, double* Psh) {
   const cov_cosmology c = *cosmo_p;
@@ -308,7 +315,8 @@ __global__ void k_norms(cov_nz nz, const double* e, const double* gx, const doub
 }
 
 // W_i(chi_n): one block per node, threads over the source-redshift nodes
-__global__ void k_kernels(const cov_cosmology* __restrict__ cosmo_p, cov_nz nz, int nchi, const double* chi, const double* z,
+__global__ void k_kernels(const cov_cosmology* __restrict__ cosmo_p, cov_nz nz, int nchi, const double* chi,
+                          const double* z,
                           const double* e, const double* norms, const double* gx, const double* gw, double* W) {
   const cov_cosmology c = *cosmo_p;
   __shared__ double sh[32];
@@ -337,7 +345,8 @@ __global__ void k_kernels(const cov_cosmology* __restrict__ cosmo_p, cov_nz nz, 
 }
 
 // sigma_W^2(chi_n) of a disk of angular radius Theta (Appendix B)
-__global__ void k_sigw2(const cov_cosmology* __restrict__ cosmo_p, double theta, const double* chi, const double* D, const double* glkx,
+__global__ void k_sigw2(const cov_cosmology* __restrict__ cosmo_p, double theta, const double* chi, const double* D,
+                        const double* glkx,
                         const double* glkw, const double* scal, double* out) {
   const cov_cosmology c = *cosmo_p;
   __shared__ double sh[32];
