@@ -25,9 +25,9 @@ Element-by-element forms, each the paper's expression written out:
              Appendix B).
 
 Block forms used for whole matrices: the 1-halo term as F diag(g) F^T with
-F[a,(n,q)] = chi^(1-2 mu_a) prod W (m/rho)^mu_a prod U and
-g = w_n omega_q f~/Omega (the same double sum, grouped per row), and the SSC
-term as S S^T.
+F[a,(n,q,j)] = chi^(1-2 mu_a) prod W (m/rho)^mu_a prod U(c_j) and
+g = w_n omega_q f~ w_j/Omega (the same sum over line-of-sight, mass and
+concentration nodes, grouped per row), and the SSC term as S S^T.
 """
 import itertools
 import math
@@ -65,10 +65,10 @@ class Covariance:
             T = self.T
             mu = len(key)
             g = T.om[None, :] * T.f * T.mr[None, :] ** mu
-            arr = g.copy()
+            arr = g[:, :, None] * T.wc[None, None, :]
             for b in key:
                 arr = arr * T.U[b]
-            vals = arr.sum(axis=1)
+            vals = arr.sum(axis=(1, 2))
             ok = np.all(T.valid[list(key)], axis=0)
             self._icache[key] = np.where(ok, vals, 0.0)
         return self._icache[key]
@@ -192,21 +192,23 @@ class Covariance:
         return C
 
     def factor_rows(self):
-        """F[a, (n, q)] of the 1-halo block form and the weights g[(n, q)]."""
+        """F[a, (n, q, j)] of the 1-halo block form and the weights g[(n, q, j)]
+        (j: concentration node; one node without scatter)."""
         T = self.T
         nchi, nm = T.f.shape
-        F = np.zeros((len(self.rows), nchi * nm))
+        nc = len(T.wc)
+        F = np.zeros((len(self.rows), nchi * nm * nc))
         for a, r in enumerate(self.rows):
             legs, tom = row_legs(r), row_tomos(r)
             mu = len(legs)
-            v = (T.chi ** (1 - 2 * mu))[:, None] * T.mr[None, :] ** mu
+            v = (T.chi ** (1 - 2 * mu))[:, None, None] * (T.mr ** mu)[None, :, None]
             for t in tom:
-                v = v * T.W[t][:, None]
+                v = v * T.W[t][:, None, None]
             for b in legs:
                 v = v * T.U[b]
             ok = np.all(T.valid[legs], axis=0)
-            F[a] = (v * ok[:, None]).ravel()
-        g = (T.wchi[:, None] * T.om[None, :] * T.f / T.omega).ravel()
+            F[a] = (v * ok[:, None, None]).ravel()
+        g = (T.wchi[:, None, None] * T.om[None, :, None] * T.f[:, :, None] * T.wc[None, None, :] / T.omega).ravel()
         return F, g
 
     def one_halo_block(self):

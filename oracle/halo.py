@@ -12,7 +12,13 @@
   that the discrete consistency relations (Eq. BoundinMass) hold exactly.
 * Concentration: Duffy et al. (2008) mean-density fit c = 10.14
   (m / 2e12)^-0.081 (1+z)^-1.01 with r_200m = (3m/(4 pi 200 rho_com))^(1/3).
-* NFW Fourier profile u(k, m) in sine/cosine integrals, u(0) = 1.
+* NFW Fourier profile u(k, m, c) in sine/cosine integrals, u(0) = 1.
+* Concentration scatter (Eq. LogNormC, the paper's "model A"): ln c is
+  normal about ln c_bar(m, z) with sigma_lnc (0.18 in the paper).  The c
+  integral of Eq. ImunuHalos is taken with an N_c-point Gauss-Hermite rule
+  in x = (ln c - ln c_bar)/sigma_lnc: nodes c_j = c_bar exp(sigma_lnc x_j),
+  weights w_j of the standard normal density (sum w_j = 1).  N_c <= 1 is the
+  delta-function p(c) of "model B" (c = c_bar, weight 1).
 
 Mass rule: N_M nodes m_q log-spaced over [m_min, m_max] (both included),
 trapezoid weights in ln m: omega_q = dlnm * m_q * (1/2 at both ends), so that
@@ -21,6 +27,7 @@ int dm g(m) ~ sum_q omega_q g(m_q).
 import math
 
 import numpy as np
+from numpy.polynomial.hermite_e import hermegauss
 from scipy.special import sici
 
 ST_Q = 0.707
@@ -108,18 +115,31 @@ def concentration(m, z):
     return DUFFY_A * (np.asarray(m) / DUFFY_MPIVOT) ** DUFFY_B * (1.0 + z) ** DUFFY_C
 
 
+def conc_rule(n_conc, sigma_lnc):
+    """Offsets s_j = sigma_lnc x_j of ln c from ln c_bar and weights w_j of
+    the concentration integral: x_j, w_j Gauss-Hermite for the standard
+    normal density (numpy's hermegauss weights / sqrt(2 pi)); n_conc <= 1
+    gives the single offset 0 with weight 1 (model B)."""
+    if n_conc <= 1:
+        return np.zeros(1), np.ones(1)
+    x, w = hermegauss(n_conc)
+    return x * sigma_lnc, w / math.sqrt(2.0 * math.pi)
+
+
 def r_vir(m, rho):
     return (3.0 * np.asarray(m) / (4.0 * math.pi * DELTA_VIR * rho)) ** (1.0 / 3.0)
 
 
-def nfw_u(k, m, z, rho):
-    """Normalised Fourier transform u(k|m) of a truncated NFW profile.
+def nfw_u(k, m, z, rho, c=None):
+    """Normalised Fourier transform u(k|m, c) of a truncated NFW profile
+    (c defaults to the median concentration c_bar(m, z)).
 
     u = [sin x (Si((1+c)x) - Si(x)) - sin(cx)/((1+c)x)
          + cos x (Ci((1+c)x) - Ci(x))] / (ln(1+c) - c/(1+c)),  x = k r_s.
     scipy.special.sici is the Si/Ci step.
     """
-    c = concentration(m, z)
+    if c is None:
+        c = concentration(m, z)
     rs = r_vir(m, rho) / c
     x = np.asarray(k, dtype=np.float64) * rs
     si1, ci1 = sici(x)

@@ -2,9 +2,13 @@
 
 Paper sections followed:
   * Eq. nProjection: P^(n)_{i1..in} = int dchi chi^(2-2n) prod_i W_i P3D(l/chi).
-  * Eq. ImunuHalos: I_mu^beta(k1..k_mu) = int dm b_beta (m/rho)^mu f_m prod u.
-    Concentration scatter is not used (delta-function p(c), the paper's
-    "model B"), so the inner c integral is a single evaluation.
+  * Eq. ImunuHalos: I_mu^beta(k1..k_mu) = int dm b_beta (m/rho)^mu f_m
+    int dc p(c, m) prod u(k_i, m, c).  With bins["n_conc"] >= 2 the inner
+    integral is the lognormal of Eq. LogNormC ("model A", sigma_lnc =
+    bins["sigma_lnc"]) on the Gauss-Hermite rule of halo.conc_rule; else p(c)
+    is a delta function at the median ("model B") and the inner integral is a
+    single evaluation.  The m_min regularisation is set on the mass rule
+    alone: its halos at m_min carry the same concentration scatter.
   * Eq. PspHMtot2: P^HM = I_2^0 + (I_1^1)^2 P_lin.
   * Eqs. B1halo, B2halos, B3halos, BspHMtot: B^HM = B^1h + B^2h + B^3h with the
     tree-level B^PT, F2 kernel, b2 term and the tidal term
@@ -69,13 +73,19 @@ class Tables:
         nl = bins["n_ell"]
         self.k = self.ell[:, None] / self.chi[None, :]
         self.valid = self.k <= bins["k_max"]
-        self.U = np.zeros((nl, nchi, nm))
+        # concentration rule: U[b, n, q, j] = u(l_b/chi_n, m_q, c_bar exp(s_j))
+        self.cs, self.wc = halo.conc_rule(int(bins.get("n_conc", 0)), float(bins.get("sigma_lnc", 0.0)))
+        nc = len(self.wc)
+        self.U = np.zeros((nl, nchi, nm, nc))
         self.Pl = np.zeros((nl, nchi))
         self.dPl = np.zeros((nl, nchi))
         for b in range(nl):
             for n in range(nchi):
                 if self.valid[b, n]:
-                    self.U[b, n] = halo.nfw_u(self.k[b, n], self.m, self.z[n], self.rho)
+                    cbar = halo.concentration(self.m, self.z[n])
+                    for j in range(nc):
+                        self.U[b, n, :, j] = halo.nfw_u(self.k[b, n], self.m, self.z[n], self.rho,
+                                                        cbar * math.exp(self.cs[j]))
                     self.Pl[b, n] = cz.plin(self.k[b, n], self.D[n], self.amp, cosmo)
                     self.dPl[b, n] = cz.dplin_dlnk(self.k[b, n], self.D[n], self.amp, cosmo, FD_H)
         # survey kernels and noise
@@ -86,11 +96,13 @@ class Tables:
 
     # -- halo integrals -------------------------------------------------
     def I(self, legs, mu, beta, n):
-        """I_mu^beta at node n for the ell bins in ``legs`` (Eq. ImunuHalos)."""
+        """I_mu^beta at node n for the ell bins in ``legs`` (Eq. ImunuHalos):
+        the sum over mass nodes q and concentration nodes j."""
         bb = (None, self.b1[n], self.b2[n])[beta]
         arr = self.om * self.f[n] * self.mr ** mu
         if bb is not None:
             arr = arr * bb
+        arr = arr[:, None] * self.wc[None, :]
         for b in legs:
             arr = arr * self.U[b, n]
         return float(np.sum(arr))

@@ -31,6 +31,8 @@ TERM_SSC = 16
 TERMS_ALL = 31
 
 FIDUCIAL = dict(Om=0.31, Ob=0.049, h=0.68, ns=0.96, sigma8=0.83, w0=-1.0, Tcmb=2.7255)
+# width of the lognormal concentration scatter of "model A" (Sec. 4.2.1)
+SIGMA_LNC = 0.18
 
 
 def _nz(n_tomo, photoz):
