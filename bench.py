@@ -62,6 +62,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64-form", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--model-a", action="store_true",
+                   help="also run the concentration-scatter comparison (model A against model B)")
+    p.add_argument("--model-a-workload", default="cfg3_5bin")
+    p.add_argument("--model-a-nodes", type=int, default=8, help="concentration nodes of model A")
     return p.parse_args()
 
 
@@ -424,6 +428,59 @@ def batch_run(prec, device, bins_list):
     return out
 
 
+def model_a_run(prec, device, name, n_conc):
+    """Concentration scatter (model A, Eq. LogNormC, sigma_lnc = 0.18) against
+    the median concentration (model B) on one workload: the whole dense step of
+    each (tables, spectra, every covariance term, the three cumulative S/N),
+    the contraction's roofline at n_conc times the halo-integral nodes, and the
+    relative changes between the two models that Sec. 6 of the paper reports
+    (data vector, covariance, S/N)."""
+    import numpy as np
+    import torch
+    from paper_1812_07437_gb300 import native as N
+    from paper_1812_07437_gb300 import workloads
+    from paper_1812_07437_gb300.handle import Handle
+    dev = torch.device("cuda", device)
+    res = {}
+    for label, nc in (("model_B", 0), ("model_A", n_conc)):
+        wl = workloads.get(name, bins=dict(n_conc=nc, sigma_lnc=workloads.SIGMA_LNC))
+        h = Handle(wl, device=device)
+        s = torch.cuda.Stream(device=dev)
+        with torch.cuda.stream(s):
+            r = dense_run(h, wl, dict(wl["cosmology"]), prec, s, 2, 1, 1, False)
+        M = h.M
+        elements = M * (M + 1) // 2
+        K = wl["bins"]["n_chi"] * wl["bins"]["n_mass"] * max(1, nc)
+        Kc = K + (wl["bins"]["n_chi"] if prec != N.COV_FP64 else 0)
+        roof = contraction_roofline(r["stages"], elements, Kc, prec, N, long_kernel=True)
+        res[label] = dict(r=r, nP=h.n_P, M=M, K=K, out={
+            "K": K, "ms_per_full_step": r["ms_per_step"],
+            # step time less the S/N stages (sequential on the stream); the assembly's own
+            # stages overlap (the gather runs beside the contraction) and are not summed
+            "assembly_elements_per_s": elements / ((r["ms_per_step"] - sum(
+                v[0] for k, v in r["stages"].items() if k.startswith("snr")) / 2) / 1e3),
+            "stages_ms_per_step": {k: v[0] / 2 for k, v in r["stages"].items() if v[1]},
+            "contraction": {k: roof[k] for k in ("achieved", "peak", "unit", "frac", "launch_ms", "peak_source")
+                            if k in roof},
+            "snr_joint_max": float(np.nanmax(r["snr"][2]))})
+        h.close()
+    a, b = res["model_A"], res["model_B"]
+    nP = a["nP"]
+    dD = (a["r"]["D"] / b["r"]["D"] - 1.0).abs()
+    var = (torch.diagonal(a["r"]["C"]) / torch.diagonal(b["r"]["C"]) - 1.0).abs()
+    snr_rel = [float(np.nanmax(np.abs(np.asarray(x) / np.asarray(y) - 1.0)))
+               for x, y in zip(a["r"]["snr"], b["r"]["snr"])]
+    out = {"workload": name, "M": a["M"], "n_conc": n_conc, "sigma_lnc": workloads.SIGMA_LNC,
+           "precision": "fp64" if prec == N.COV_FP64 else "split_bf16",
+           "model_A": a["out"], "model_B": b["out"],
+           "A_vs_B": {"D_P_max_rel": float(dD[:nP].max()), "D_B_max_rel": float(dD[nP:].max()),
+                      "var_P_max_rel": float(var[:nP].max()), "var_B_max_rel": float(var[nP:].max()),
+                      "snr_max_rel_P_B_joint": snr_rel}}
+    del res
+    torch.cuda.empty_cache()
+    return out
+
+
 def snr_tiles_run(wl, prec, device, row_sets):
     """Cumulative S/N of the workload's own data vector without a dense square:
     a handle in cumulative row order assembles its lower-packed tiles (plus one
@@ -499,7 +556,7 @@ def run_ours(args):
     h = Handle(wl, device=local)
     M = h.M
     elements = M * (M + 1) // 2
-    K = wl["bins"]["n_chi"] * wl["bins"]["n_mass"]
+    K = wl["bins"]["n_chi"] * wl["bins"]["n_mass"] * max(1, wl["bins"].get("n_conc", 0))
     Kc = K + (wl["bins"]["n_chi"] if prec != N.COV_FP64 else 0)  # SSC rows ride in the split contraction
     stream = torch.cuda.Stream(device=dev)
     packed = args.layout == "tiles" or (args.layout == "auto" and M * M * 8 > 64e9)
@@ -694,6 +751,8 @@ def run_ours(args):
         out["snr_tiles"] = snr_tiles_run(workloads.get(args.workload), sp, local,
                                          [(r, sets[r]) for r in args.snr_rows.split(",") if r])
         out["snr_tiles"]["precision"] = "fp64" if sp == N.COV_FP64 else "split_bf16"
+    if args.model_a and rank == 0 and world == 1:
+        out["model_a"] = model_a_run(prec, local, args.model_a_workload, args.model_a_nodes)
     if not args.no_serve and packed and rank == 0 and world == 1:
         sv = serving_run(prec, args.serve_requests, args.serve_rate, args.serve_budget_gb, args.serve_slots, local)
         # the same mix offered at about half the rate the first run achieved

@@ -71,12 +71,23 @@ typedef struct {
 
 /* n_ell log-spaced ell bins on [ell_min, ell_max] (Sec. 3.2.1, App. A), sky
  * fraction f_sky, n_chi Gauss-Legendre line-of-sight nodes, n_mass log mass
- * nodes on [m_min, m_max] Msun/h, 3D cut k_max h/Mpc (Sec. 4.4). */
+ * nodes on [m_min, m_max] Msun/h, 3D cut k_max h/Mpc (Sec. 4.4).
+ *
+ * Concentration scatter (Eq. LogNormC; the paper's "model A" of Sec. 6):
+ * with n_conc >= 2 every halo integral of Eq. ImunuHalos also averages the
+ * NFW profiles over a lognormal concentration of width sigma_lnc (0.18 in the
+ * paper) about the median c(m, z), on an n_conc-point Gauss-Hermite rule in
+ * ln c.  n_conc = 0 or 1 is the delta-function p(c) ("model B", the
+ * default).  The 1-halo contraction then runs over n_chi * n_mass * n_conc
+ * nodes: its work and its operand memory grow by n_conc.  n_conc <= 32,
+ * 0 <= sigma_lnc <= 2, n_mass * max(n_conc, 1) <= 4096. */
 typedef struct {
   int n_ell;
   double ell_min, ell_max, f_sky;
   int n_chi, n_mass;
   double m_min, m_max, k_max;
+  int n_conc;
+  double sigma_lnc;
 } cov_bins;
 
 /* Row set and row order of the data vector (Sec. 5). */
@@ -185,9 +196,11 @@ int cov_snr(cov_handle* h, const double* d_C, int64_t ldc, const double* d_D, in
             double* h_snr, void* stream);
 
 /* Copy an internal FP64 table to host memory for inspection (tests).  name is
- * one of "chi", "wchi", "z", "growth", "mass", "f", "b1", "b2", "U", "Plin",
- * "dPlin", "W", "sigw2", "P3", "RP3", "B3", "RB3", "B1h3", "Ps", "B1h";
- * *count receives the number of doubles (pass host = NULL to query). */
+ * one of "chi", "wchi", "z", "growth", "mass", "conc_offsets", "conc_weights",
+ * "f", "b1", "b2", "U", "Plin", "dPlin", "W", "sigw2", "P3", "RP3", "B3",
+ * "RB3", "B1h3", "Ps", "B1h"; *count receives the number of doubles (pass
+ * host = NULL to query).  "mass", "f", "b1", "b2" and "U" run over the
+ * (mass, concentration) nodes, the concentration index fastest. */
 int cov_table(cov_handle* h, const char* name, double* host, int64_t* count, void* stream);
 
 /* Stage timing with CUDA events recorded on the caller's stream around each

@@ -94,8 +94,10 @@ static int plan(cov_handle* h) {
   h->nl = b.n_ell;
   h->nt = nz.n_tomo;
   h->nchi = b.n_chi;
-  h->nm = b.n_mass;
-  h->K = b.n_chi * b.n_mass;
+  h->nmb = b.n_mass;
+  h->nc = b.n_conc > 1 ? b.n_conc : 1;  // concentration nodes (Eq. LogNormC); 1 without scatter
+  h->nm = b.n_mass * h->nc;
+  h->K = b.n_chi * h->nm;
   // ell bins: log-spaced edges, centre = (lo + hi)/2, width = hi - lo
   double r = b.ell_max / b.ell_min;
   h->ell_edges.resize(h->nl + 1);
@@ -192,6 +194,9 @@ static int validate(const cov_cosmology* c, const cov_nz* nz, const cov_bins* b)
   if (!(b->f_sky > 0 && b->f_sky < 1)) return COV_ERR_INVALID;
   if (b->n_chi < 2 || b->n_chi > 4096 || b->n_mass < 2 || b->n_mass > 4096) return COV_ERR_INVALID;
   if (!(b->m_min > 0) || !(b->m_max > b->m_min) || !(b->k_max > 0)) return COV_ERR_INVALID;
+  if (b->n_conc < 0 || b->n_conc > 32 || !(b->sigma_lnc >= 0 && b->sigma_lnc <= 2) ||
+      b->n_mass * std::max(b->n_conc, 1) > 4096)
+    return COV_ERR_INVALID;
   if (!(c->Om > 0 && c->Om <= 1) || !(c->Ob > 0 && c->Ob < c->Om) || !(c->h > 0) || !(c->sigma8 > 0) ||
       !(c->Tcmb > 0))
     return COV_ERR_INVALID;
@@ -219,7 +224,8 @@ static void free_all(cov_handle* h) {
                   h->B1hp,  h->Bp,    h->A,       h->Ahi,     h->Alo,    h->Ascale, h->G2,        h->G3,
                   h->C2,    h->C3,    h->tc_status, h->Thi,   h->Tlo,    h->Tscale, h->Trows,     h->Tmat,
                   h->Srows, h->cosmo_d, h->Fsig,  h->Esig,    h->Msig,   h->FsigT,  h->EsigT,     h->MsigT,
-                  h->invN,  h->omN,   h->work,    h->chol_scratch, h->chol_status};
+                  h->invN,  h->omN,   h->work,    h->chol_scratch, h->chol_status, h->mb, h->omb, h->cs,
+                  h->cw};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->tile_ring) cudaFree(h->tile_ring);
@@ -236,7 +242,8 @@ static void free_all(cov_handle* h) {
 // Device tables that cov_init allocates for a planned handle (pointer, bytes).
 static void init_allocs(cov_handle* h, std::vector<std::pair<void**, size_t>>& al) {
   const size_t d = sizeof(double);
-  size_t nl = h->nl, nt = h->nt, nchi = h->nchi, nm = h->nm, ntri = std::max(h->ntri, 1);
+  size_t nl = h->nl, nt = h->nt, nchi = h->nchi, nm = h->nm, nmb = h->nmb, nc = h->nc;
+  size_t ntri = std::max(h->ntri, 1);
   al = {
       {(void**)&h->gl64x, d * WL_N_GL_CHI}, {(void**)&h->gl64w, d * WL_N_GL_CHI},
       {(void**)&h->glkx, d * WL_N_K},       {(void**)&h->glkw, d * WL_N_K},
@@ -245,7 +252,9 @@ static void init_allocs(cov_handle* h, std::vector<std::pair<void**, size_t>>& a
       {(void**)&h->wchi, d * nchi},         {(void**)&h->z, d * nchi},
       {(void**)&h->D, d * nchi},            {(void**)&h->ell_d, d * nl},
       {(void**)&h->m, d * nm},              {(void**)&h->om, d * nm},
-      {(void**)&h->sig0, d * nm},           {(void**)&h->dlns, d * nm},
+      {(void**)&h->sig0, d * nmb},          {(void**)&h->dlns, d * nmb},
+      {(void**)&h->mb, d * nmb},            {(void**)&h->omb, d * nmb},
+      {(void**)&h->cs, d * nc},             {(void**)&h->cw, d * nc},
       {(void**)&h->f, d * nchi * nm},       {(void**)&h->b1, d * nchi * nm},
       {(void**)&h->b2, d * nchi * nm},      {(void**)&h->U, d * nl * nchi * nm},
       {(void**)&h->Pl, d * nl * nchi},      {(void**)&h->dPl, d * nl * nchi},
@@ -486,6 +495,8 @@ extern "C" int cov_table(cov_handle* h, const char* name, double* host, int64_t*
       {"z", h->z, h->nchi},
       {"growth", h->D, h->nchi},
       {"mass", h->m, h->nm},
+      {"conc_offsets", h->cs, h->nc},
+      {"conc_weights", h->cw, h->nc},
       {"f", h->f, (int64_t)h->nchi * h->nm},
       {"b1", h->b1, (int64_t)h->nchi * h->nm},
       {"b2", h->b2, (int64_t)h->nchi * h->nm},

@@ -98,7 +98,9 @@ struct cov_handle {
   cov_nz nz{};
   cov_bins bins{};
   // plan (host)
-  int nl = 0, nt = 0, nchi = 0, nm = 0, ntri = 0, K = 0;
+  // nm counts the halo-integral nodes: n_mass mass nodes (nmb) times nc
+  // concentration nodes, the concentration index fastest (nc = 1 without scatter)
+  int nl = 0, nt = 0, nchi = 0, nm = 0, ntri = 0, K = 0, nmb = 0, nc = 1;
   int64_t M = 0, nP = 0, nB = 0;
   int nleg = 0;            // n_ell * n_tomo
   int64_t ntrow = 0;       // rows of the 1-halo trispectrum factor
@@ -114,6 +116,8 @@ struct cov_handle {
   double* scal = nullptr;
   double *chi = nullptr, *wchi = nullptr, *z = nullptr, *D = nullptr;
   double *ell_d = nullptr, *m = nullptr, *om = nullptr, *sig0 = nullptr, *dlns = nullptr;
+  double *mb = nullptr, *omb = nullptr;  // [nmb] mass nodes and weights; m, om: [nm] per (mass, c) node
+  double *cs = nullptr, *cw = nullptr;   // [nc] ln c offsets from the median and their weights
   double *f = nullptr, *b1 = nullptr, *b2 = nullptr, *U = nullptr, *Pl = nullptr, *dPl = nullptr;
   double* Psh = nullptr;  // [n_ell][n_chi][4] P_lin at the shifted k of the ln k differences
   double *zedges = nullptr, *norms = nullptr, *W = nullptr, *sigw2 = nullptr;
@@ -371,8 +375,13 @@ __device__ __forceinline__ void dev_sici(double x, double* si, double* ci) {
 
 // Normalised truncated-NFW Fourier profile u(k|m) with the mean-density
 // (200 x rho_com) mass definition and the Duffy et al. (2008) concentration.
-__device__ __forceinline__ double dev_nfw_u(double k, double m, double z, double rho) {
-  double c = WL_DUFFY_A * pow(m / WL_DUFFY_MPIVOT, WL_DUFFY_B) * pow(1.0 + z, WL_DUFFY_C);
+// median concentration c(m, z) (Duffy et al. 2008, 200 x mean density)
+__device__ __forceinline__ double dev_conc(double m, double z) {
+  return WL_DUFFY_A * pow(m / WL_DUFFY_MPIVOT, WL_DUFFY_B) * pow(1.0 + z, WL_DUFFY_C);
+}
+
+// normalised Fourier transform u(k | m, c) of the truncated NFW profile
+__device__ __forceinline__ double dev_nfw_u(double k, double m, double c, double rho) {
   double rv = cbrt(3.0 * m / (4.0 * WL_PI * WL_DELTA_VIR * rho));
   double x = k * rv / c;
   double s1, c1, s2, c2;

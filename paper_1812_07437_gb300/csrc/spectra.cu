@@ -6,8 +6,11 @@
 // super-sample rows (Eq. WLSSCflatskyLimber).
 //
 // Layout: per-node spectra are [entry][n_chi] (node contiguous); factor rows
-// are [row][n_chi * n_mass] with the mass index contiguous, matching the
-// chi-major halo tables U[b][n][q], f[n][q].
+// are [row][n_chi * nm] with the halo-integral node index q contiguous,
+// matching the chi-major halo tables U[b][n][q], f[n][q].  q runs over the
+// mass nodes, or over (mass, concentration) pairs with the concentration
+// fastest when the lognormal scatter of Eq. LogNormC is on: every sum over q
+// here is then the mass and the concentration integral at once.
 #include "common.cuh"
 
 // One warp per (ell bin, node): I_2^0(k,k), I_1^1(k), I_2^1(k,k) -> P^HM and

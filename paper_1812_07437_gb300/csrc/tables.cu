@@ -40,6 +40,83 @@ __global__ void k_gauss_legendre(int n, double* x, double* w) {
 __global__ void k_chimax(const cov_cosmology* __restrict__ cosmo_p, double zmax, const double* glx,
                          const double* glw, double* scal);
 
+// Normalised probabilists' Hermite polynomials h_k = He_k / sqrt(k!) by the
+// three-term recurrence h_{k+1} = (x h_k - sqrt(k) h_{k-1}) / sqrt(k+1),
+// h_0 = 1, h_1 = x.  Returns h_n(x) and h_{n-1}(x) in *prev (n >= 1).
+__device__ double dev_hermite_h(int n, double x, double* prev) {
+  double p0 = 1.0, p1 = x;
+  for (int k = 1; k < n; ++k) {
+    double p2 = (x * p1 - sqrt((double)k) * p0) / sqrt(k + 1.0);
+    p0 = p1;
+    p1 = p2;
+  }
+  *prev = p0;
+  return p1;
+}
+
+#define WL_GH_GRID 1023
+// Concentration rule of Eq. LogNormC (one block of 256 threads): Gauss-Hermite
+// nodes x_j and weights w_j of the standard normal density (sum w_j = 1),
+// written as ln c offsets cs[j] = sigma x_j and weights cw[j].  The roots of
+// He_n lie in |x| < sqrt(4n + 2); the grid of WL_GH_GRID intervals on that
+// range is finer than their spacing for n <= 32, so each interval holds at
+// most one root.  Each root is bisected to the last bit and weighted by
+// w = 1 / (n h_{n-1}(x)^2).  n <= 1: one node, offset 0, weight 1.  A rule
+// that does not find n roots is written with NaN weights.
+__global__ void k_gauss_hermite(int n, double sigma, double* cs, double* cw) {
+  __shared__ double root[WL_GH_GRID];
+  if (n <= 1) {
+    if (threadIdx.x == 0) {
+      cs[0] = 0.0;
+      cw[0] = 1.0;
+    }
+    return;
+  }
+  const double L = sqrt(4.0 * n + 2.0) + 0.5, dx = 2.0 * L / WL_GH_GRID;
+  double pr;
+  for (int i = threadIdx.x; i < WL_GH_GRID; i += blockDim.x) {
+    double xa = -L + i * dx, xb = -L + (i + 1) * dx;
+    double va = dev_hermite_h(n, xa, &pr), vb = dev_hermite_h(n, xb, &pr);
+    double r = nan("");
+    if (va == 0.0) {
+      r = xa;  // a root on the left end; one on the right end belongs to the next interval
+    } else if (vb != 0.0 && (va < 0.0) != (vb < 0.0)) {
+      double lo = xa, hi = xb;
+      for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        double vm = dev_hermite_h(n, mid, &pr);
+        if (vm == 0.0) {
+          lo = hi = mid;
+          break;
+        }
+        if ((vm < 0.0) == (va < 0.0))
+          lo = mid;
+        else
+          hi = mid;
+      }
+      r = 0.5 * (lo + hi);
+    }
+    root[i] = r;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int found = 0;
+    for (int i = 0; i < WL_GH_GRID; ++i) {
+      if (root[i] != root[i]) continue;
+      if (found < n) {
+        double hprev;
+        dev_hermite_h(n, root[i], &hprev);
+        cs[found] = sigma * root[i];
+        cw[found] = 1.0 / (n * hprev * hprev);
+      }
+      ++found;
+    }
+    if (found != n)
+      for (int j = 0; j < n; ++j) cw[j] = nan("");
+  }
+}
+
 // RK4 integration of the linear growth ODE in ln a from a = 1e-3 to a_t
 __device__ double dev_growth_raw(double at, const cov_cosmology& c) {
   double x = log(WL_A_INIT), x1 = log(at);
@@ -130,10 +207,11 @@ __global__ void k_amplitude(const cov_cosmology* __restrict__ cosmo_p, const dou
   if (threadIdx.x == 0) scal[SC_AMP] = c.sigma8 * c.sigma8 / s;
 }
 
-// mass nodes, sigma(m, 0) and d ln sigma / d ln m (one block per mass node)
+// mass nodes, sigma(m, 0) and d ln sigma / d ln m (one block per mass node);
+// m, om are also written per (mass, concentration) node: om times the c weight
 __global__ void k_sigma(const cov_cosmology* __restrict__ cosmo_p, cov_bins b, const double* glkx,
-                        const double* glkw, const double* scal,
-                        double* m, double* om, double* sig0, double* dlns) {
+                        const double* glkw, const double* scal, int nc, const double* cw,
+                        double* mb, double* omb, double* sig0, double* dlns, double* m, double* om) {
   const cov_cosmology c = *cosmo_p;
   __shared__ double sh[32];
   int q = blockIdx.x;
@@ -154,12 +232,16 @@ __global__ void k_sigma(const cov_cosmology* __restrict__ cosmo_p, cov_bins b, c
   s2 = block_sum(s2, sh);
   ds2 = block_sum(ds2, sh);
   if (threadIdx.x == 0) {
-    m[q] = mq;
+    mb[q] = mq;
     double w = dl * mq;
     if (q == 0 || q == b.n_mass - 1) w *= 0.5;
-    om[q] = w;
+    omb[q] = w;
     sig0[q] = sqrt(s2);
     dlns[q] = (R / 6.0) * ds2 / s2;
+    for (int j = 0; j < nc; ++j) {
+      m[q * nc + j] = mq;
+      om[q * nc + j] = w * cw[j];
+    }
   }
 }
 
@@ -167,8 +249,11 @@ __device__ __forceinline__ double st_amp() {
   return 1.0 / (1.0 + pow(2.0, -WL_ST_P) * tgamma(0.5 - WL_ST_P) / sqrt(WL_PI));
 }
 
-// Sheth-Tormen f_m, PBS biases and the m_min regularisation; one block per node
-__global__ void k_halo(const cov_cosmology* __restrict__ cosmo_p, int nm, const double* D, const double* m,
+// Sheth-Tormen f_m, PBS biases and the m_min regularisation on the mass rule;
+// one block per line-of-sight node.  The values are written for every
+// concentration node of each mass node ([n][q * nc + j]), so the regularised
+// halos at m_min carry the same concentration scatter as the others.
+__global__ void k_halo(const cov_cosmology* __restrict__ cosmo_p, int nm, int nc, const double* D, const double* m,
                        const double* om,
                        const double* sig0, const double* dlns, double* f, double* b1, double* b2) {
   const cov_cosmology c = *cosmo_p;
@@ -187,10 +272,12 @@ __global__ void k_halo(const cov_cosmology* __restrict__ cosmo_p, int nm, const 
     double b1L = -2.0 * nu * a / WL_DELTA_C;
     double b2L = (a * a + ap) * 4.0 * nu * nu / (WL_DELTA_C * WL_DELTA_C) + a * 2.0 * nu / (WL_DELTA_C * WL_DELTA_C);
     double bb1 = 1.0 + b1L, bb2 = (8.0 / 21.0) * b1L + b2L;
-    int idx = n * nm + q;
-    f[idx] = fm;
-    b1[idx] = bb1;
-    b2[idx] = bb2;
+    for (int j = 0; j < nc; ++j) {
+      size_t idx = ((size_t)n * nm + q) * nc + j;
+      f[idx] = fm;
+      b1[idx] = bb1;
+      b2[idx] = bb2;
+    }
     double wq = om[q] * m[q] / rho * fm;
     s0 += wq;
     if (q > 0) {
@@ -202,31 +289,38 @@ __global__ void k_halo(const cov_cosmology* __restrict__ cosmo_p, int nm, const 
   s1 = block_sum(s1, sh);
   s2 = block_sum(s2, sh);
   if (threadIdx.x == 0) {
-    int i0 = n * nm;
+    size_t i0 = (size_t)n * nm * nc;
     double mr0 = m[0] / rho;
     double alpha0 = (1.0 - s0) / mr0;
     double ft = f[i0] + alpha0 / om[0];
-    f[i0] = ft;
     double den = om[0] * mr0 * ft;
-    b1[i0] = (1.0 - s1) / den;
-    b2[i0] = (0.0 - s2) / den;
+    double a1 = (1.0 - s1) / den, a2 = (0.0 - s2) / den;
+    for (int j = 0; j < nc; ++j) {
+      f[i0 + j] = ft;
+      b1[i0 + j] = a1;
+      b2[i0 + j] = a2;
+    }
   }
 }
 
 // NFW profiles on the Limber grid and P_lin, dP_lin/dln k at k = l_b/chi_n
-__global__ void k_profiles(const cov_cosmology* __restrict__ cosmo_p, cov_bins b, const double* ell,
-                           const double* chi, const double* z,
+// at every (mass, concentration) node: u(k | m_q, c_bar(m_q, z_n) exp(cs[j]))
+__global__ void k_profiles(const cov_cosmology* __restrict__ cosmo_p, cov_bins b, int nm, int nc, const double* cs,
+                           const double* ell, const double* chi, const double* z,
                            const double* D, const double* m, const double* scal, double* U, double* Pl,
                            double* dPl, double* Psh) {
   const cov_cosmology c = *cosmo_p;
   int bn = blockIdx.x;  // b * nchi + n
-  int nchi = b.n_chi, nm = b.n_mass;
+  int nchi = b.n_chi;
   int bb = bn / nchi, n = bn % nchi;
   double k = ell[bb] / chi[n];
   bool valid = k <= b.k_max;
   double rho = WL_RHO_CRIT0 * c.Om;
-  for (int q = threadIdx.x; q < nm; q += blockDim.x)
-    U[(size_t)bn * nm + q] = valid ? dev_nfw_u(k, m[q], z[n], rho) : 0.0;
+  for (int q = threadIdx.x; q < nm; q += blockDim.x) {
+    double cq = dev_conc(m[q], z[n]);
+    if (nc > 1) cq *= exp(cs[q % nc]);
+    U[(size_t)bn * nm + q] = valid ? dev_nfw_u(k, m[q], cq, rho) : 0.0;
+  }
   if (threadIdx.x < 4) {
     // P_lin at k exp(s), s = -2h, -h, +h, +2h (the 4th-order differences in ln k)
     const double sh[4] = {-2.0 * WL_FD_H, -WL_FD_H, WL_FD_H, 2.0 * WL_FD_H};
@@ -367,7 +461,8 @@ int wl_quadrature(cov_handle* h, cudaStream_t s) {
   k_gauss_legendre<<<1, 64, 0, s>>>(WL_N_GL_CHI, h->gl64x, h->gl64w);
   k_gauss_legendre<<<(WL_N_K + 127) / 128, 128, 0, s>>>(WL_N_K, h->glkx, h->glkw);
   k_gauss_legendre<<<(h->nchi + 127) / 128, 128, 0, s>>>(h->nchi, h->glcx, h->glcw);
-  WL_LAUNCH(h, "k_gauss_legendre");
+  k_gauss_hermite<<<1, 256, 0, s>>>(h->nc, h->bins.sigma_lnc, h->cs, h->cw);
+  WL_LAUNCH(h, "quadrature kernels");
   return COV_OK;
 }
 
@@ -380,10 +475,11 @@ int wl_tables(cov_handle* h, cudaStream_t s) {
                                             h->wchi, h->z, h->D);
   k_growth_norm<<<(h->nchi + 127) / 128, 128, 0, s>>>(h->nchi, h->scal, h->D);
   k_amplitude<<<1, 256, 0, s>>>(c, h->glkx, h->glkw, h->scal);
-  k_sigma<<<h->nm, 256, 0, s>>>(c, b, h->glkx, h->glkw, h->scal, h->m, h->om, h->sig0, h->dlns);
-  k_halo<<<h->nchi, 128, 0, s>>>(c, h->nm, h->D, h->m, h->om, h->sig0, h->dlns, h->f, h->b1, h->b2);
-  k_profiles<<<h->nl * h->nchi, 128, 0, s>>>(c, b, h->ell_d, h->chi, h->z, h->D, h->m, h->scal, h->U, h->Pl,
-                                             h->dPl, h->Psh);
+  k_sigma<<<h->nmb, 256, 0, s>>>(c, b, h->glkx, h->glkw, h->scal, h->nc, h->cw, h->mb, h->omb, h->sig0, h->dlns,
+                                 h->m, h->om);
+  k_halo<<<h->nchi, 128, 0, s>>>(c, h->nmb, h->nc, h->D, h->mb, h->omb, h->sig0, h->dlns, h->f, h->b1, h->b2);
+  k_profiles<<<h->nl * h->nchi, 128, 0, s>>>(c, b, h->nm, h->nc, h->cs, h->ell_d, h->chi, h->z, h->D, h->m, h->scal,
+                                             h->U, h->Pl, h->dPl, h->Psh);
   k_edges<<<1, 64, 0, s>>>(nz, h->zedges, h->scal);
   k_norms<<<h->nt, 64, 0, s>>>(nz, h->zedges, h->gl64x, h->gl64w, h->norms);
   k_kernels<<<h->nchi, 64, 0, s>>>(c, nz, h->nchi, h->chi, h->z, h->zedges, h->norms, h->gl64x, h->gl64w, h->W);

@@ -69,7 +69,7 @@ class cov_nz(C.Structure):
 class cov_bins(C.Structure):
     _fields_ = [("n_ell", C.c_int), ("ell_min", C.c_double), ("ell_max", C.c_double), ("f_sky", C.c_double),
                 ("n_chi", C.c_int), ("n_mass", C.c_int), ("m_min", C.c_double), ("m_max", C.c_double),
-                ("k_max", C.c_double)]
+                ("k_max", C.c_double), ("n_conc", C.c_int), ("sigma_lnc", C.c_double)]
 
 
 class cov_opts(C.Structure):
@@ -179,5 +179,6 @@ def structs_from_workload(wl):
     ns = cov_nz(int(nz["n_tomo"]), *(float(nz[k]) for k in (
         "z0", "alpha", "zmin", "zmax", "photoz_sigma0", "n_gal_arcmin2", "sigma_e")))
     bs = cov_bins(int(b["n_ell"]), float(b["ell_min"]), float(b["ell_max"]), float(b["f_sky"]), int(b["n_chi"]),
-                  int(b["n_mass"]), float(b["m_min"]), float(b["m_max"]), float(b["k_max"]))
+                  int(b["n_mass"]), float(b["m_min"]), float(b["m_max"]), float(b["k_max"]),
+                  int(b.get("n_conc", 0)), float(b.get("sigma_lnc", 0.0)))
     return cs, ns, bs

@@ -50,6 +50,13 @@ def test_invalid_arguments_rejected_on_host(lib):
     bs2 = N.cov_bins(*[getattr(bs, f) for f, _ in N.cov_bins._fields_])
     bs2.f_sky = 1.5
     assert lib.cov_init(C.byref(cs), C.byref(ns), C.byref(bs2), None, C.byref(h)) == N.COV_ERR_INVALID
+    # concentration rule: at most 32 nodes, 0 <= sigma_lnc <= 2, n_mass * n_conc <= 4096
+    for n_conc, sig, n_mass in ((33, 0.18, 12), (-1, 0.18, 12), (8, -0.1, 12), (8, float("nan"), 12),
+                                (8, 2.5, 12), (16, 0.18, 257)):
+        bs3 = N.cov_bins(*[getattr(bs, f) for f, _ in N.cov_bins._fields_])
+        bs3.n_conc, bs3.sigma_lnc, bs3.n_mass = n_conc, sig, n_mass
+        assert lib.cov_init(C.byref(cs), C.byref(ns), C.byref(bs3), None, C.byref(h)) == N.COV_ERR_INVALID
+        assert not h.value
     assert lib.cov_spectra(None, None, None) == N.COV_ERR_INVALID
     assert lib.cov_snr(None, None, 0, None, 0, None, None) == N.COV_ERR_INVALID
     assert lib.cov_assemble_band(None, 0, 256, None, 0, N.COV_LAYOUT_TILES, N.COV_TERMS_ALL, N.COV_SPLIT_BF16,
