@@ -11,7 +11,13 @@
   the first mass node and the node-0 biases replaced by alpha_1, alpha_2 so
   that the discrete consistency relations (Eq. BoundinMass) hold exactly.
 * Concentration: Duffy et al. (2008) mean-density fit c = 10.14
-  (m / 2e12)^-0.081 (1+z)^-1.01 with r_200m = (3m/(4 pi 200 rho_com))^(1/3).
+  (m / 2e12)^-0.081 (1+z)^-1.01 with r_200m = (3m/(4 pi 200 rho_com))^(1/3);
+  or the Bullock et al. (2001) median the paper uses (Sec. 6):
+  c_bar = K a(z) / a_c with nu(F m, a_c) = 1, i.e. the collapse epoch a_c at
+  which D(a_c) sigma(F m, z=0) = delta_c (D(1) = 1), F = 0.01, K = 4.0.  a_c
+  is the root of the growth ODE's solution on [1e-3, 100]; where F m has not
+  collapsed by a = 100 (the growth is then within 0.4% of its asymptote) a_c
+  is taken as 100.
 * NFW Fourier profile u(k, m, c) in sine/cosine integrals, u(0) = 1.
 * Concentration scatter (Eq. LogNormC, the paper's "model A"): ln c is
   normal about ln c_bar(m, z) with sigma_lnc (0.18 in the paper).  The c
@@ -28,7 +34,10 @@ import math
 
 import numpy as np
 from numpy.polynomial.hermite_e import hermegauss
+from scipy.optimize import brentq
 from scipy.special import sici
+
+from . import cosmology as cz
 
 ST_Q = 0.707
 ST_P = 0.3
@@ -38,6 +47,11 @@ DUFFY_B = -0.081
 DUFFY_C = -1.01
 DUFFY_MPIVOT = 2.0e12
 DELTA_VIR = 200.0
+BULLOCK_F = 0.01
+BULLOCK_K = 4.0
+A_COLLAPSE_MAX = 100.0
+CONC_DUFFY = 0
+CONC_BULLOCK = 1
 
 
 def st_amplitude():
@@ -113,6 +127,34 @@ def regularise(m, om, fm, b1, b2, rho):
 def concentration(m, z):
     """Duffy et al. (2008) c(m, z) for the 200 x mean-density mass definition."""
     return DUFFY_A * (np.asarray(m) / DUFFY_MPIVOT) ** DUFFY_B * (1.0 + z) ** DUFFY_C
+
+
+def collapse_epoch(sigma_Fm, cosmo):
+    """a_c with D(a_c) sigma(F m, 0) = delta_c for each sigma(F m, 0) (D(1) = 1),
+    D from the growth ODE (cosmology.growth's RK4 rule carried to a_c), by
+    Brent's method in ln a; A_COLLAPSE_MAX where no root lies below it, the
+    start of the growth rule where the root lies before it."""
+    d1 = cz._growth_raw(1.0, cosmo)
+    dmax = cz._growth_raw(A_COLLAPSE_MAX, cosmo) / d1
+    dmin = cz._growth_raw(cz.A_INIT, cosmo) / d1
+    out = []
+    for s in np.atleast_1d(sigma_Fm):
+        target = DELTA_C / s
+        if dmax <= target:
+            out.append(A_COLLAPSE_MAX)
+            continue
+        if dmin >= target:  # collapsed before the growth rule starts (never for m >= 1e2 Msun/h)
+            out.append(cz.A_INIT)
+            continue
+        g = lambda lna: cz._growth_raw(math.exp(lna), cosmo) / d1 - target
+        out.append(math.exp(brentq(g, math.log(cz.A_INIT), math.log(A_COLLAPSE_MAX), xtol=1e-15, rtol=9e-16,
+                                   maxiter=200)))
+    return np.array(out)
+
+
+def bullock_concentration(a_c, z):
+    """Bullock et al. (2001) median c_bar = K a(z) / a_c."""
+    return BULLOCK_K / ((1.0 + z) * np.asarray(a_c))
 
 
 def conc_rule(n_conc, sigma_lnc):

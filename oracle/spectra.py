@@ -61,6 +61,11 @@ class Tables:
         self.m, self.om = halo.mass_nodes(bins["n_mass"], bins["m_min"], bins["m_max"])
         self.mr = self.m / self.rho
         sig0, dlns = cz.sigma_and_dlnsigma_dlnm(self.m, self.amp, cosmo)
+        # median concentration rule (Duffy fit, or the Bullock et al. median of Sec. 6)
+        self.conc_model = int(bins.get("conc_model", halo.CONC_DUFFY))
+        if self.conc_model == halo.CONC_BULLOCK:
+            sigF, _ = cz.sigma_and_dlnsigma_dlnm(halo.BULLOCK_F * self.m, self.amp, cosmo)
+            self.a_c = halo.collapse_epoch(sigF, cosmo)
         nchi, nm = bins["n_chi"], bins["n_mass"]
         self.f = np.empty((nchi, nm))
         self.b1 = np.empty((nchi, nm))
@@ -82,7 +87,7 @@ class Tables:
         for b in range(nl):
             for n in range(nchi):
                 if self.valid[b, n]:
-                    cbar = halo.concentration(self.m, self.z[n])
+                    cbar = self.cbar(n)
                     for j in range(nc):
                         self.U[b, n, :, j] = halo.nfw_u(self.k[b, n], self.m, self.z[n], self.rho,
                                                         cbar * math.exp(self.cs[j]))
@@ -93,6 +98,12 @@ class Tables:
         self.W = survey.lensing_kernels(self.chi, self.z, nz, cosmo, self.zedges)
         self.noise = survey.shot_noise(nz)
         self.sigW2 = sigma_w2(self.chi, self.D, self.theta, self.amp, cosmo)
+
+    def cbar(self, n):
+        """Median concentration of every mass node at line-of-sight node n."""
+        if self.conc_model == halo.CONC_BULLOCK:
+            return halo.bullock_concentration(self.a_c, self.z[n])
+        return halo.concentration(self.m, self.z[n])
 
     # -- halo integrals -------------------------------------------------
     def I(self, legs, mu, beta, n):

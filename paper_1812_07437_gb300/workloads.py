@@ -22,6 +22,7 @@ Fixed choices where the configurations are silent: Omega_b = 0.049,
 T_CMB = 2.7255 K, w0 = -1, k_max = 50 h/Mpc, m in [1e10, 1e16] Msun/h.
 """
 import copy
+import math
 
 TERM_G = 1
 TERM_1H = 2
@@ -61,6 +62,25 @@ WORKLOADS = {
     "mid_2bin": _wl("mid_2bin", 2, 0.0, 8, 20.0, 3000.0, 40, 36, TERMS_ALL),
     "mid_3bin": _wl("mid_3bin", 3, 0.05, 6, 30.0, 4000.0, 48, 40, TERMS_ALL),
 }
+
+
+# The paper's own set-up (Sec. 1, Appendix A and Sec. 6): its cosmology, 14
+# log-spaced ell bins on [10, 5000], n(z) with z0 = 0.9/sqrt(2) normalised on
+# [0.001, 2.5], 30 sources per arcmin^2, sigma_e = 0.3, f_sky = 0.36, no
+# photometric-redshift scatter, halo masses from 1e9 to 1e16 Msun/h and the
+# Bullock et al. median concentration (conc_model 1).
+PAPER_COSMOLOGY = dict(Om=0.238, Ob=0.042, h=0.732, ns=0.958, sigma8=0.76, w0=-1.0, Tcmb=2.7255)
+
+
+def paper_workload(n_tomo, n_chi=128, n_mass=96, sigma_e=0.3, n_conc=0):
+    """The paper's set-up with n_tomo equipopulated bins (sigma_e = 0: no shape noise)."""
+    return dict(name=f"paper_{n_tomo}bin", cosmology=dict(PAPER_COSMOLOGY),
+                nz=dict(n_tomo=n_tomo, z0=0.9 / math.sqrt(2.0), alpha=1.5, zmin=0.001, zmax=2.5,
+                        photoz_sigma0=0.0, n_gal_arcmin2=30.0, sigma_e=sigma_e),
+                bins=dict(n_ell=14, ell_min=10.0, ell_max=5000.0, f_sky=0.36, n_chi=n_chi, n_mass=n_mass,
+                          m_min=1.0e9, m_max=1.0e16, k_max=50.0, conc_model=1, n_conc=n_conc,
+                          sigma_lnc=SIGMA_LNC),
+                terms=TERMS_ALL)
 
 
 def get(name, **overrides):
