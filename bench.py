@@ -66,6 +66,8 @@ def parse():
                    help="also run the concentration-scatter comparison (model A against model B)")
     p.add_argument("--model-a-workload", default="cfg3_5bin")
     p.add_argument("--model-a-nodes", type=int, default=8, help="concentration nodes of model A")
+    p.add_argument("--paper-replica", action="store_true",
+                   help="also run the S/N experiments of the paper's own set-up (Sec. 5)")
     return p.parse_args()
 
 
@@ -481,6 +483,88 @@ def model_a_run(prec, device, name, n_conc):
     return out
 
 
+def paper_run(device):
+    """The paper's own set-up (its cosmology, 14 ell bins on [10, 5000], m_min = 1e9,
+    Bullock median concentration, sigma_e = 0.3): the cumulative S/N at ell_max = 5000 of
+    P, B and the joint vector for 1, 2 and 5 tomographic bins and of P for 10 bins, with
+    the covariance term sets of the paper's Sec. 5 figures (G; G + NGins; G + NGssc; all),
+    P at 10 bins also without shape noise, and the relative changes the paper states
+    them by.  The covariances are assembled in the FP64 form: without photo-z scatter the
+    tomographic kernels overlap strongly and the scaled covariance's smallest eigenvalue
+    falls to ~1e-3 at 2 bins and below at 5, where the split form's ~1e-5 element error
+    can move it below zero.  The 10-bin case holds the power-spectrum rows alone (in the
+    cumulative row order, its S/N taken in place on packed tiles)."""
+    import numpy as np
+    import torch
+    from paper_1812_07437_gb300 import native as N
+    from paper_1812_07437_gb300 import workloads
+    from paper_1812_07437_gb300.handle import Handle, packed_tiles
+    dev = torch.device("cuda", device)
+    ins = N.COV_TERM_1H | N.COV_TERM_BBPT | N.COV_TERM_PB
+    sets = {"G": N.COV_TERM_G, "G+NGins": N.COV_TERM_G | ins, "G+NGssc": N.COV_TERM_G | N.COV_TERM_SSC,
+            "all": N.COV_TERMS_ALL}
+
+    def last(v):
+        v = np.asarray(v)
+        f = v[np.isfinite(v)]
+        return float(f[-1]) if f.size else None
+
+    out = {}
+    t0 = time.perf_counter()
+    for nt, sigma_e, which in ((1, 0.3, "PBJ"), (2, 0.3, "PBJ"), (5, 0.3, "PBJ"), (10, 0.3, "P"), (10, 0.0, "P")):
+        key = f"{nt}bin" + ("" if sigma_e > 0 else "_no_noise")
+        wl = workloads.paper_workload(nt, sigma_e=sigma_e)
+        joint = which == "PBJ"
+        # the power-spectrum rows alone: a cumulative-order handle, its S/N in place on packed tiles
+        h = Handle(wl, device=device) if joint else Handle(wl, device=device, rows=N.COV_ROWS_P,
+                                                           order=N.COV_ORDER_CUMULATIVE)
+        res = {"M": h.M, "n_P": h.n_P, "n_B": h.n_B}
+        try:
+            D = torch.zeros(h.M, dtype=torch.float64, device=dev)
+            h.spectra(D)
+            if joint:
+                C = torch.zeros(h.M, h.M, dtype=torch.float64, device=dev)
+            else:
+                C = torch.full((packed_tiles(h.M + 1) * 65536,), float("nan"), dtype=torch.float64, device=dev)
+            for name, terms in sets.items():
+                if joint:
+                    h.assemble(C, terms, N.COV_FP64)
+                    res[name] = {w: last(h.snr(C, D, wi)) for w, wi in
+                                 (("P", N.COV_WHICH_P), ("B", N.COV_WHICH_B), ("joint", N.COV_WHICH_JOINT))}
+                else:
+                    h.assemble_band(0, h.M, C, N.COV_LAYOUT_TILES, terms, N.COV_FP64)
+                    res[name] = {"P": last(h.snr_tiles(C, D))}
+            del C, D
+        except Exception as e:  # noqa: BLE001  (one case's failure is recorded; the others still run)
+            res["error"] = f"{type(e).__name__}: {e}"
+        out[key] = res
+        h.close()
+        torch.cuda.empty_cache()
+    red = lambda a, b: 1.0 - a / b if a is not None and b is not None else None
+    gain = lambda a, b: a / b - 1.0 if a is not None and b else None
+    get = lambda key, s, w: out.get(key, {}).get(s, {}).get(w)
+    out["derived"] = {
+        "P_10bin_loss_vs_G": {k: red(get("10bin", k, "P"), get("10bin", "G", "P"))
+                              for k in ("G+NGins", "G+NGssc", "all")},
+        "P_loss_vs_10bin_all_terms": {f"{n}bin": red(get(f"{n}bin", "all", "P"), get("10bin", "all", "P"))
+                                      for n in (5, 2, 1)},
+        "B_loss_from_ssc": {f"{n}bin": red(get(f"{n}bin", "all", "B"), get(f"{n}bin", "G+NGins", "B"))
+                            for n in (1, 2, 5)},
+        "joint_loss_from_ssc": {f"{n}bin": red(get(f"{n}bin", "all", "joint"), get(f"{n}bin", "G+NGins", "joint"))
+                                for n in (1, 2, 5)},
+        "joint_gain_over_P": {f"{n}bin": gain(get(f"{n}bin", "all", "joint"), get(f"{n}bin", "all", "P"))
+                              for n in (1, 2, 5)},
+        "paper_states": {"P_10bin_loss_vs_G": {"G+NGins": 0.30, "G+NGssc": 0.40, "all": 0.45},
+                         "P_loss_vs_10bin_all_terms": {"5bin": 0.01, "2bin": 0.05, "1bin": 0.25},
+                         "B_loss_from_ssc": {"1bin": 0.20, "2bin": 0.15, "5bin": 0.15},
+                         "joint_loss_from_ssc": {"1bin": 0.30, "2bin": 0.25, "5bin": 0.25},
+                         "joint_gain_over_P": {"1bin": 0.10, "2bin": 0.10, "5bin": 0.10}}}
+    out["seconds"] = time.perf_counter() - t0
+    out["precision"] = "fp64"
+    out["quadrature"] = "N_chi = 128, N_M = 96"
+    return out
+
+
 def snr_tiles_run(wl, prec, device, row_sets):
     """Cumulative S/N of the workload's own data vector without a dense square:
     a handle in cumulative row order assembles its lower-packed tiles (plus one
@@ -751,8 +835,17 @@ def run_ours(args):
         out["snr_tiles"] = snr_tiles_run(workloads.get(args.workload), sp, local,
                                          [(r, sets[r]) for r in args.snr_rows.split(",") if r])
         out["snr_tiles"]["precision"] = "fp64" if sp == N.COV_FP64 else "split_bf16"
+    # optional stages: a failure is recorded in the line instead of losing it
     if args.model_a and rank == 0 and world == 1:
-        out["model_a"] = model_a_run(prec, local, args.model_a_workload, args.model_a_nodes)
+        try:
+            out["model_a"] = model_a_run(prec, local, args.model_a_workload, args.model_a_nodes)
+        except Exception as e:  # noqa: BLE001
+            out["model_a"] = {"error": f"{type(e).__name__}: {e}"}
+    if args.paper_replica and rank == 0 and world == 1:
+        try:
+            out["paper_replica"] = paper_run(local)
+        except Exception as e:  # noqa: BLE001
+            out["paper_replica"] = {"error": f"{type(e).__name__}: {e}"}
     if not args.no_serve and packed and rank == 0 and world == 1:
         sv = serving_run(prec, args.serve_requests, args.serve_rate, args.serve_budget_gb, args.serve_slots, local)
         # the same mix offered at about half the rate the first run achieved

@@ -69,9 +69,16 @@ typedef struct {
   double z0, alpha, zmin, zmax, photoz_sigma0, n_gal_arcmin2, sigma_e;
 } cov_nz;
 
+/* Median concentration c(m, z) of the NFW profiles (Sec. 4.1, Sec. 6). */
+#define COV_CONC_DUFFY 0   /* Duffy et al. (2008), 200 x mean density: 10.14 (m/2e12)^-0.081 (1+z)^-1.01 */
+#define COV_CONC_BULLOCK 1 /* Bullock et al. (2001), the paper's choice: K a(z)/a_c with nu(F m, a_c) = 1, */
+                           /* F = 0.01, K = 4 (a_c capped at a = 100 where F m never collapses), floored  */
+                           /* at c = 1                                                                    */
+
 /* n_ell log-spaced ell bins on [ell_min, ell_max] (Sec. 3.2.1, App. A), sky
  * fraction f_sky, n_chi Gauss-Legendre line-of-sight nodes, n_mass log mass
- * nodes on [m_min, m_max] Msun/h, 3D cut k_max h/Mpc (Sec. 4.4).
+ * nodes on [m_min, m_max] Msun/h, 3D cut k_max h/Mpc (Sec. 4.4), median
+ * concentration conc_model (COV_CONC_*; zero-initialised: Duffy).
  *
  * Concentration scatter (Eq. LogNormC; the paper's "model A" of Sec. 6):
  * with n_conc >= 2 every halo integral of Eq. ImunuHalos also averages the
@@ -88,6 +95,7 @@ typedef struct {
   double m_min, m_max, k_max;
   int n_conc;
   double sigma_lnc;
+  int conc_model;
 } cov_bins;
 
 /* Row set and row order of the data vector (Sec. 5). */
@@ -197,8 +205,9 @@ int cov_snr(cov_handle* h, const double* d_C, int64_t ldc, const double* d_D, in
 
 /* Copy an internal FP64 table to host memory for inspection (tests).  name is
  * one of "chi", "wchi", "z", "growth", "mass", "conc_offsets", "conc_weights",
- * "f", "b1", "b2", "U", "Plin", "dPlin", "W", "sigw2", "P3", "RP3", "B3",
- * "RB3", "B1h3", "Ps", "B1h"; *count receives the number of doubles (pass
+ * "collapse_a" (Bullock median only; empty otherwise), "f", "b1", "b2", "U",
+ * "Plin", "dPlin", "W", "sigw2", "P3", "RP3", "B3", "RB3", "B1h3", "Ps",
+ * "B1h"; *count receives the number of doubles (pass
  * host = NULL to query).  "mass", "f", "b1", "b2" and "U" run over the
  * (mass, concentration) nodes, the concentration index fastest. */
 int cov_table(cov_handle* h, const char* name, double* host, int64_t* count, void* stream);

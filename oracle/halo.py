@@ -17,7 +17,9 @@
   which D(a_c) sigma(F m, z=0) = delta_c (D(1) = 1), F = 0.01, K = 4.0.  a_c
   is the root of the growth ODE's solution on [1e-3, 100]; where F m has not
   collapsed by a = 100 (the growth is then within 0.4% of its asymptote) a_c
-  is taken as 100.
+  is taken as 100.  The median is floored at c = 1 (scale radius inside the
+  virial radius): below it the fit is far outside the masses it was calibrated
+  on and the Si/Ci form of u loses ~1/c^2 of its digits.
 * NFW Fourier profile u(k, m, c) in sine/cosine integrals, u(0) = 1.
 * Concentration scatter (Eq. LogNormC, the paper's "model A"): ln c is
   normal about ln c_bar(m, z) with sigma_lnc (0.18 in the paper).  The c
@@ -49,6 +51,7 @@ DUFFY_MPIVOT = 2.0e12
 DELTA_VIR = 200.0
 BULLOCK_F = 0.01
 BULLOCK_K = 4.0
+BULLOCK_C_MIN = 1.0
 A_COLLAPSE_MAX = 100.0
 CONC_DUFFY = 0
 CONC_BULLOCK = 1
@@ -153,8 +156,8 @@ def collapse_epoch(sigma_Fm, cosmo):
 
 
 def bullock_concentration(a_c, z):
-    """Bullock et al. (2001) median c_bar = K a(z) / a_c."""
-    return BULLOCK_K / ((1.0 + z) * np.asarray(a_c))
+    """Bullock et al. (2001) median c_bar = K a(z) / a_c, floored at BULLOCK_C_MIN."""
+    return np.maximum(BULLOCK_K / ((1.0 + z) * np.asarray(a_c)), BULLOCK_C_MIN)
 
 
 def conc_rule(n_conc, sigma_lnc):

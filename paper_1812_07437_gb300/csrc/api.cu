@@ -195,7 +195,7 @@ static int validate(const cov_cosmology* c, const cov_nz* nz, const cov_bins* b)
   if (b->n_chi < 2 || b->n_chi > 4096 || b->n_mass < 2 || b->n_mass > 4096) return COV_ERR_INVALID;
   if (!(b->m_min > 0) || !(b->m_max > b->m_min) || !(b->k_max > 0)) return COV_ERR_INVALID;
   if (b->n_conc < 0 || b->n_conc > 32 || !(b->sigma_lnc >= 0 && b->sigma_lnc <= 2) ||
-      b->n_mass * std::max(b->n_conc, 1) > 4096)
+      b->n_mass * std::max(b->n_conc, 1) > 4096 || (b->conc_model != COV_CONC_DUFFY && b->conc_model != COV_CONC_BULLOCK))
     return COV_ERR_INVALID;
   if (!(c->Om > 0 && c->Om <= 1) || !(c->Ob > 0 && c->Ob < c->Om) || !(c->h > 0) || !(c->sigma8 > 0) ||
       !(c->Tcmb > 0))
@@ -225,7 +225,7 @@ static void free_all(cov_handle* h) {
                   h->C2,    h->C3,    h->tc_status, h->Thi,   h->Tlo,    h->Tscale, h->Trows,     h->Tmat,
                   h->Srows, h->cosmo_d, h->Fsig,  h->Esig,    h->Msig,   h->FsigT,  h->EsigT,     h->MsigT,
                   h->invN,  h->omN,   h->work,    h->chol_scratch, h->chol_status, h->mb, h->omb, h->cs,
-                  h->cw};
+                  h->cw,    h->sigF,  h->ac};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->tile_ring) cudaFree(h->tile_ring);
@@ -255,6 +255,7 @@ static void init_allocs(cov_handle* h, std::vector<std::pair<void**, size_t>>& a
       {(void**)&h->sig0, d * nmb},          {(void**)&h->dlns, d * nmb},
       {(void**)&h->mb, d * nmb},            {(void**)&h->omb, d * nmb},
       {(void**)&h->cs, d * nc},             {(void**)&h->cw, d * nc},
+      {(void**)&h->sigF, d * nmb},          {(void**)&h->ac, d * nmb},
       {(void**)&h->f, d * nchi * nm},       {(void**)&h->b1, d * nchi * nm},
       {(void**)&h->b2, d * nchi * nm},      {(void**)&h->U, d * nl * nchi * nm},
       {(void**)&h->Pl, d * nl * nchi},      {(void**)&h->dPl, d * nl * nchi},
@@ -497,6 +498,7 @@ extern "C" int cov_table(cov_handle* h, const char* name, double* host, int64_t*
       {"mass", h->m, h->nm},
       {"conc_offsets", h->cs, h->nc},
       {"conc_weights", h->cw, h->nc},
+      {"collapse_a", h->ac, h->bins.conc_model == COV_CONC_BULLOCK ? h->nmb : 0},
       {"f", h->f, (int64_t)h->nchi * h->nm},
       {"b1", h->b1, (int64_t)h->nchi * h->nm},
       {"b2", h->b2, (int64_t)h->nchi * h->nm},

@@ -30,6 +30,10 @@
 #define WL_N_ZS 64         // nodes per source-redshift piece of W_i
 #define WL_N_RK4 1024      // RK4 steps of the growth ODE
 #define WL_A_INIT 1.0e-3
+#define WL_BULLOCK_F 0.01        // Bullock et al. median: nu(F m, a_c) = 1, c = K a / a_c
+#define WL_BULLOCK_K 4.0
+#define WL_BULLOCK_C_MIN 1.0     // floor of that median: scale radius inside the virial radius
+#define WL_A_COLLAPSE_MAX 100.0  // a_c where F m has not collapsed by then
 #define WL_N_K 4096        // nodes of the sigma(R) and sigma_W^2 rules
 #define WL_LNK_MIN (-11.512925464970229)  // ln 1e-5
 #define WL_LNK_MAX (6.907755278982137)    // ln 1e3
@@ -118,6 +122,7 @@ struct cov_handle {
   double *ell_d = nullptr, *m = nullptr, *om = nullptr, *sig0 = nullptr, *dlns = nullptr;
   double *mb = nullptr, *omb = nullptr;  // [nmb] mass nodes and weights; m, om: [nm] per (mass, c) node
   double *cs = nullptr, *cw = nullptr;   // [nc] ln c offsets from the median and their weights
+  double *sigF = nullptr, *ac = nullptr; // [nmb] sigma(F m, 0) and collapse epoch a_c (Bullock median)
   double *f = nullptr, *b1 = nullptr, *b2 = nullptr, *U = nullptr, *Pl = nullptr, *dPl = nullptr;
   double* Psh = nullptr;  // [n_ell][n_chi][4] P_lin at the shifted k of the ln k differences
   double *zedges = nullptr, *norms = nullptr, *W = nullptr, *sigw2 = nullptr;

@@ -47,9 +47,10 @@ std::string key_of(const cov_request& r) {
   char buf[512];
   const cov_nz& z = r.nz;
   const cov_bins& b = r.bins;
-  snprintf(buf, sizeof buf, "%d|%a|%a|%a|%a|%a|%a|%a|%d|%a|%a|%a|%d|%d|%a|%a|%a|%d|%a", z.n_tomo, z.z0, z.alpha,
-           z.zmin, z.zmax, z.photoz_sigma0, z.n_gal_arcmin2, z.sigma_e, b.n_ell, b.ell_min, b.ell_max, b.f_sky,
-           b.n_chi, b.n_mass, b.m_min, b.m_max, b.k_max, b.n_conc > 1 ? b.n_conc : 1, b.n_conc > 1 ? b.sigma_lnc : 0.0);
+  snprintf(buf, sizeof buf, "%d|%a|%a|%a|%a|%a|%a|%a|%d|%a|%a|%a|%d|%d|%a|%a|%a|%d|%a|%d", z.n_tomo, z.z0,
+           z.alpha, z.zmin, z.zmax, z.photoz_sigma0, z.n_gal_arcmin2, z.sigma_e, b.n_ell, b.ell_min, b.ell_max,
+           b.f_sky, b.n_chi, b.n_mass, b.m_min, b.m_max, b.k_max, b.n_conc > 1 ? b.n_conc : 1,
+           b.n_conc > 1 ? b.sigma_lnc : 0.0, b.conc_model);
   return buf;
 }
 

@@ -208,10 +208,11 @@ __global__ void k_amplitude(const cov_cosmology* __restrict__ cosmo_p, const dou
 }
 
 // mass nodes, sigma(m, 0) and d ln sigma / d ln m (one block per mass node);
-// m, om are also written per (mass, concentration) node: om times the c weight
+// m, om are also written per (mass, concentration) node: om times the c weight.
+// For the Bullock median also sigma(F m, 0), the variance of the collapsing mass.
 __global__ void k_sigma(const cov_cosmology* __restrict__ cosmo_p, cov_bins b, const double* glkx,
                         const double* glkw, const double* scal, int nc, const double* cw,
-                        double* mb, double* omb, double* sig0, double* dlns, double* m, double* om) {
+                        double* mb, double* omb, double* sig0, double* dlns, double* m, double* om, double* sigF) {
   const cov_cosmology c = *cosmo_p;
   __shared__ double sh[32];
   int q = blockIdx.x;
@@ -219,8 +220,10 @@ __global__ void k_sigma(const cov_cosmology* __restrict__ cosmo_p, cov_bins b, c
   double mq = b.m_min * exp(dl * q);
   double rho = WL_RHO_CRIT0 * c.Om;
   double R = cbrt(3.0 * mq / (4.0 * WL_PI * rho));
+  const bool bullock = b.conc_model == COV_CONC_BULLOCK;
+  double RF = cbrt(3.0 * (WL_BULLOCK_F * mq) / (4.0 * WL_PI * rho));
   double amp = scal[SC_AMP];
-  double half = 0.5 * (WL_LNK_MAX - WL_LNK_MIN), s2 = 0.0, ds2 = 0.0;
+  double half = 0.5 * (WL_LNK_MAX - WL_LNK_MIN), s2 = 0.0, ds2 = 0.0, s2F = 0.0;
   for (int i = threadIdx.x; i < WL_N_K; i += blockDim.x) {
     double lk = WL_LNK_MIN + half * (glkx[i] + 1.0);
     double k = exp(lk), T = dev_eh_T(k, c);
@@ -228,9 +231,14 @@ __global__ void k_sigma(const cov_cosmology* __restrict__ cosmo_p, cov_bins b, c
     double x = k * R, Wx = dev_tophat(x);
     s2 += half * glkw[i] * d2 * Wx * Wx;
     ds2 += half * glkw[i] * d2 * 2.0 * Wx * dev_dtophat(x) * k;
+    if (bullock) {
+      double WF = dev_tophat(k * RF);
+      s2F += half * glkw[i] * d2 * WF * WF;
+    }
   }
   s2 = block_sum(s2, sh);
   ds2 = block_sum(ds2, sh);
+  if (bullock) s2F = block_sum(s2F, sh);
   if (threadIdx.x == 0) {
     mb[q] = mq;
     double w = dl * mq;
@@ -238,11 +246,50 @@ __global__ void k_sigma(const cov_cosmology* __restrict__ cosmo_p, cov_bins b, c
     omb[q] = w;
     sig0[q] = sqrt(s2);
     dlns[q] = (R / 6.0) * ds2 / s2;
+    if (bullock) sigF[q] = sqrt(s2F);
     for (int j = 0; j < nc; ++j) {
       m[q * nc + j] = mq;
       om[q * nc + j] = w * cw[j];
     }
   }
+}
+
+// Collapse epoch of the Bullock et al. median (Sec. 6), one warp per mass
+// node: a_c with D(a_c) sigma(F m, 0) = delta_c, D(1) = 1, D the growth ODE's
+// solution (dev_growth_raw).  Each round the 32 lanes evaluate D at 32
+// interior points of the bracket in ln a and keep the sub-interval where D
+// crosses the target, 33 times narrower, until the bracket stops shrinking
+// (about 11 rounds; at most 40).  a_c = WL_A_COLLAPSE_MAX where D stays below
+// the target up to there; the start of the growth rule where D starts above it.
+__global__ void k_collapse(const cov_cosmology* __restrict__ cosmo_p, const double* scal, const double* sigF,
+                           double* ac) {
+  const cov_cosmology c = *cosmo_p;
+  const int q = blockIdx.x, lane = threadIdx.x;
+  const double d1 = scal[SC_D1], target = WL_DELTA_C / sigF[q];
+  double out;
+  if (dev_growth_raw(WL_A_COLLAPSE_MAX, c) / d1 <= target) {
+    out = WL_A_COLLAPSE_MAX;
+  } else if (dev_growth_raw(WL_A_INIT, c) / d1 >= target) {
+    out = WL_A_INIT;
+  } else {
+    double lo = log(WL_A_INIT), hi = log(WL_A_COLLAPSE_MAX);
+    for (int it = 0; it < 40; ++it) {
+      double w = (hi - lo) / 33.0;
+      bool above = dev_growth_raw(exp(lo + (lane + 1) * w), c) / d1 >= target;
+      unsigned mask = __ballot_sync(0xffffffffu, above);
+      double nlo = lo + 32 * w, nhi = hi;
+      if (mask) {
+        int f = __ffs(mask) - 1;
+        nlo = f ? lo + f * w : lo;
+        nhi = lo + (f + 1) * w;
+      }
+      if (!(nlo > lo || nhi < hi) || !(nlo < nhi)) break;  // converged to the last bit
+      lo = nlo;
+      hi = nhi;
+    }
+    out = exp(0.5 * (lo + hi));
+  }
+  if (lane == 0) ac[q] = out;
 }
 
 __device__ __forceinline__ double st_amp() {
@@ -304,9 +351,10 @@ __global__ void k_halo(const cov_cosmology* __restrict__ cosmo_p, int nm, int nc
 }
 
 // NFW profiles on the Limber grid and P_lin, dP_lin/dln k at k = l_b/chi_n
-// at every (mass, concentration) node: u(k | m_q, c_bar(m_q, z_n) exp(cs[j]))
+// at every (mass, concentration) node: u(k | m_q, c_bar(m_q, z_n) exp(cs[j])),
+// c_bar the Duffy fit or the Bullock median max(K / ((1 + z) a_c(m_q)), 1)
 __global__ void k_profiles(const cov_cosmology* __restrict__ cosmo_p, cov_bins b, int nm, int nc, const double* cs,
-                           const double* ell, const double* chi, const double* z,
+                           const double* ac, const double* ell, const double* chi, const double* z,
                            const double* D, const double* m, const double* scal, double* U, double* Pl,
                            double* dPl, double* Psh) {
   const cov_cosmology c = *cosmo_p;
@@ -317,7 +365,8 @@ __global__ void k_profiles(const cov_cosmology* __restrict__ cosmo_p, cov_bins b
   bool valid = k <= b.k_max;
   double rho = WL_RHO_CRIT0 * c.Om;
   for (int q = threadIdx.x; q < nm; q += blockDim.x) {
-    double cq = dev_conc(m[q], z[n]);
+    double cq = b.conc_model == COV_CONC_BULLOCK ? fmax(WL_BULLOCK_K / ((1.0 + z[n]) * ac[q / nc]), WL_BULLOCK_C_MIN)
+                                                 : dev_conc(m[q], z[n]);
     if (nc > 1) cq *= exp(cs[q % nc]);
     U[(size_t)bn * nm + q] = valid ? dev_nfw_u(k, m[q], cq, rho) : 0.0;
   }
@@ -476,10 +525,11 @@ int wl_tables(cov_handle* h, cudaStream_t s) {
   k_growth_norm<<<(h->nchi + 127) / 128, 128, 0, s>>>(h->nchi, h->scal, h->D);
   k_amplitude<<<1, 256, 0, s>>>(c, h->glkx, h->glkw, h->scal);
   k_sigma<<<h->nmb, 256, 0, s>>>(c, b, h->glkx, h->glkw, h->scal, h->nc, h->cw, h->mb, h->omb, h->sig0, h->dlns,
-                                 h->m, h->om);
+                                 h->m, h->om, h->sigF);
+  if (b.conc_model == COV_CONC_BULLOCK) k_collapse<<<h->nmb, 32, 0, s>>>(c, h->scal, h->sigF, h->ac);
   k_halo<<<h->nchi, 128, 0, s>>>(c, h->nmb, h->nc, h->D, h->mb, h->omb, h->sig0, h->dlns, h->f, h->b1, h->b2);
-  k_profiles<<<h->nl * h->nchi, 128, 0, s>>>(c, b, h->nm, h->nc, h->cs, h->ell_d, h->chi, h->z, h->D, h->m, h->scal,
-                                             h->U, h->Pl, h->dPl, h->Psh);
+  k_profiles<<<h->nl * h->nchi, 128, 0, s>>>(c, b, h->nm, h->nc, h->cs, h->ac, h->ell_d, h->chi, h->z, h->D, h->m,
+                                             h->scal, h->U, h->Pl, h->dPl, h->Psh);
   k_edges<<<1, 64, 0, s>>>(nz, h->zedges, h->scal);
   k_norms<<<h->nt, 64, 0, s>>>(nz, h->zedges, h->gl64x, h->gl64w, h->norms);
   k_kernels<<<h->nchi, 64, 0, s>>>(c, nz, h->nchi, h->chi, h->z, h->zedges, h->norms, h->gl64x, h->gl64w, h->W);

@@ -41,6 +41,9 @@ COV_ROWS_B = 2
 COV_ORDER_NATURAL = 0
 COV_ORDER_CUMULATIVE = 1
 
+COV_CONC_DUFFY = 0
+COV_CONC_BULLOCK = 1
+
 EXPORTED = ["cov_init", "cov_update", "cov_layout", "cov_counts", "cov_spectra", "cov_assemble", "cov_snr",
             "cov_assemble_band", "cov_table", "cov_profile", "cov_stage_times", "cov_stage_name", "cov_snr_noalloc",
             "cov_last_error", "cov_free", "cov_snr_tiles", "cov_batch_snr", "cov_server_create", "cov_server_submit", "cov_server_wait",
@@ -69,7 +72,7 @@ class cov_nz(C.Structure):
 class cov_bins(C.Structure):
     _fields_ = [("n_ell", C.c_int), ("ell_min", C.c_double), ("ell_max", C.c_double), ("f_sky", C.c_double),
                 ("n_chi", C.c_int), ("n_mass", C.c_int), ("m_min", C.c_double), ("m_max", C.c_double),
-                ("k_max", C.c_double), ("n_conc", C.c_int), ("sigma_lnc", C.c_double)]
+                ("k_max", C.c_double), ("n_conc", C.c_int), ("sigma_lnc", C.c_double), ("conc_model", C.c_int)]
 
 
 class cov_opts(C.Structure):
@@ -180,5 +183,5 @@ def structs_from_workload(wl):
         "z0", "alpha", "zmin", "zmax", "photoz_sigma0", "n_gal_arcmin2", "sigma_e")))
     bs = cov_bins(int(b["n_ell"]), float(b["ell_min"]), float(b["ell_max"]), float(b["f_sky"]), int(b["n_chi"]),
                   int(b["n_mass"]), float(b["m_min"]), float(b["m_max"]), float(b["k_max"]),
-                  int(b.get("n_conc", 0)), float(b.get("sigma_lnc", 0.0)))
+                  int(b.get("n_conc", 0)), float(b.get("sigma_lnc", 0.0)), int(b.get("conc_model", 0)))
     return cs, ns, bs

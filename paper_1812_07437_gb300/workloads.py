@@ -83,6 +83,11 @@ def paper_workload(n_tomo, n_chi=128, n_mass=96, sigma_e=0.3, n_conc=0):
                 terms=TERMS_ALL)
 
 
+# the paper's set-up with 2 tomographic bins (M = 818) at reduced quadrature and
+# concentration scatter: a parity case that spans several tiles
+WORKLOADS["paper_2bin"] = paper_workload(2, n_chi=32, n_mass=24, n_conc=4)
+
+
 def get(name, **overrides):
     """A deep copy of a named workload, with top-level or nested overrides."""
     wl = copy.deepcopy(WORKLOADS[name])

@@ -57,6 +57,10 @@ def test_invalid_arguments_rejected_on_host(lib):
         bs3.n_conc, bs3.sigma_lnc, bs3.n_mass = n_conc, sig, n_mass
         assert lib.cov_init(C.byref(cs), C.byref(ns), C.byref(bs3), None, C.byref(h)) == N.COV_ERR_INVALID
         assert not h.value
+    for model in (-1, 2):  # median concentration: COV_CONC_DUFFY or COV_CONC_BULLOCK
+        bs4 = N.cov_bins(*[getattr(bs, f) for f, _ in N.cov_bins._fields_])
+        bs4.conc_model = model
+        assert lib.cov_init(C.byref(cs), C.byref(ns), C.byref(bs4), None, C.byref(h)) == N.COV_ERR_INVALID
     assert lib.cov_spectra(None, None, None) == N.COV_ERR_INVALID
     assert lib.cov_snr(None, None, 0, None, 0, None, None) == N.COV_ERR_INVALID
     assert lib.cov_assemble_band(None, 0, 256, None, 0, N.COV_LAYOUT_TILES, N.COV_TERMS_ALL, N.COV_SPLIT_BF16,

@@ -51,12 +51,37 @@ def test_bullock_median_monotone_and_normalised():
     wl = workloads.get("tiny_2bin", cosmology=dict(COSMO), bins=dict(conc_model=halo.CONC_BULLOCK, m_min=1e9))
     T = Tables(wl)
     c0 = T.cbar(0)
-    free = T.a_c < halo.A_COLLAPSE_MAX  # strictly falling below the cap, flat at it
-    assert np.all(np.diff(c0[free]) < 0) and np.all(np.diff(c0) <= 0)
-    for n in (3, 9):
-        np.testing.assert_allclose(T.cbar(n) * (1 + T.z[n]), c0 * (1 + T.z[0]), rtol=1e-15)
+    free = c0 > halo.BULLOCK_C_MIN  # strictly falling above the floor, flat on it
+    assert free.sum() >= 6 and np.all(np.diff(c0[free]) < 0) and np.all(np.diff(c0) <= 0)
+    assert c0.min() == halo.BULLOCK_C_MIN
+    for n in (3, 9):  # proportional to a(z) wherever the floor is not reached
+        cn = T.cbar(n)
+        up = cn > halo.BULLOCK_C_MIN
+        np.testing.assert_allclose(cn[up] * (1 + T.z[n]), c0[up] * (1 + T.z[0]), rtol=1e-15)
+        assert np.all(cn[~up] == halo.BULLOCK_C_MIN)
     ac = T.a_c[3]
     assert halo.bullock_concentration(ac, 1.0 / ac - 1.0) == pytest.approx(halo.BULLOCK_K, rel=1e-14)
     # F m is the collapsing mass at a_c: sigma(F m, a_c) = delta_c
     sigF, _ = cz.sigma_and_dlnsigma_dlnm(halo.BULLOCK_F * T.m[3], T.amp, T.cosmo)
     assert cz.growth(1.0 / ac - 1.0, T.cosmo)[0] * sigF[0] == pytest.approx(halo.DELTA_C, rel=1e-12)
+
+
+@pytest.mark.filterwarnings("ignore::scipy.integrate.IntegrationWarning")
+def test_nfw_closed_form_conditioning_at_small_concentration():
+    """The Si/Ci closed form of u(k|m, c) divides O(1) terms that cancel to
+    O(c^2) by ln(1+c) - c/(1+c) ~ c^2/2, so for c << 1 its rounding error is
+    absolute, ~eps/c^2: against adaptive quadrature of the defining integral
+    |du| <= 1e-12 |u| + 2e-15/c^2.  Hence the floor c >= 1 of the Bullock
+    median (where it holds, u is good to ~1e-15 absolute)."""
+    rho = cz.rho_mean(workloads.FIDUCIAL)
+    m = 1e16
+    rv = halo.r_vir(m, rho)
+    for c in (1.0, 0.3, 0.1, 0.04, 0.01):
+        for k in (0.05, 1.0, 10.0):
+            rs = rv / c
+            prof = lambda r: 1.0 / ((r / rs) * (1 + r / rs) ** 2)
+            norm = integrate.quad(lambda r: 4 * math.pi * r * r * prof(r), 0, rv, epsrel=1e-13)[0]
+            ft = integrate.quad(lambda r: 4 * math.pi * r * r * prof(r) * math.sin(k * r) / (k * r), 0, rv,
+                                limit=4000, epsrel=1e-13, epsabs=0)[0]
+            u = ft / norm
+            assert abs(float(halo.nfw_u(k, m, 0.0, rho, c)) - u) <= 1e-12 * abs(u) + 2e-15 / (c * c), (c, k)
