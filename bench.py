@@ -71,6 +71,29 @@ def parse():
     return p.parse_args()
 
 
+def rank_cosmology(fiducial, rank):
+    """The cosmology one rank computes: rank 0 the fiducial, ranks 1-6 a +1% step
+    of one parameter each, ranks 7-12 the -1% steps, then +-2%, and so on: every
+    rank a different problem.  Ranks solve independent problems, so the data
+    path has no collective (weak scaling)."""
+    cosmo = dict(fiducial)
+    if rank > 0:
+        keys = ["Om", "sigma8", "h", "ns", "Ob", "w0"]
+        i = rank - 1
+        sign = 1.0 if (i // len(keys)) % 2 == 0 else -1.0
+        cosmo[keys[i % len(keys)]] *= 1.0 + sign * 0.01 * (1 + i // (2 * len(keys)))
+    return cosmo
+
+
+def job_step_ms(ms, world, device):
+    """The job's step time: the largest of the ranks' (all-reduce MAX when world > 1)."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -492,13 +515,12 @@ def paper_run(device):
     them by.  The covariances are assembled in the FP64 form: without photo-z scatter the
     tomographic kernels overlap strongly and the scaled covariance's smallest eigenvalue
     falls to ~1e-3 at 2 bins and below at 5, where the split form's ~1e-5 element error
-    can move it below zero.  The 10-bin case holds the power-spectrum rows alone (in the
-    cumulative row order, its S/N taken in place on packed tiles)."""
+    can move it below zero.  The 10-bin case holds the power-spectrum rows alone."""
     import numpy as np
     import torch
     from paper_1812_07437_gb300 import native as N
     from paper_1812_07437_gb300 import workloads
-    from paper_1812_07437_gb300.handle import Handle, packed_tiles
+    from paper_1812_07437_gb300.handle import Handle
     dev = torch.device("cuda", device)
     ins = N.COV_TERM_1H | N.COV_TERM_BBPT | N.COV_TERM_PB
     sets = {"G": N.COV_TERM_G, "G+NGins": N.COV_TERM_G | ins, "G+NGssc": N.COV_TERM_G | N.COV_TERM_SSC,
@@ -515,25 +537,18 @@ def paper_run(device):
         key = f"{nt}bin" + ("" if sigma_e > 0 else "_no_noise")
         wl = workloads.paper_workload(nt, sigma_e=sigma_e)
         joint = which == "PBJ"
-        # the power-spectrum rows alone: a cumulative-order handle, its S/N in place on packed tiles
-        h = Handle(wl, device=device) if joint else Handle(wl, device=device, rows=N.COV_ROWS_P,
-                                                           order=N.COV_ORDER_CUMULATIVE)
+        # 10 bins: a handle of the power-spectrum rows alone
+        h = Handle(wl, device=device, rows=N.COV_ROWS_JOINT if joint else N.COV_ROWS_P)
         res = {"M": h.M, "n_P": h.n_P, "n_B": h.n_B}
+        ws = (("P", N.COV_WHICH_P), ("B", N.COV_WHICH_B), ("joint", N.COV_WHICH_JOINT)) if joint else \
+            (("P", N.COV_WHICH_P),)
         try:
             D = torch.zeros(h.M, dtype=torch.float64, device=dev)
+            C = torch.zeros(h.M, h.M, dtype=torch.float64, device=dev)
             h.spectra(D)
-            if joint:
-                C = torch.zeros(h.M, h.M, dtype=torch.float64, device=dev)
-            else:
-                C = torch.full((packed_tiles(h.M + 1) * 65536,), float("nan"), dtype=torch.float64, device=dev)
             for name, terms in sets.items():
-                if joint:
-                    h.assemble(C, terms, N.COV_FP64)
-                    res[name] = {w: last(h.snr(C, D, wi)) for w, wi in
-                                 (("P", N.COV_WHICH_P), ("B", N.COV_WHICH_B), ("joint", N.COV_WHICH_JOINT))}
-                else:
-                    h.assemble_band(0, h.M, C, N.COV_LAYOUT_TILES, terms, N.COV_FP64)
-                    res[name] = {"P": last(h.snr_tiles(C, D))}
+                h.assemble(C, terms, N.COV_FP64)
+                res[name] = {w: last(h.snr(C, D, wi)) for w, wi in ws}
             del C, D
         except Exception as e:  # noqa: BLE001  (one case's failure is recorded; the others still run)
             res["error"] = f"{type(e).__name__}: {e}"
@@ -627,12 +642,7 @@ def run_ours(args):
     prec = N.COV_SPLIT_BF16 if prec_name == "split_bf16" else N.COV_FP64
 
     def rank_cosmo(wl):
-        cosmo = dict(wl["cosmology"])
-        if rank > 0:  # Fisher-style +-1% steps, one cosmology per rank
-            keys = ["Om", "sigma8", "h", "ns", "Ob", "w0"]
-            k = keys[(rank - 1) % len(keys)]
-            cosmo[k] *= 1.0 + 0.01 * (1 if rank % 2 else -1)
-        return cosmo
+        return rank_cosmology(wl["cosmology"], rank)
 
     wl = workloads.get(args.workload)
     cosmo = rank_cosmo(wl)
@@ -770,10 +780,7 @@ def run_ours(args):
         snr_sizes = [h.n_P, h.n_B, M]
         cfg = {"layout": "dense M x M"}
 
-    t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_step = float(t.item())
+    ms_step = job_step_ms(ms_step, world, dev)
     value = world * elements / (ms_step / 1e3)
     roof = contraction_roofline(stages, elements, Kc, prec, N, long_kernel=packed)
     if prec != N.COV_FP64:
