@@ -106,3 +106,30 @@ def test_bad_options_rejected(Server):
         Server(n_slots=2, hbm_budget=0, dry_run_us=10)  # a dry run needs an explicit budget
     with pytest.raises(N.CovError):
         Server(n_slots=2, hbm_budget=1 << 30, precision=7, dry_run_us=10)
+
+
+def test_concentration_model_is_part_of_the_resident_key(Server):
+    """A request differing only in its concentration rule (scatter nodes, width,
+    median) does not run on another's resident state; a one-node rule is model B
+    and does; the scatter's wider factor rows raise the footprint."""
+    base = workloads.get("tiny_2bin")
+    scat = workloads.get("tiny_2bin", bins=dict(n_conc=4, sigma_lnc=workloads.SIGMA_LNC))
+    probe = Server(n_slots=1, hbm_budget=1 << 40, dry_run_us=1000)
+    assert probe.footprint(scat)[1] > probe.footprint(base)[1]
+    probe.close()
+    s = Server(n_slots=1, hbm_budget=1 << 36, dry_run_us=2000)
+    c2 = dict(workloads.FIDUCIAL, Om=0.32)
+    wls = [base,
+           scat,
+           workloads.get("tiny_2bin", bins=dict(n_conc=4, sigma_lnc=0.25)),
+           workloads.get("tiny_2bin", bins=dict(conc_model=N.COV_CONC_BULLOCK)),
+           workloads.get("tiny_2bin", cosmology=c2),                                          # base again
+           workloads.get("tiny_2bin", cosmology=c2, bins=dict(n_conc=1, sigma_lnc=0.18)),     # model B again
+           workloads.get("tiny_2bin", cosmology=c2, bins=dict(n_conc=4, sigma_lnc=workloads.SIGMA_LNC))]
+    reused = []
+    for wl in wls:  # one slot, one request at a time
+        info = s.wait(s.submit(wl), timeout=60.0)[0]
+        assert info["state"] == N.COV_REQ_DONE, info
+        reused.append(info["reused"])
+    s.close()
+    assert reused == [0, 0, 0, 0, 1, 1, 1]
