@@ -46,7 +46,11 @@ extern "C" {
 #define COV_TERM_SSC 16u /* super-sample term (Eq. WLSSCflatskyLimber)        */
 #define COV_TERMS_ALL 31u
 
-/* arithmetic of the (chi, M) contractions */
+/* arithmetic of the (chi, M) contractions.  The split form's elements carry
+ * an error of ~1e-5 sqrt(C_aa C_bb); a covariance whose unit-diagonal scaling
+ * has eigenvalues near that (strongly overlapping tomographic kernels, e.g. no
+ * photo-z scatter and several bins) can then lose positive definiteness and
+ * the S/N returns COV_ERR_NOT_PD: assemble such covariances in COV_FP64. */
 #define COV_FP64 0       /* plain FP64 on CUDA cores                          */
 #define COV_SPLIT_BF16 1 /* tcgen05 tensor cores, A = hi + lo in BF16, FP32 acc */
 
