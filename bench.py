@@ -458,7 +458,7 @@ def model_a_run(prec, device, name, n_conc):
     the median concentration (model B) on one workload: the whole dense step of
     each (tables, spectra, every covariance term, the three cumulative S/N),
     the contraction's roofline at n_conc times the halo-integral nodes, and the
-    relative changes between the two models that Sec. 6 of the paper reports
+    relative changes between the two models that Sec. 5.4 of the paper reports
     (data vector, covariance, S/N)."""
     import numpy as np
     import torch

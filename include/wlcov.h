@@ -73,7 +73,7 @@ typedef struct {
   double z0, alpha, zmin, zmax, photoz_sigma0, n_gal_arcmin2, sigma_e;
 } cov_nz;
 
-/* Median concentration c(m, z) of the NFW profiles (Sec. 4.1, Sec. 6). */
+/* Median concentration c(m, z) of the NFW profiles (Sec. 4.1, Sec. 5.4). */
 #define COV_CONC_DUFFY 0   /* Duffy et al. (2008), 200 x mean density: 10.14 (m/2e12)^-0.081 (1+z)^-1.01 */
 #define COV_CONC_BULLOCK 1 /* Bullock et al. (2001), the paper's choice: K a(z)/a_c with nu(F m, a_c) = 1, */
                            /* F = 0.01, K = 4 (a_c capped at a = 100 where F m never collapses), floored  */
@@ -81,10 +81,10 @@ typedef struct {
 
 /* n_ell log-spaced ell bins on [ell_min, ell_max] (Sec. 3.2.1, App. A), sky
  * fraction f_sky, n_chi Gauss-Legendre line-of-sight nodes, n_mass log mass
- * nodes on [m_min, m_max] Msun/h, 3D cut k_max h/Mpc (Sec. 4.4), median
+ * nodes on [m_min, m_max] Msun/h, 3D cut k_max h/Mpc (Sec. 4.5), median
  * concentration conc_model (COV_CONC_*; zero-initialised: Duffy).
  *
- * Concentration scatter (Eq. LogNormC; the paper's "model A" of Sec. 6):
+ * Concentration scatter (Eq. LogNormC; the paper's "model A" of Sec. 5.4):
  * with n_conc >= 2 every halo integral of Eq. ImunuHalos also averages the
  * NFW profiles over a lognormal concentration of width sigma_lnc (0.18 in the
  * paper) about the median c(m, z), on an n_conc-point Gauss-Hermite rule in

@@ -28,7 +28,7 @@ layout      data-vector ordering of P and B entries
 spectra     halo-model 3D polyspectra, responses, Limber projection
 covariance  Gaussian, 1-halo, BB+PT, PB and super-sample terms
 snr         cumulative signal-to-noise
-pca         principal components of the joint covariance (Sec. 7): one-sided
+pca         principal components of the joint covariance (Sec. 6): one-sided
             Jacobi eigen-pairs, S/N per mode and cumulative
 pipeline    one call that runs the whole path for a workload dictionary
 """

@@ -1,7 +1,7 @@
 """Halo model ingredients (oracle, FP64): Sec. 4 of the paper.
 
 * Sheth-Tormen mass function f_m(m) = dn/dm with nu = (delta_c/sigma)^2
-  (Sec. 4.4, Eq. BoundinMass context).  Parameters q = 0.707, p = 0.3,
+  (Sec. 4.5, Eq. BoundinMass context).  Parameters q = 0.707, p = 0.3,
   A from the normalisation int f(nu) dnu = 1; delta_c = 1.686.
 * Peak-background-split biases b1, b2 (Sec. 4.2.1, Eq. TidalKernel context):
   Lagrangian b_n^L = (1/G) d^n G/d delta_b^n with delta_c -> delta_c - delta_b
@@ -12,7 +12,7 @@
   that the discrete consistency relations (Eq. BoundinMass) hold exactly.
 * Concentration: Duffy et al. (2008) mean-density fit c = 10.14
   (m / 2e12)^-0.081 (1+z)^-1.01 with r_200m = (3m/(4 pi 200 rho_com))^(1/3);
-  or the Bullock et al. (2001) median the paper uses (Sec. 6):
+  or the Bullock et al. (2001) median the paper uses (Sec. 5.4):
   c_bar = K a(z) / a_c with nu(F m, a_c) = 1, i.e. the collapse epoch a_c at
   which D(a_c) sigma(F m, z=0) = delta_c (D(1) = 1), F = 0.01, K = 4.0.  a_c
   is the root of the growth ODE's solution on [1e-3, 100]; where F m has not

@@ -1,4 +1,4 @@
-"""Principal components of the joint covariance (oracle, FP64): Sec. 7.
+"""Principal components of the joint covariance (oracle, FP64): Sec. 6.
 
 Test infrastructure, like the rest of the oracle package (see its header).
 

@@ -21,7 +21,7 @@ Paper sections followed:
     sigma_W^2(chi) = 4 int d^2eps/(2 pi)^2 [J1(eps chi Theta)/(eps chi Theta)]^2
     P_lin(eps, z(chi)) with a 4096-node Gauss-Legendre rule in ln eps on
     [ln 1e-5, ln 1e3].
-  * k_max = 50 h/Mpc (Sec. 4.4): a 3D polyspectrum or response at a
+  * k_max = 50 h/Mpc (Sec. 4.5): a 3D polyspectrum or response at a
     line-of-sight node is set to zero when any of its legs has l/chi > k_max.
 
 Line-of-sight rule: N_chi Gauss-Legendre nodes on [0, chi(z_max)].
@@ -61,7 +61,7 @@ class Tables:
         self.m, self.om = halo.mass_nodes(bins["n_mass"], bins["m_min"], bins["m_max"])
         self.mr = self.m / self.rho
         sig0, dlns = cz.sigma_and_dlnsigma_dlnm(self.m, self.amp, cosmo)
-        # median concentration rule (Duffy fit, or the Bullock et al. median of Sec. 6)
+        # median concentration rule (Duffy fit, or the Bullock et al. median of Sec. 5.4)
         self.conc_model = int(bins.get("conc_model", halo.CONC_DUFFY))
         if self.conc_model == halo.CONC_BULLOCK:
             sigF, _ = cz.sigma_and_dlnsigma_dlnm(halo.BULLOCK_F * self.m, self.amp, cosmo)

@@ -254,7 +254,7 @@ __global__ void k_sigma(const cov_cosmology* __restrict__ cosmo_p, cov_bins b, c
   }
 }
 
-// Collapse epoch of the Bullock et al. median (Sec. 6), one warp per mass
+// Collapse epoch of the Bullock et al. median (Sec. 5.4), one warp per mass
 // node: a_c with D(a_c) sigma(F m, 0) = delta_c, D(1) = 1, D the growth ODE's
 // solution (dev_growth_raw).  Each round the 32 lanes evaluate D at 32
 // interior points of the bracket in ln a and keep the sub-interval where D

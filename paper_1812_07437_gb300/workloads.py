@@ -32,7 +32,7 @@ TERM_SSC = 16
 TERMS_ALL = 31
 
 FIDUCIAL = dict(Om=0.31, Ob=0.049, h=0.68, ns=0.96, sigma8=0.83, w0=-1.0, Tcmb=2.7255)
-# width of the lognormal concentration scatter of "model A" (Sec. 4.2.1)
+# width of the lognormal concentration scatter of "model A" (Eq. LogNormC, Sec. 4.2.2; Sec. 5.4)
 SIGMA_LNC = 0.18
 
 
@@ -64,7 +64,7 @@ WORKLOADS = {
 }
 
 
-# The paper's own set-up (Sec. 1, Appendix A and Sec. 6): its cosmology, 14
+# The paper's own set-up (Sec. 1, Appendix A and Sec. 5.4): its cosmology, 14
 # log-spaced ell bins on [10, 5000], n(z) with z0 = 0.9/sqrt(2) normalised on
 # [0.001, 2.5], 30 sources per arcmin^2, sigma_e = 0.3, f_sky = 0.36, no
 # photometric-redshift scatter, halo masses from 1e9 to 1e16 Msun/h and the

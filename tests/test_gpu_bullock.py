@@ -1,4 +1,4 @@
-"""GPU parity of the Bullock et al. median concentration (Sec. 6) and of the
+"""GPU parity of the Bullock et al. median concentration (Sec. 5.4) and of the
 paper's own set-up against the FP64 oracle, through the C ABI.
 
 * tiny_2bin with the Bullock median (model B): tables, spectra, every

@@ -1,4 +1,4 @@
-"""Pins of the oracle's Bullock et al. median concentration (Sec. 6):
+"""Pins of the oracle's Bullock et al. median concentration (Sec. 5.4):
 c_bar = K a(z) / a_c with nu(F m, a_c) = 1, i.e. D(a_c) sigma(F m, 0) = delta_c.
 
 The collapse epoch is a root of the growth ODE's solution; these checks fix it

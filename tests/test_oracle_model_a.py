@@ -125,7 +125,7 @@ def test_block_form_equals_element_form_with_scatter(model_a):
 
 def test_scatter_changes_one_halo_more_than_spectra(model_a):
     """The scatter moves the 1-halo covariance by more than the data vector
-    (the paper's Sec. 6 finding: percent-level on P and B, tens of percent on
+    (the paper's Sec. 5.4 finding: percent-level on P and B, tens of percent on
     the bispectrum covariance); both move."""
     base = OracleRun(workloads.get("tiny_2bin"))
     dD = np.max(np.abs(model_a.D / base.D - 1.0))

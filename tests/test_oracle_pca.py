@@ -1,4 +1,4 @@
-"""Pins of the oracle's principal-component analysis (Sec. 7, Eqs. SNPCA,
+"""Pins of the oracle's principal-component analysis (Sec. 6, Eqs. SNPCA,
 NewObs, SNperEign, CumulSN).
 
 * The one-sided Jacobi eigen-pairs agree with LAPACK's QR-based solver on
