@@ -86,6 +86,8 @@ def paper_workload(n_tomo, n_chi=128, n_mass=96, sigma_e=0.3, n_conc=0):
 # the paper's set-up with 2 tomographic bins (M = 818) at reduced quadrature and
 # concentration scatter: a parity case that spans several tiles
 WORKLOADS["paper_2bin"] = paper_workload(2, n_chi=32, n_mass=24, n_conc=4)
+# the same set-up at the paper-replica quadrature (N_chi = 128, N_M = 96), no scatter
+WORKLOADS["paper_2bin_full"] = paper_workload(2)
 
 
 def get(name, **overrides):

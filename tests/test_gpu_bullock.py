@@ -8,6 +8,8 @@ paper's own set-up against the FP64 oracle, through the C ABI.
   (four 256-row tiles, ragged tail): the same bar in FP64, 1e-4 per element
   and 1e-3 on the S/N in the split-BF16 form.  Its exact triangle counts come
   from the oracle's stored file (tests/golden/make_counts.py).
+* paper_2bin_full: the same set-up at the paper-replica quadrature, its
+  cumulative S/N against the oracle's stored curve (tests/golden/make_snr.py).
 """
 import os
 import sys
@@ -122,3 +124,21 @@ def test_snr_matches_oracle_both_precisions(name):
             m = np.isfinite(ref)
             assert np.array_equal(m, np.isfinite(got))
             assert np.max(np.abs(got[m] / ref[m] - 1)) <= stol, (precision, which)
+
+
+def test_paper_set_up_at_full_quadrature_matches_stored_oracle_snr():
+    """The paper's 2-bin set-up at the quadrature of the paper-replica runs
+    (N_chi = 128, N_M = 96, Bullock median, M = 818): cumulative S/N of P, B and
+    the joint vector in the FP64 form against the oracle's stored curve
+    (tests/golden/make_snr.py) to 1e-10."""
+    import make_snr
+    from paper_1812_07437_gb300.handle import Handle
+    h = Handle(workloads.get("paper_2bin_full"))
+    ref = make_snr.load("paper_2bin_full")
+    C, D = _cov(h, N.COV_TERMS_ALL, N.COV_FP64)
+    Ct = torch.tensor(C, device="cuda:0")
+    for tag, w in (("P", N.COV_WHICH_P), ("B", N.COV_WHICH_B), ("J", N.COV_WHICH_JOINT)):
+        got, r = h.snr(Ct, D, w), ref[tag]
+        m = np.isfinite(r)
+        assert np.array_equal(m, np.isfinite(got)) and np.max(np.abs(got[m] / r[m] - 1)) <= TOL, tag
+    h.close()
