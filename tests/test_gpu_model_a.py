@@ -125,3 +125,29 @@ def test_one_concentration_node_is_model_b_bitwise():
         assert np.array_equal(Cb, C1) and torch.equal(Db, D1)
     hb.close()
     h1.close()
+
+
+def test_largest_rule_and_zero_width():
+    """The largest concentration rule the API takes (32 nodes): the rule and the
+    data vector against the oracle; a zero-width lognormal (sigma_lnc = 0, all
+    nodes at the median) reproduces model B to rounding."""
+    from paper_1812_07437_gb300.handle import Handle
+    wl = workloads.get("tiny_2bin", bins=dict(n_conc=32, sigma_lnc=workloads.SIGMA_LNC))
+    h, r = Handle(wl), OracleRun(wl)
+    s, w = halo.conc_rule(32, workloads.SIGMA_LNC)
+    close(h.table("conc_offsets"), s, 1e-13, 1e-15)
+    close(h.table("conc_weights"), w, 1e-12, 1e-15)
+    D = torch.zeros(h.M, dtype=torch.float64, device="cuda:0")
+    h.spectra(D)
+    torch.cuda.synchronize()
+    close(D.cpu().numpy(), r.D)
+    h.close()
+    hb = Handle(workloads.get("tiny_2bin"))
+    h0 = Handle(workloads.get("tiny_2bin", bins=dict(n_conc=8, sigma_lnc=0.0)))
+    Cb, Db = _cov(hb, TERMS_ALL)
+    C0, D0 = _cov(h0, TERMS_ALL)
+    d = np.sqrt(np.diag(Cb))
+    assert np.max(np.abs(C0 - Cb) / np.outer(d, d)) <= 1e-13
+    assert torch.max(torch.abs(D0 / Db - 1)).item() <= 1e-13
+    hb.close()
+    h0.close()
