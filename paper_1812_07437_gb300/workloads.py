@@ -88,6 +88,8 @@ def paper_workload(n_tomo, n_chi=128, n_mass=96, sigma_e=0.3, n_conc=0):
 WORKLOADS["paper_2bin"] = paper_workload(2, n_chi=32, n_mass=24, n_conc=4)
 # the same set-up at the paper-replica quadrature (N_chi = 128, N_M = 96), no scatter
 WORKLOADS["paper_2bin_full"] = paper_workload(2)
+# the 5-bin set-up on which the paper compares the concentration models (Sec. 5.4)
+WORKLOADS["paper_5bin"] = paper_workload(5)
 
 
 def get(name, **overrides):
