@@ -117,7 +117,12 @@ typedef struct {
   int rows;          /* COV_ROWS_*                                           */
   int order;         /* COV_ORDER_*: the cumulative order makes every        */
                      /* cumulative S/N selection a leading block (cov_snr_tiles) */
+  int tc_kernel;     /* split-form contraction kernel: COV_TC_AUTO (CTA pairs */
+                     /* where 2-CTA clusters fit) or COV_TC_SINGLE (one CTA   */
+                     /* per 256 x 256 tile); both give the same sums          */
 } cov_opts;
+#define COV_TC_AUTO 0
+#define COV_TC_SINGLE 1
 
 typedef struct cov_handle cov_handle;
 
@@ -265,7 +270,7 @@ int cov_snr_noalloc(const double* d_C, int64_t ldc, const double* d_D, int64_t M
  * `terms` in `precision`: the Fisher pattern (finite-difference steps around a
  * fiducial cosmology) and emulator training sets.  The first cosmology runs
  * eagerly and prepares everything; with COV_BATCH_TUNE it first runs once per
- * candidate launch configuration (tensor-core contraction in 2 x 2 clusters or
+ * candidate launch configuration (tensor-core contraction in CTA pairs or
  * one CTA per tile; Cholesky with or without panel look-ahead), keeps the
  * fastest for this handle and reports the candidate times in *info.  The
  * cosmology-dependent step (tables, spectra, dense covariance, three S/N) is
@@ -279,9 +284,9 @@ int cov_snr_noalloc(const double* d_C, int64_t ldc, const double* d_D, int64_t M
 #define COV_BATCH_TUNE 1u
 
 typedef struct {
-  int tc_kernel;          /* contraction kernel used: 1 = 2 x 2 clusters, 0 = one CTA per tile, -1 = automatic */
+  int tc_kernel;          /* contraction kernel used: 1 = CTA pairs, 0 = one CTA per tile, -1 = automatic       */
   int chol_lookahead;     /* 1: Cholesky panel look-ahead on a side stream                                    */
-  double candidate_ms[4]; /* tuning: (clusters, look-ahead), (clusters, none), (one CTA, look-ahead), (one CTA, none) */
+  double candidate_ms[4]; /* tuning: (pairs, look-ahead), (pairs, none), (one CTA, look-ahead), (one CTA, none) */
   double first_ms;        /* the first cosmology, tuning included                                             */
   double capture_ms;      /* capture and instantiation of the step                                            */
   double replay_ms;       /* per further cosmology (host clock, copies included)                              */

@@ -337,6 +337,7 @@ extern "C" int cov_init(const cov_cosmology* cosmo, const cov_nz* nz, const cov_
   h->budget = opts ? opts->hbm_budget : 0;
   h->row_set = opts ? opts->rows : COV_ROWS_JOINT;
   h->row_order = opts ? opts->order : COV_ORDER_NATURAL;
+  h->tc_kernel = (opts && opts->tc_kernel == COV_TC_SINGLE) ? 0 : -1;
   if (h->row_set < 0 || h->row_set > 2 || h->row_order < 0 || h->row_order > 1) {
     g_init_err = "invalid row set or row order";
     delete h;

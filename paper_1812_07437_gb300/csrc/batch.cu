@@ -4,7 +4,7 @@
 //
 // The first cosmology runs eagerly: it allocates every workspace, builds the
 // S/N selections and launch orders and, when asked, times the candidate
-// launch configurations (tensor-core contraction in 2 x 2 clusters or one CTA
+// launch configurations (tensor-core contraction in CTA pairs or one CTA
 // per tile; Cholesky with or without panel look-ahead) and keeps the fastest.
 // The step that depends on the cosmology (tables, spectra, the dense
 // covariance, the three S/N factorisations) is then captured once into a CUDA

@@ -173,7 +173,7 @@ struct cov_handle {
   cov_cosmology* cosmo_d = nullptr;  // the cosmology the kernels read (device copy of cosmo)
   bool deferred = false;  // inside a captured batch step: no host synchronisation, no host-side copies
   bool chol_lookahead = true;  // Cholesky panel look-ahead on the side stream
-  int tc_kernel = -1;          // contraction kernel: -1 automatic, 0 one CTA per tile, 1 2 x 2 clusters
+  int tc_kernel = -1;          // contraction kernel: -1 automatic, 0 one CTA per tile, 1 CTA pairs
   struct Selection {           // cumulative S/N selections (P, B, joint; all rows in place)
     bool ready = false;
     int64_t Ms = 0;

@@ -286,11 +286,16 @@ __device__ __forceinline__ uint32_t mbar_try(uint64_t* bar, uint32_t parity) {
   return ok;
 }
 
-// bounded wait; false when the limit expired or another role raised the status
+// bounded wait; false when the limit expired, another role of this CTA gave
+// up, or any CTA of the launch raised the status word (so that one expired
+// wait ends the whole launch quickly)
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
   for (uint32_t i = 0; i < TC_SPIN_LIMIT; ++i) {
     if (mbar_try(bar, parity)) return true;
-    if ((i & 1023u) == 1023u && *abort_flag) return false;
+    if ((i & 1023u) == 1023u && (*abort_flag || *(volatile int*)status)) {
+      *abort_flag = 1;
+      return false;
+    }
   }
   *abort_flag = 1;
   atomicExch(status, 1);
@@ -554,21 +559,24 @@ __global__ void __launch_bounds__(128, 1)
   }
 }
 
-// ---------------------------------------------------------------- 2 x 2 clusters
-// Four CTAs of a cluster compute the 2 x 2 tiles (I0 + r, J0 + c), r, c in
-// {0, 1}, of a 512 x 512 super-tile.  Row panel I0 + r is needed by CTAs
-// (r, 0) and (r, 1), column panel J0 + c by (0, c) and (1, c); each CTA loads
-// one 128-row half of its row panel and one half of its column panel and
-// multicasts each half to the two CTAs that use it, so every CTA receives the
-// same 64 KB per K block while reading only 32 KB from L2 (the contraction is
-// bound by L2 bandwidth, not by HBM or the tensor pipe).  A CTA's stage s is
-// written by itself, its row peer and its column peer, so its MMA completion
-// is multicast to the empty barriers of those three, and each empty barrier
-// counts three arrivals.  Tiles above the diagonal or past the band are
-// computed (their halves feed the neighbours) but not stored.
-#define MC_BOX_ROWS 128
-#define MC_GROUP 4  // super-rows per launch-order group
-#define MC_HALF_BYTES (MC_BOX_ROWS * TW_BK * 2)  // 8 KB
+// ---------------------------------------------------------------- CTA pairs
+// Two CTAs of a 2-CTA cluster compute one 256 x 512 pair tile, the 256 x 256
+// lower tiles (I, J) and (I, J + 1), with tcgen05.mma.cta_group::2: M = 256
+// rows split over the pair (128 per CTA), N = 256 columns per MMA, of which
+// each CTA holds 128 in its own shared memory.  CTA p (p = 0, 1) loads rows
+// 128 p .. 128 p + 127 of the row panel I and of the column panels J and
+// J + 1 (hi and lo: 48 KB per K block), so a pair reads 96 KB from L2 per K
+// block for two tiles where two one-CTA tiles read 128 KB.  CTA p accumulates
+// rows 128 p .. 128 p + 127 of both tiles in its TMEM (128 x 512 FP32).  The
+// even CTA waits for the copies of both CTAs (they complete on its full
+// barrier), issues the MMAs and commits to the empty and accumulator barriers
+// of both CTAs.  Pair tiles whose second tile lies above the diagonal load and
+// multiply the first tile only.
+#define PR_STAGES 4
+#define PR_HALF (128 * TW_BK * 2)         // 8 KB: 128 rows x 32 BF16
+#define PR_STAGE_BYTES (6 * PR_HALF)      // A hi/lo, B0 hi/lo, B1 hi/lo
+#define PR_SMEM (PR_STAGES * PR_STAGE_BYTES + 1024)
+#define PR_GROUP 8  // tile rows per launch-order group
 
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
@@ -578,147 +586,228 @@ __device__ __forceinline__ uint32_t cluster_rank() {
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
-__device__ __forceinline__ void tma_load_2d_mc(const CUtensorMap* map, uint64_t* bar, void* dst, int c0, int c1,
-                                               uint16_t mask) {
+// address of the same shared variable in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+// TMA load into this CTA's shared memory, completing on a barrier of either
+// CTA of the pair
+__device__ __forceinline__ void tma_load_2d_pair(const CUtensorMap* map, uint32_t bar, void* dst, int c0, int c1) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, "
-      "{%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
-      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "h"(mask)
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1)
       : "memory");
 }
-__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
+__device__ __forceinline__ void umma_bf16_pair(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                               uint32_t acc) {
   asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"(mask)
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          dtmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
       : "memory");
+}
+// arrive on one barrier (of either CTA) when the pair MMAs issued so far complete
+__device__ __forceinline__ void umma_commit_pair(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-__global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128, 1)
-    k_syrk_tc256_mc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
-                    int64_t M, int nk, const double* __restrict__ rscale, OutMap out, int* status,
-                    const int2* __restrict__ supers, int64_t t1) {
+// kind::f16, BF16 x BF16 -> FP32, K-major, M = 256 (a CTA pair), N = 256
+__device__ __forceinline__ uint32_t idesc_bf16_256x256() {
+  uint32_t d = 0;
+  d |= 1u << 4;
+  d |= 1u << 7;
+  d |= 1u << 10;
+  d |= (uint32_t)(256 >> 3) << 17;
+  d |= (uint32_t)(256 >> 4) << 24;
+  return d;
+}
+
+// Epilogue of this CTA's 128 rows of a pair tile: C = s_i s_j acc for rows
+// r_base .. r_base + 127 and the nh column halves of 256 from col0, staged
+// through shared memory (transpose) as in tile_epilogue.
+__device__ __forceinline__ void pair_epilogue(uint8_t* smem, uint32_t tmem, int warp, int lane, int64_t r_base,
+                                              int64_t col0, int nh, int64_t M, const double* __restrict__ rscale,
+                                              const OutMap& out) {
+  uint32_t* stg = (uint32_t*)smem + warp * (32 * 33 + 32);
+  int* erow = (int*)(stg + 32 * 33);
+  const int64_t r0 = r_base + warp * 32;
+  const int64_t gi = r0 + lane;
+  erow[lane] = (gi < M) ? pow2_exp(rscale[gi]) : 0;
+#pragma unroll 1
+  for (int h = 0; h < nh; ++h) {
+#pragma unroll 1
+    for (int c = 0; c < 8; ++c) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(256 * h + c * 32), v);
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) stg[lane * 33 + jj] = __float_as_uint(v[jj]);
+      __syncwarp();
+      const int64_t gj = col0 + 256 * h + c * 32 + lane;
+      const int ej = (gj < M) ? pow2_exp(rscale[gj]) : 0;
+#pragma unroll 4
+      for (int rr = 0; rr < 32; ++rr) {
+        const int64_t gr = r0 + rr;
+        if (gr < M && gj < M && gj <= gr) *out.at(gr, gj) = f32_scaled(stg[rr * 33 + lane], erow[rr] + ej);
+      }
+      __syncwarp();
+    }
+  }
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(128, 1)
+    k_syrk_pair(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, int64_t M,
+                int nk, const double* __restrict__ rscale, OutMap out, int* status, const int2* __restrict__ pairs) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar[TW_STAGES];
-  __shared__ __align__(8) uint64_t empty_bar[TW_STAGES];
+  __shared__ __align__(8) uint64_t full_bar[PR_STAGES];   // used in the even CTA
+  __shared__ __align__(8) uint64_t empty_bar[PR_STAGES];
   __shared__ __align__(8) uint64_t acc_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_flag;
+  __shared__ volatile int issued_sh[2];  // even CTA: K blocks issued by itself [0] and by the odd CTA [1]
 
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t rank = cluster_rank();
-  const int rr = (int)(rank >> 1), cc = (int)(rank & 1);
-  const int2 sup = supers[blockIdx.x >> 2];
-  const int64_t ti = (int64_t)sup.x + rr, tj = (int64_t)sup.y + cc;
+  const uint32_t p = cluster_rank() & 1u;  // 0: the CTA that issues the MMAs
+  const int2 pt = pairs[blockIdx.x >> 1];
+  const int64_t ti = pt.x, tj = pt.y;
+  const bool two = tj + 1 <= ti;  // the second tile (ti, tj + 1) is a lower tile
   const int row_i = (int)(ti * TW_BM), row_j = (int)(tj * TW_BM);
-  const bool store = ti < t1 && tj <= ti;
-  // CTAs (rr, 0), (rr, 1) share the row panel; (0, cc), (1, cc) the column panel
-  const uint16_t row_mask = (uint16_t)(3u << (2 * rr));
-  const uint16_t col_mask = (uint16_t)((1u << cc) | (1u << (2 + cc)));
-  const uint16_t writers = (uint16_t)(row_mask | col_mask);  // self, row peer, column peer
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
-    for (int st = 0; st < TW_STAGES; ++st) {
+    issued_sh[0] = 0;
+    issued_sh[1] = 0;
+    for (int st = 0; st < PR_STAGES; ++st) {
       mbar_init(&full_bar[st], 1);
-      mbar_init(&empty_bar[st], 3);
+      mbar_init(&empty_bar[st], 1);
     }
     mbar_init(&acc_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
                  "r"(512));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  cluster_sync_all();  // every barrier of the cluster is initialised before any multicast
+  cluster_sync_all();  // both CTAs' barriers are initialised before any copy or commit reaches them
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  uint32_t tmem = tmem_base_sh;
+  const uint32_t tmem = tmem_base_sh;
 
   if (warp == 0 && lane == 0) {
-    // my halves: rows cc*128.. of the row panel, rows rr*128.. of the column panel
+    const uint32_t bytes = (uint32_t)((two ? 6 : 4) * PR_HALF * 2);  // both CTAs' copies of one K block
+    const int64_t pi = ti * nk, pj0 = tj * nk, pj1 = (tj + 1) * nk;
+    const int off = (int)p * 128;
     for (int kb = 0; kb < TW_PREFETCH && kb < nk; ++kb) {
-      tma_prefetch_2d(&map_hi, 0, (int)((ti * nk + kb) * TW_BM) + cc * MC_BOX_ROWS);
-      tma_prefetch_2d(&map_lo, 0, (int)((ti * nk + kb) * TW_BM) + cc * MC_BOX_ROWS);
-      tma_prefetch_2d(&map_hi, 0, (int)((tj * nk + kb) * TW_BM) + rr * MC_BOX_ROWS);
-      tma_prefetch_2d(&map_lo, 0, (int)((tj * nk + kb) * TW_BM) + rr * MC_BOX_ROWS);
+      tma_prefetch_2d(&map_hi, 0, (int)((pi + kb) * TW_BM) + off);
+      tma_prefetch_2d(&map_lo, 0, (int)((pi + kb) * TW_BM) + off);
+      tma_prefetch_2d(&map_hi, 0, (int)((pj0 + kb) * TW_BM) + off);
+      tma_prefetch_2d(&map_lo, 0, (int)((pj0 + kb) * TW_BM) + off);
+      if (two) {
+        tma_prefetch_2d(&map_hi, 0, (int)((pj1 + kb) * TW_BM) + off);
+        tma_prefetch_2d(&map_lo, 0, (int)((pj1 + kb) * TW_BM) + off);
+      }
     }
     int issued = 0;
     for (int kb = 0; kb < nk; ++kb) {
-      int st = kb % TW_STAGES;
-      uint32_t ph = (uint32_t)(kb / TW_STAGES) & 1u;
+      const int st = kb % PR_STAGES;
+      const uint32_t ph = (uint32_t)(kb / PR_STAGES) & 1u;
       if (!mbar_wait(&empty_bar[st], ph ^ 1u, &abort_flag, status)) break;
       issued = kb + 1;
-      uint8_t* sp = smem + (size_t)st * TW_STAGE_BYTES;
-      mbar_expect_tx(&full_bar[st], TW_STAGE_BYTES);
-      int yi = (int)((ti * nk + kb) * TW_BM) + cc * MC_BOX_ROWS;
-      int yj = (int)((tj * nk + kb) * TW_BM) + rr * MC_BOX_ROWS;
+      if (p == 0) mbar_expect_tx(&full_bar[st], bytes);
+      const uint32_t fb = cluster_addr(&full_bar[st], 0);
+      uint8_t* sp = smem + (size_t)st * PR_STAGE_BYTES;
+      const int yi = (int)((pi + kb) * TW_BM) + off, yj0 = (int)((pj0 + kb) * TW_BM) + off,
+                yj1 = (int)((pj1 + kb) * TW_BM) + off;
       if (kb + TW_PREFETCH < nk) {
         tma_prefetch_2d(&map_hi, 0, yi + TW_PREFETCH * TW_BM);
         tma_prefetch_2d(&map_lo, 0, yi + TW_PREFETCH * TW_BM);
-        tma_prefetch_2d(&map_hi, 0, yj + TW_PREFETCH * TW_BM);
-        tma_prefetch_2d(&map_lo, 0, yj + TW_PREFETCH * TW_BM);
+        tma_prefetch_2d(&map_hi, 0, yj0 + TW_PREFETCH * TW_BM);
+        tma_prefetch_2d(&map_lo, 0, yj0 + TW_PREFETCH * TW_BM);
+        if (two) {
+          tma_prefetch_2d(&map_hi, 0, yj1 + TW_PREFETCH * TW_BM);
+          tma_prefetch_2d(&map_lo, 0, yj1 + TW_PREFETCH * TW_BM);
+        }
       }
-      tma_load_2d_mc(&map_hi, &full_bar[st], sp + 0 * TW_OP_BYTES + cc * MC_HALF_BYTES, 0, yi, row_mask);
-      tma_load_2d_mc(&map_lo, &full_bar[st], sp + 1 * TW_OP_BYTES + cc * MC_HALF_BYTES, 0, yi, row_mask);
-      tma_load_2d_mc(&map_hi, &full_bar[st], sp + 2 * TW_OP_BYTES + rr * MC_HALF_BYTES, 0, yj, col_mask);
-      tma_load_2d_mc(&map_lo, &full_bar[st], sp + 3 * TW_OP_BYTES + rr * MC_HALF_BYTES, 0, yj, col_mask);
+      tma_load_2d_pair(&map_hi, fb, sp + 0 * PR_HALF, 0, yi);
+      tma_load_2d_pair(&map_lo, fb, sp + 1 * PR_HALF, 0, yi);
+      tma_load_2d_pair(&map_hi, fb, sp + 2 * PR_HALF, 0, yj0);
+      tma_load_2d_pair(&map_lo, fb, sp + 3 * PR_HALF, 0, yj0);
+      if (two) {
+        tma_load_2d_pair(&map_hi, fb, sp + 4 * PR_HALF, 0, yj1);
+        tma_load_2d_pair(&map_lo, fb, sp + 5 * PR_HALF, 0, yj1);
+      }
     }
-    // wait until the three consumers have released the last use of every
-    // stage: no peer signals this CTA's barriers after that
-    for (int kb = issued; kb < issued + TW_STAGES && !abort_flag; ++kb) {
-      if (kb < TW_STAGES) continue;  // stage never used
-      int st = kb % TW_STAGES;
-      uint32_t ph = (uint32_t)(kb / TW_STAGES) & 1u;
+    // the even CTA learns how many K blocks each CTA issued (for the drain)
+    if (p == 0) {
+      issued_sh[0] = issued;
+    } else {
+      asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cluster_addr((const void*)&issued_sh[1], 0)),
+                   "r"(issued)
+                   : "memory");
+    }
+    // wait until the MMAs have released the last use of every stage: no
+    // commit of the even CTA reaches this CTA's barriers after that
+    for (int kb = issued; kb < issued + PR_STAGES && !abort_flag; ++kb) {
+      if (kb < PR_STAGES) continue;  // stage never used
+      const int st = kb % PR_STAGES;
+      const uint32_t ph = (uint32_t)(kb / PR_STAGES) & 1u;
       if (!mbar_wait(&empty_bar[st], ph ^ 1u, &abort_flag, status)) break;
     }
-    if (abort_flag) {  // bounded drain of the copies this CTA has in flight
-      for (int kb = issued - TW_STAGES < 0 ? 0 : issued - TW_STAGES; kb < issued; ++kb) {
-        uint32_t ph = (uint32_t)(kb / TW_STAGES) & 1u;
-        for (uint32_t i = 0; i < TC_SPIN_LIMIT && !mbar_try(&full_bar[kb % TW_STAGES], ph); ++i) {
-        }
-      }
-    }
-  } else if (warp == 1 && lane == 0) {
-    const uint32_t idesc = idesc_bf16_128x256();
+  } else if (warp == 1 && lane == 0 && p == 0) {
+    const uint32_t idesc = idesc_bf16_256x256();
+    const uint32_t empty_peer0 = cluster_addr(&empty_bar[0], 1), acc_peer = cluster_addr(&acc_bar, 1);
     for (int kb = 0; kb < nk; ++kb) {
-      int st = kb % TW_STAGES;
-      uint32_t ph = (uint32_t)(kb / TW_STAGES) & 1u;
+      const int st = kb % PR_STAGES;
+      const uint32_t ph = (uint32_t)(kb / PR_STAGES) & 1u;
       if (!mbar_wait(&full_bar[st], ph, &abort_flag, status)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      uint32_t sa = smem_u32(smem + (size_t)st * TW_STAGE_BYTES);
-      uint32_t a_hi = sa, a_lo = sa + TW_OP_BYTES, b_hi = sa + 2 * TW_OP_BYTES, b_lo = sa + 3 * TW_OP_BYTES;
+      const uint32_t sa = smem_u32(smem + (size_t)st * PR_STAGE_BYTES);
+      const uint32_t a_hi = sa, a_lo = sa + PR_HALF;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        uint32_t dt = tmem + (uint32_t)(256 * h);
-        uint32_t aoff = (uint32_t)(h * 128 * 64);
+        if (h == 1 && !two) break;
+        const uint32_t dt = tmem + (uint32_t)(256 * h);
+        const uint32_t b_hi = sa + (2 + 2 * h) * PR_HALF, b_lo = b_hi + PR_HALF;
 #pragma unroll
         for (int k = 0; k < TW_BK / 16; ++k) {
-          uint32_t off = k * 32;
-          uint32_t first = (kb == 0 && k == 0) ? 0u : 1u;
-          umma_bf16(dt, umma_desc_sw64(a_hi + aoff + off), umma_desc_sw64(b_hi + off), idesc, first);
-          umma_bf16(dt, umma_desc_sw64(a_hi + aoff + off), umma_desc_sw64(b_lo + off), idesc, 1u);
-          umma_bf16(dt, umma_desc_sw64(a_lo + aoff + off), umma_desc_sw64(b_hi + off), idesc, 1u);
+          const uint32_t o = k * 32;
+          const uint32_t first = (kb == 0 && k == 0) ? 0u : 1u;
+          umma_bf16_pair(dt, umma_desc_sw64(a_hi + o), umma_desc_sw64(b_hi + o), idesc, first);
+          umma_bf16_pair(dt, umma_desc_sw64(a_hi + o), umma_desc_sw64(b_lo + o), idesc, 1u);
+          umma_bf16_pair(dt, umma_desc_sw64(a_lo + o), umma_desc_sw64(b_hi + o), idesc, 1u);
         }
       }
-      umma_commit_mc(&empty_bar[st], writers);
+      umma_commit_pair(smem_u32(&empty_bar[st]));
+      umma_commit_pair(empty_peer0 + 8u * (uint32_t)st);
     }
-    umma_commit(&acc_bar);
+    umma_commit_pair(smem_u32(&acc_bar));
+    umma_commit_pair(acc_peer);
   }
   __syncwarp();
-  bool have = mbar_wait(&acc_bar, 0u, &abort_flag, status);
+  const bool have = mbar_wait(&acc_bar, 0u, &abort_flag, status);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (have && !abort_flag && store) {
-    tile_epilogue(smem, tmem, warp, lane, row_i, row_j, M, rscale, out);
-  }
+  if (have && !abort_flag && *(volatile int*)status == 0)
+    pair_epilogue(smem, tmem, warp, lane, (int64_t)row_i + 128 * p, row_j, two ? 2 : 1, M, rscale, out);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
-  cluster_sync_all();  // no CTA leaves while a peer may still write into it
+  cluster_sync_all();  // both CTAs are past their MMAs, copies and epilogues
+  if (p == 0 && threadIdx.x == 0 && *(volatile int*)status != 0) {
+    // bounded drain of copies that may still be in flight after an expired wait
+    const int n = issued_sh[0] > issued_sh[1] ? issued_sh[0] : issued_sh[1];
+    for (int kb = n - PR_STAGES < 0 ? 0 : n - PR_STAGES; kb < n; ++kb) {
+      const uint32_t ph = (uint32_t)(kb / PR_STAGES) & 1u;
+      for (uint32_t i = 0; i < (1u << 16) && !mbar_try(&full_bar[kb % PR_STAGES], ph); ++i) {
+      }
+    }
+  }
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  cluster_sync_all();  // no CTA leaves while its peer may still reach it
 }
 
 // ---------------------------------------------------------------- host side
@@ -839,10 +928,9 @@ int wl_trows_split(cov_handle* h, cudaStream_t s) {
 
 // C (lower, FP64) = (hi + lo)(hi + lo)^T scaled, without the lo lo^T term
 // Launch orders, cached per (tile-row range, kind).  kind 0: the lower tiles
-// (ti, tj), tj <= ti, of tile rows [t0, t1), row by row.  kind 1: the 2 x 2
-// super-tiles (top-left tile (t0 + 2 I, 2 J)) that hold at least one of them;
-// the cluster kernel computes all four tiles of each and stores the ones
-// inside the band's lower part.
+// (ti, tj), tj <= ti, of tile rows [t0, t1), row by row.  kind 1: the pair
+// tiles (ti, tj), tj even, each covering the lower tiles (ti, tj) and
+// (ti, tj + 1) (the second only when tj + 1 <= ti).
 int wl_tile_order(cov_handle* h, int kind, int64_t t0, int64_t t1, const int2** tiles, int64_t* n) {
   for (auto& c : h->tile_cache)
     if (c.p && c.kind == kind && c.t0 == t0 && c.t1 == t1) {
@@ -855,16 +943,13 @@ int wl_tile_order(cov_handle* h, int kind, int64_t t0, int64_t t1, const int2** 
     for (int64_t ti = t0; ti < t1; ++ti)
       for (int64_t tj = 0; tj <= ti; ++tj) v.push_back(make_int2((int)ti, (int)tj));
   } else {
-    // groups of MC_GROUP super-rows; inside a group, column by column, so the
-    // ~37 clusters of one wave share a few row and column panels in L2
-    for (int64_t g0 = t0; g0 < t1; g0 += 2 * MC_GROUP) {
-      int64_t g1 = std::min<int64_t>(g0 + 2 * MC_GROUP, t1);
-      int64_t jmax = g1 - 1;  // last tile row of the group
-      for (int64_t j0 = 0; j0 <= jmax; j0 += 2)
-        for (int64_t i0 = g0; i0 < g1; i0 += 2) {
-          int64_t last = std::min<int64_t>(i0 + 1, t1 - 1);
-          if (j0 <= last) v.push_back(make_int2((int)i0, (int)j0));
-        }
+    // groups of PR_GROUP tile rows; inside a group, column pair by column
+    // pair, so the ~76 pairs of one wave share a few row and column panels in L2
+    for (int64_t g0 = t0; g0 < t1; g0 += PR_GROUP) {
+      int64_t g1 = std::min<int64_t>(g0 + PR_GROUP, t1);
+      for (int64_t j0 = 0; j0 < g1; j0 += 2)
+        for (int64_t i = g0; i < g1; ++i)
+          if (j0 <= i) v.push_back(make_int2((int)i, (int)j0));
     }
   }
   // One allocation for the whole ring, sized for the largest matrix of the
@@ -894,8 +979,8 @@ int wl_tile_order(cov_handle* h, int kind, int64_t t0, int64_t t1, const int2** 
   return COV_OK;
 }
 
-// Whether 4-CTA clusters of the multicast kernel can be resident on this device.
-static int mc_clusters_ok() {
+// Whether CTA pairs of the pair kernel can be resident on this device.
+static int pair_clusters_ok() {
   static std::once_flag once[WL_MAX_DEVICES];
   static int ok[WL_MAX_DEVICES];
   int d = 0;
@@ -903,24 +988,24 @@ static int mc_clusters_ok() {
   if (d < 0 || d >= WL_MAX_DEVICES) return 0;
   std::call_once(once[d], [&] {
     ok[d] = 0;
-    if (cudaFuncSetAttribute(k_syrk_tc256_mc, cudaFuncAttributeMaxDynamicSharedMemorySize, TW_SMEM) != cudaSuccess) {
+    if (cudaFuncSetAttribute(k_syrk_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, PR_SMEM) != cudaSuccess) {
       cudaGetLastError();
       return;
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(4);
+    cfg.gridDim = dim3(2);
     cfg.blockDim = dim3(128);
-    cfg.dynamicSmemBytes = TW_SMEM;
+    cfg.dynamicSmemBytes = PR_SMEM;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, (void*)k_syrk_tc256_mc, &cfg) == cudaSuccess && n > 0) ok[d] = n;
+    if (cudaOccupancyMaxActiveClusters(&n, (void*)k_syrk_pair, &cfg) == cudaSuccess && n > 0) ok[d] = n;
     cudaGetLastError();
   });
   return ok[d];
 }
 
 // Launch the contraction over tile rows [r0, row1) of out's band (no status
-// handling): the 2 x 2 cluster kernel when 4-CTA clusters can be placed, else
-// one CTA per tile.
+// handling): CTA pairs when 2-CTA clusters can be placed, else one CTA per
+// tile.
 static int launch_tc(cov_handle* h, const void* hi, const void* lo, const double* rscale, int64_t rows, int Kp,
                      OutMap out, int64_t r0, int64_t row1, cudaStream_t s) {
   int rc;
@@ -929,14 +1014,14 @@ static int launch_tc(cov_handle* h, const void* hi, const void* lo, const double
   if (t1 <= t0) return COV_OK;
   const int2* tiles = nullptr;
   int64_t nblk = 0;
-  if (h->tc_kernel != 0 && mc_clusters_ok()) {
-    CUtensorMap chi, clo;
-    if ((rc = make_map(h, &chi, (void*)hi, rows, Kp, MC_BOX_ROWS))) return rc;
-    if ((rc = make_map(h, &clo, (void*)lo, rows, Kp, MC_BOX_ROWS))) return rc;
+  if (h->tc_kernel != 0 && pair_clusters_ok()) {
+    CUtensorMap mhi, mlo;
+    if ((rc = make_map(h, &mhi, (void*)hi, rows, Kp, 128))) return rc;
+    if ((rc = make_map(h, &mlo, (void*)lo, rows, Kp, 128))) return rc;
     if ((rc = wl_tile_order(h, 1, t0, t1, &tiles, &nblk))) return rc;
-    k_syrk_tc256_mc<<<(unsigned)(4 * nblk), 128, TW_SMEM, s>>>(chi, clo, rows, Kp / TW_BK, rscale, out,
-                                                                h->tc_status, tiles, t1);
-    WL_LAUNCH(h, "k_syrk_tc256_mc");
+    k_syrk_pair<<<(unsigned)(2 * nblk), 128, PR_SMEM, s>>>(mhi, mlo, rows, Kp / TW_BK, rscale, out, h->tc_status,
+                                                           tiles);
+    WL_LAUNCH(h, "k_syrk_pair");
   } else {
     CUtensorMap mhi, mlo;
     if ((rc = make_map(h, &mhi, (void*)hi, rows, Kp))) return rc;

@@ -125,6 +125,25 @@ def test_cfg2_split_bf16_matches_fp64_form(cfg2):
         assert np.max(np.abs(ss / s64 - 1)) <= TOL_SNR
 
 
+def test_cfg2_pair_kernel_equals_one_cta_kernel(cfg2):
+    """The CTA-pair contraction (tcgen05.mma.cta_group::2, 256 x 512 pair
+    tiles) and the one-CTA contraction (256 x 256 tiles) form the same
+    products over the same K blocks: over the whole cfg2 matrix (25 tile rows,
+    diagonal pair tiles with one tile, a ragged last tile row of 231 rows) the
+    two agree far inside the split form's own error."""
+    from paper_1812_07437_gb300.handle import Handle
+    h, r, C64, D = cfg2
+    Cp, _ = _cov(h, N.COV_TERMS_ALL, N.COV_SPLIT_BF16)
+    h1 = Handle(workloads.get("cfg2_5bin"), tc_kernel=N.COV_TC_SINGLE)
+    C1, _ = _cov(h1, N.COV_TERMS_ALL, N.COV_SPLIT_BF16)
+    h1.close()
+    Lp, L1 = torch.tril(Cp), torch.tril(C1)
+    assert torch.isfinite(Lp).all() and torch.isfinite(L1).all()
+    d = torch.sqrt(torch.diagonal(torch.tril(C64)))
+    err = (torch.abs(Lp - L1) / torch.outer(d, d)).tril()
+    assert float(err.max()) <= 1e-6, f"pair vs one-CTA max normalised diff {float(err.max()):.3e}"
+
+
 WHICH = (("P", N.COV_WHICH_P), ("B", N.COV_WHICH_B), ("J", N.COV_WHICH_JOINT))
 
 
