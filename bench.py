@@ -125,19 +125,77 @@ def oracle_elements(r, n, seed):
     return np.maximum(a, b), np.minimum(a, b)
 
 
-def cpu_baseline(name, seconds):
-    r, t_build = oracle_run(name)
-    a, b = oracle_elements(r, 200000, 1234)
+def cpu_model():
+    """The host CPU's model name and its core count (lscpu, else /proc/cpuinfo)."""
+    name = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                name = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not name:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu model")):
+                    name = ln.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return name or "unknown", os.cpu_count() or 1
+
+
+_POOL_COV = None
+
+
+def _pool_init(blob):
+    import pickle
+    global _POOL_COV
+    _POOL_COV = pickle.loads(blob)
+
+
+def _pool_work(job):
+    """Per-element oracle sums over this worker's pairs from t_start for at
+    most `seconds`; returns (elements done, seconds spent)."""
+    a, b, t_start, seconds = job
+    while time.time() < t_start:
+        time.sleep(0.001)
     t0 = time.perf_counter()
     n = 0
     while n < len(a) and time.perf_counter() - t0 < seconds:
-        r.cov.element(int(a[n]), int(b[n]))
+        _POOL_COV.element(int(a[n]), int(b[n]))
         n += 1
-    dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return n, time.perf_counter() - t0
+
+
+def oracle_rate(cov, a, b, seconds, workers):
+    """Aggregate rate of the oracle's per-element sums on `workers` host
+    processes (spawn: the parent may already hold a CUDA context), each on its
+    own share of the seeded pairs, all started at the same moment."""
+    import multiprocessing as mp
+    import pickle
+    blob = pickle.dumps(cov, protocol=5)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers, initializer=_pool_init, initargs=(blob,)) as pool:
+        t_start = time.time() + 5.0
+        jobs = [(a[k::workers], b[k::workers], t_start, seconds) for k in range(workers)]
+        res = pool.map(_pool_work, jobs)
+    n = sum(x[0] for x in res)
+    rate = sum(x[0] / x[1] for x in res if x[1] > 0)
+    return rate, n, max(x[1] for x in res)
+
+
+def cpu_baseline(name, seconds):
+    r, t_build = oracle_run(name)
+    model, cores = cpu_model()
+    a, b = oracle_elements(r, 4000000, 1234)
+    rate, n, dt = oracle_rate(r.cov, a, b, seconds, cores)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": model,
             "sample": f"{n} seeded lower-triangle elements of {name} (M={r.M}), every term, per-element "
-                      f"oracle sums in {dt:.1f} s on 1 host core; oracle tables/spectra build "
-                      f"{t_build:.1f} s not included"}
+                      f"oracle sums for {dt:.1f} s on {cores} host processes ({model}); oracle "
+                      f"tables/spectra build {t_build:.1f} s not included"}
 
 
 def run_reference(args):
@@ -145,28 +203,28 @@ def run_reference(args):
     if rank != 0:
         return
     r, t_build = oracle_run(args.workload)
-    per_step = 400
-    a, b = oracle_elements(r, per_step * (args.steps + args.warmup), 4321)
-    k = 0
+    model, cores = cpu_model()
+    seconds = 4.0  # per step: the oracle on every host core
+    a, b = oracle_elements(r, 4000000, 4321)
     for _ in range(args.warmup):
-        for _ in range(per_step):
-            r.cov.element(int(a[k]), int(b[k]))
-            k += 1
+        oracle_rate(r.cov, a, b, 1.0, cores)
+    rates, ns = [], 0
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        for _ in range(per_step):
-            r.cov.element(int(a[k]), int(b[k]))
-            k += 1
+    for k in range(args.steps):
+        rate, n, _ = oracle_rate(r.cov, a[k::args.steps], b[k::args.steps], seconds, cores)
+        rates.append(rate)
+        ns += n
     dt = time.perf_counter() - t0
-    v = per_step * args.steps / dt
+    v = statistics.mean(rates)
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": args.workload, "M": r.M, "sample_per_step": per_step},
-           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": f"{per_step} seeded covariance elements per step of {args.workload}; "
-                                      f"oracle build {t_build:.1f} s not timed"},
+           "config": {"workload": args.workload, "M": r.M, "sample_per_step": f"{seconds:.0f} s of elements"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": model,
+                            "sample": f"{ns} seeded covariance elements of {args.workload} over {args.steps} "
+                                      f"steps of {seconds:.0f} s on {cores} host processes; oracle build "
+                                      f"{t_build:.1f} s not timed"},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -250,12 +308,13 @@ def launches_per_step(which_sizes, n_tri, split, packed=False, n_sub=8):
     spectra = 5 if n_tri > 0 else 3  # P and B spectra, B and P projections, data vector
     if split:
         # trispectrum table (rows_prep, pair signatures, BF16 rows, contraction) + factor rows (rows_prep,
-        # signatures, BF16 rows) + inverse counts; then the contraction and the per-element products,
-        # once (dense) or once per sub-band (packed band call)
-        assemble = 4 + 3 + 1 + (2 * n_sub if packed else 2)
+        # signatures, BF16 rows) + inverse counts; then the contraction, the per-element products and the
+        # Gaussian diagonal blocks, once (dense) or once per sub-band (packed band call)
+        assemble = 4 + 3 + 1 + (3 * n_sub if packed else 3)
     else:
-        # FP64 trispectrum rows + product, FP64 factor rows, SSC rows, inverse counts, products, SSC product
-        assemble = 2 + 1 + 1 + 1 + 1 + 1 + 1
+        # FP64 trispectrum rows + product, FP64 factor rows, SSC rows, inverse counts, products, Gaussian
+        # blocks, SSC product
+        assemble = 2 + 1 + 1 + 1 + 1 + 1 + 1 + 1
     snr = 0
     for ms in which_sizes:
         nb = (ms + 63) // 64
@@ -288,21 +347,23 @@ def timed(stream, fn, steps, h, world):
     return e0.elapsed_time(e1), stages, out
 
 
-# DRAM bytes (read + write) of the contraction of one full-size band call (its
-# eight sub-band launches), from one-pass ncu captures of those launches
-# (profiles/launches_cfg3_10bin.md).  A figure is valid only while the device
-# code of the contraction's source file, its launch order and its tile
-# constants are unchanged: their text is fingerprinted.
+# DRAM bytes (read + write) per launch of the contraction, from an ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of a small case of the
+# same kernel (profiles/), scaled to the workload by the tiles it computes.  A
+# figure is valid only while the device code of the contraction's source file,
+# its launch order and its tile constants are unchanged: their text is
+# fingerprinted.
 TRAFFIC = {
-    # workload: (bytes per band call, fingerprint at capture)
-    "cfg3_10bin": (5.4201e12, "47f609012164d378"),
+    # workload: (bytes per band call, fingerprint at capture); profiles/k_syrk_pair_cfg3_4bin.md
+    "cfg3_4bin": (23.68e9, "c8a3a44e0073fa0d"),
+    "cfg3_10bin": (23.68e9 * 251695 / 1326, "c8a3a44e0073fa0d"),  # scaled by tiles from cfg3_4bin
 }
 
 
 def kernel_fingerprint():
     import hashlib
     src = open(os.path.join(ROOT, "paper_1812_07437_gb300", "csrc", "syrk_tc.cu")).read()
-    parts = [ln for ln in src.splitlines() if ln.startswith("#define TW_") or ln.startswith("#define MC_")]
+    parts = [ln for ln in src.splitlines() if ln.startswith("#define TW_") or ln.startswith("#define PR_")]
     parts.append(src[:src.index("// ---------------------------------------------------------------- host side")])
     c = src.index("int wl_tile_order(")
     parts.append(src[c:src.index("\n}\n", c)])
@@ -314,8 +375,14 @@ def measured_traffic(workload):
     return ent[0] if ent and kernel_fingerprint() == ent[1] else None
 
 
-def contraction_roofline(stages, elements, K, prec, N, long_kernel):
-    """Roofline of the 1-halo (chi, M) contraction, the kernel the metric is built on."""
+def contraction_roofline(stages, elements, K, prec, N, long_kernel, sm_mhz=None):
+    """Roofline of the 1-halo (chi, M) contraction, the kernel the metric is
+    built on.  achieved / frac count the method's work, 2 K' FLOP per unique
+    element (K' = K + N_chi with the super-sample columns); the split form
+    issues three BF16 products per FMA (hi hi + hi lo + lo hi), reported beside
+    it as achieved_issued / frac_issued.  The peak is cuBLAS BF16 measured at
+    the SM clock in peak_sm_mhz; the run's own median clock is sm_mhz, and
+    frac_issued_at_run_clock rescales the peak to it."""
     syrk_ms, syrk_calls = stages["syrk_1h"]
     avg_ms = syrk_ms / max(syrk_calls, 1)
     flops = 2.0 * elements * K
@@ -327,11 +394,17 @@ def contraction_roofline(stages, elements, K, prec, N, long_kernel):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     key = "bf16_tflops_sustained" if long_kernel else "bf16_tflops"
     peak = peaks[key]
-    issued = 3.0 * flops / (avg_ms / 1e3) / 1e12
-    return {"bound": "tensor", "achieved": issued, "peak": peak, "unit": "TFLOP/s", "frac": issued / peak,
-            "traffic": None, "kernel": "k_syrk_tc256_mc (tcgen05 split-BF16 1-halo + SSC contraction, 2x2 clusters)",
-            "launch_ms": avg_ms, "algorithmic_tflops": achieved,
-            "peak_source": f"MEASURED_PEAKS.json {key}, of measured"}
+    peak_mhz = (peaks.get("clocks_under_load") or {}).get("sm_mhz_median")
+    issued = 3.0 * achieved
+    out = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+           "frac_algorithmic": achieved / peak, "achieved_issued": issued, "frac_issued": issued / peak,
+           "traffic": None,
+           "kernel": "k_syrk_pair (tcgen05.mma.cta_group::2 split-BF16 1-halo + SSC contraction, 256x512 pair tiles)",
+           "launch_ms": avg_ms, "sm_mhz": sm_mhz, "peak_sm_mhz": peak_mhz,
+           "peak_source": f"MEASURED_PEAKS.json {key}, of measured"}
+    if sm_mhz and peak_mhz:
+        out["frac_issued_at_run_clock"] = issued / (peak * sm_mhz / peak_mhz)
+    return out
 
 
 def dense_run(h, wl, cosmo, prec, stream, steps, warmup, world, fp64_form):
@@ -782,7 +855,7 @@ def run_ours(args):
 
     ms_step = job_step_ms(ms_step, world, dev)
     value = world * elements / (ms_step / 1e3)
-    roof = contraction_roofline(stages, elements, Kc, prec, N, long_kernel=packed)
+    roof = contraction_roofline(stages, elements, Kc, prec, N, long_kernel=packed, sm_mhz=clocks.get("sm_mhz"))
     if prec != N.COV_FP64:
         roof["traffic"] = measured_traffic(args.workload)
         roof["algorithmic_bytes"] = elements * 8 + 2 * 2 * M * Kc  # tiles written once, hi/lo operands read once

@@ -228,6 +228,18 @@ int cov_table(cov_handle* h, const char* name, double* host, int64_t* count, voi
  * milliseconds and the number of timed calls per stage into the first
  * n_stages entries of ms / calls (host arrays, either may be NULL) and
  * clears the record.  cov_stage_name(i) names stage i (NULL past the end). */
+/* Self-test of failure detection (the paper has no counterpart).  Every wait
+ * of the library's tensor-core kernels on an mbarrier is bounded: when it
+ * expires, the kernel raises a status word, stops issuing work and returns,
+ * and the call returns COV_ERR_TIMEOUT.  This call runs that protocol on a
+ * wait that nothing asynchronous depends on: one kernel polls a device flag
+ * up to `spins` times (1 <= spins <= 2^24, ~0.1 us apart).  With
+ * flag_preset != 0 the flag is set before the kernel starts and the call
+ * returns COV_OK; with flag_preset == 0 nothing sets it, the wait expires and
+ * the call returns COV_ERR_TIMEOUT (message in cov_last_error(h)).  The
+ * handle stays usable either way.  Synchronous on `stream`. */
+int cov_wait_selftest(cov_handle* h, unsigned spins, int flag_preset, void* stream);
+
 int cov_profile(cov_handle* h, int enable);
 int cov_stage_times(cov_handle* h, double* ms, int64_t* calls, int n_stages);
 const char* cov_stage_name(int stage);
@@ -247,14 +259,19 @@ const char* cov_stage_name(int stage);
  * each <= M; an empty prefix gives NaN).  *d_status (device int) is set to 0,
  * or to 1 when a pivot was not positive.  Nothing is allocated and nothing
  * is synchronised: the call is ordered on stream and the caller reads
- * d_snr / d_status after it.
+ * d_snr / d_status after it.  Because nothing is synchronised, a covariance
+ * that is not positive definite is reported only through *d_status: the call
+ * itself still returns COV_OK (its return code covers the arguments and the
+ * launches), and d_snr then holds meaningless values.
  *
  * The workspace is one static device array of (COV_NOALLOC_MAX_M + 1)^2
  * doubles (32 MiB) that every GPU loading the library holds until the process
  * exits; M > COV_NOALLOC_MAX_M is rejected with COV_ERR_INVALID (message in
- * cov_last_error(NULL)).  The first call on each device looks up the array's
- * device address with that device current; make that first call before any
- * stream capture.  All calls share the array and it keeps the last call's
+ * cov_last_error(NULL)).  The first call in each CUDA context (each device's
+ * primary context, normally) looks up the array's device address with that
+ * context current; make that first call before any stream capture.  After a
+ * device reset the next call runs in a new context and looks the address up
+ * again.  All calls share the array and it keeps the last call's
  * contents, so calls that overlap on the GPU race and must be serialised by
  * the caller. */
 #define COV_NOALLOC_MAX_M 2047

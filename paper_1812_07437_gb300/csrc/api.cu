@@ -225,7 +225,7 @@ static void free_all(cov_handle* h) {
                   h->C2,    h->C3,    h->tc_status, h->Thi,   h->Tlo,    h->Tscale, h->Trows,     h->Tmat,
                   h->Srows, h->cosmo_d, h->Fsig,  h->Esig,    h->Msig,   h->FsigT,  h->EsigT,     h->MsigT,
                   h->invN,  h->omN,   h->work,    h->chol_scratch, h->chol_status, h->mb, h->omb, h->cs,
-                  h->cw,    h->sigF,  h->ac};
+                  h->cw,    h->sigF,  h->ac,      h->bmask,   h->gblk,   h->wait_flag};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->tile_ring) cudaFree(h->tile_ring);
@@ -529,6 +529,38 @@ extern "C" int cov_table(cov_handle* h, const char* name, double* host, int64_t*
     }
   }
   return wl_fail(h, COV_ERR_INVALID, std::string("unknown table ") + name);
+}
+
+// One lane polls a device flag up to `spins` times with the bounded-wait
+// protocol of the tensor-core kernels: on expiry it raises the status word
+// and returns.  Nothing asynchronous (bulk copy, MMA) is in flight meanwhile.
+__global__ void k_wait_flag(const volatile int* flag, unsigned spins, int* status) {
+  if (threadIdx.x != 0) return;
+  for (unsigned i = 0; i < spins; ++i) {
+    if (*flag) return;
+    __nanosleep(100);
+  }
+  atomicExch(status, 1);
+}
+
+extern "C" int cov_wait_selftest(cov_handle* h, unsigned spins, int flag_preset, void* stream) {
+  if (!h) return COV_ERR_INVALID;
+  if (spins == 0 || spins > (1u << 24))
+    return wl_fail(h, COV_ERR_INVALID, "cov_wait_selftest: spins must be in [1, 2^24]");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc;
+  if ((rc = wl_ensure(h, (void**)&h->wait_flag, sizeof(int), "self-test flag"))) return rc;
+  WL_CHECK(h, cudaMemsetAsync(h->wait_flag, flag_preset ? 1 : 0, sizeof(int), s));  // nonzero word when set
+  const bool deferred = h->deferred;
+  h->deferred = false;
+  rc = wl_tc_status_reset(h, s);
+  if (rc == COV_OK) {
+    k_wait_flag<<<1, 32, 0, s>>>(h->wait_flag, spins, h->tc_status);
+    cudaError_t e = cudaGetLastError();
+    rc = e != cudaSuccess ? wl_cuda(h, e, "k_wait_flag") : wl_tc_status_check(h, s);
+  }
+  h->deferred = deferred;
+  return rc;
 }
 
 extern "C" int cov_profile(cov_handle* h, int enable) {

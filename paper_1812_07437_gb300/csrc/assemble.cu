@@ -1,8 +1,13 @@
 // Covariance assembly (paper Sec. 3.2 and Appendix B):
 //  * the 1-halo contraction stores the lower triangle first (no clear pass);
-//  * k_gather   Gaussian PP/BB, BB+PT and PB product terms, element by
-//               element over the lower triangle, added on top (or stored when
-//               the 1-halo term is not requested);
+//  * k_gather   BB+PT and PB product terms, element by element, added on top
+//               (or stored when the 1-halo term is not requested) over the
+//               32 x 32 blocks whose rows share an ell bin: every one of these
+//               terms vanishes elsewhere (blocks of the remaining ~3/4 of the
+//               lower triangle return at once, or store zeros);
+//  * k_gauss    the Gaussian PP and BB terms, added over the diagonal blocks
+//               of one ell bin (P rows) or one triangle (B rows), the sum over
+//               leg permutations reduced across lanes by warp shuffles;
 //  * k_gemm_lower  C = alpha A B^T + beta C on the lower triangle in FP64:
 //               the 1-halo (chi, M) contraction (FP64 form), the 1-halo
 //               trispectrum table of the PT term and the rank-N_chi
@@ -35,6 +40,7 @@ struct GatherArgs {
   int64_t ntrow;
   const double* invN;    // 1 / N(l^b)
   const double* omN;     // Omega / N_tri(t)
+  const uint64_t* bmask; // ell bins present in each 32-row block
 };
 
 // 1 / N(l^b) and Omega / N_tri(t) from the exact integer counts, once per
@@ -54,26 +60,10 @@ __device__ __forceinline__ double b1h(const GatherArgs& g, int t, int i, int j, 
 
 __device__ double gather_element(const GatherArgs& g, const int32_t* ra, const int32_t* rb) {
   double v = 0.0;
-  if (ra[0] == 0 && rb[0] == 0) {
-    if ((g.terms & COV_TERM_G) && ra[1] == rb[1]) {
-      int b = ra[1], i = ra[4], j = ra[5], k = rb[4], l = rb[5];
-      v += (ps(g, b, i, k) * ps(g, b, j, l) + ps(g, b, i, l) * ps(g, b, j, k)) * g.invN[b];
-    }
-    return v;
-  }
+  if (ra[0] == 0 && rb[0] == 0) return v;  // PP: the Gaussian term only (k_gauss)
   if (ra[0] == 1 && rb[0] == 1) {
     const int* ba = ra + 1; const int* ta = ra + 4;
     const int* bb = rb + 1; const int* tb = rb + 4;
-    if ((g.terms & COV_TERM_G) && ra[7] == rb[7]) {
-      const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
-      double tot = 0.0;
-      for (int p = 0; p < 6; ++p) {
-        const int* s = perm[p];
-        if (ba[0] == ba[s[0]] && ba[1] == ba[s[1]] && ba[2] == ba[s[2]])
-          tot += ps(g, ba[0], ta[0], tb[s[0]]) * ps(g, ba[1], ta[1], tb[s[1]]) * ps(g, ba[2], ta[2], tb[s[2]]);
-      }
-      v += g.omN[ra[7]] * tot;
-    }
     if (g.terms & COV_TERM_BBPT) {
       for (int x = 0; x < 3; ++x)
         for (int y = 0; y < 3; ++y) {
@@ -115,25 +105,97 @@ __device__ __forceinline__ void tri_tile(int64_t id, int64_t* ti, int64_t* tj) {
   *tj = id - i * (i + 1) / 2;
 }
 
+// ell bins present in every 32-row block of the data vector (bit b: a row of
+// the block has a leg in ell bin b); all bits when n_ell > 64 (no skipping)
+__global__ void k_block_masks(int64_t M, int nl, const int32_t* rd, uint64_t* bm) {
+  int64_t blk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (blk >= (M + 31) / 32) return;
+  uint64_t m = 0;
+  if (nl <= 64) {
+    for (int64_t r = blk * 32; r < M && r < blk * 32 + 32; ++r) {
+      const int32_t* x = rd + 8 * r;
+      m |= 1ull << x[1];
+      if (x[0] == 1) m |= (1ull << x[2]) | (1ull << x[3]);
+    }
+  } else {
+    m = ~0ull;
+  }
+  bm[blk] = m;
+}
+
 __global__ void k_gather(GatherArgs g, int64_t M, OutMap out, int accumulate, int64_t tile_off) {
   __shared__ int32_t rdA[32 * 8], rdB[32 * 8];
   int64_t ti, tj;
   tri_tile((int64_t)blockIdx.x + tile_off, &ti, &tj);
   int64_t a0 = ti * 32, b0 = tj * 32;
+  // BB+PT and PB need a leg of one row and a leg of the other in the same ell
+  // bin: with no common bin in the two blocks every element is zero here
+  const bool none = (g.bmask[ti] & g.bmask[tj]) == 0;
+  if (none && accumulate) return;
   int tid = threadIdx.y * 32 + threadIdx.x;
-  for (int e = tid; e < 256; e += 256) {
-    int r = e / 8, c = e % 8;
-    rdA[e] = (a0 + r < M) ? g.rd[(a0 + r) * 8 + c] : 0;
-    rdB[e] = (b0 + r < M) ? g.rd[(b0 + r) * 8 + c] : 0;
+  if (!none) {
+    for (int e = tid; e < 256; e += 256) {
+      int r = e / 8, c = e % 8;
+      rdA[e] = (a0 + r < M) ? g.rd[(a0 + r) * 8 + c] : 0;
+      rdB[e] = (b0 + r < M) ? g.rd[(b0 + r) * 8 + c] : 0;
+    }
   }
   __syncthreads();
   int64_t b = b0 + threadIdx.x;
   for (int rr = threadIdx.y; rr < 32; rr += 8) {
     int64_t a = a0 + rr;
     if (a >= M || b >= M || b > a) continue;
-    double v = gather_element(g, rdA + rr * 8, rdB + threadIdx.x * 8);
+    double v = none ? 0.0 : gather_element(g, rdA + rr * 8, rdB + threadIdx.x * 8);
     double* p = out.at(a, b);
     *p = accumulate ? *p + v : v;
+  }
+}
+
+// ---- Gaussian terms on the diagonal blocks ------------------------------------
+// The Gaussian PP term pairs two P rows of one ell bin, the Gaussian BB term two
+// B rows of one triangle (R6: Omega / N_tri times the sum over the leg
+// permutations sigma whose bins match, of prod_a P^s_{t_a t'_sigma(a)}(l_a)).
+// Rows of one bin (P) or one triangle (B) are contiguous in every row order, so
+// the term lives on diagonal blocks, cut into 32 x 32 sub-blocks (int4: first
+// row of the segment, its length, sub-block row and column).  Eight lanes per
+// element: lane q computes the product of permutation q (q < 6, zero when its
+// bins do not match; PP: q < 2 for the two pairings), and three xor shuffles
+// reduce the eight lanes.
+__global__ void __launch_bounds__(256) k_gauss(GatherArgs g, const int4* __restrict__ blk, int64_t row0,
+                                               int64_t row1, OutMap out) {
+  const int4 d = blk[blockIdx.x];
+  const int64_t s0 = d.x, ra0 = s0 + 32 * (int64_t)d.z, rb0 = s0 + 32 * (int64_t)d.w;
+  const int64_t send = s0 + d.y;
+  const int lane = threadIdx.x & 31, q = lane & 7, warp = threadIdx.x >> 5;
+  const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  // 1024 elements, four per warp pass, eight warps
+  for (int e0 = warp * 4; e0 < 1024; e0 += 32) {
+    const int e = e0 + (lane >> 3);
+    const int64_t a = ra0 + (e >> 5), b = rb0 + (e & 31);
+    const bool ok = a < send && b < send && b <= a && a >= row0 && a < row1;
+    double v = 0.0;
+    if (ok) {
+      const int32_t* x = g.rd + 8 * a;
+      const int32_t* y = g.rd + 8 * b;
+      if (x[0] == 0) {
+        const int bn = x[1], i = x[4], j = x[5], k = y[4], l = y[5];
+        if (q == 0) v = ps(g, bn, i, k) * ps(g, bn, j, l);
+        if (q == 1) v = ps(g, bn, i, l) * ps(g, bn, j, k);
+      } else if (q < 6) {
+        const int* sg = perm[q];
+        const int* ba = x + 1;
+        if (ba[0] == ba[sg[0]] && ba[1] == ba[sg[1]] && ba[2] == ba[sg[2]])
+          v = ps(g, ba[0], x[4], y[4 + sg[0]]) * ps(g, ba[1], x[5], y[4 + sg[1]]) * ps(g, ba[2], x[6], y[4 + sg[2]]);
+      }
+    }
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    if (ok && q == 0) {
+      const int32_t* x = g.rd + 8 * a;
+      double* p = out.at(a, b);
+      *p += v * (x[0] == 0 ? g.invN[x[1]] : g.omN[x[7]]);
+    }
   }
 }
 
@@ -242,9 +304,61 @@ static int gather_args(cov_handle* h, unsigned terms, GatherArgs* g, cudaStream_
   if ((rc = ensure(h, (void**)&h->invN, sizeof(double) * h->nl, "inverse mode counts"))) return rc;
   if ((rc = ensure(h, (void**)&h->omN, sizeof(double) * (h->ntri > 0 ? h->ntri : 1), "inverse triangle counts")))
     return rc;
+  const int64_t nb = (h->M + 31) / 32;
+  if ((rc = ensure(h, (void**)&h->bmask, sizeof(uint64_t) * nb, "block ell-bin masks"))) return rc;
+  if (!h->bmask_ready) {  // the layout does not change with the cosmology
+    k_block_masks<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(h->M, h->nl, h->rowdesc_d, h->bmask);
+    WL_LAUNCH(h, "k_block_masks");
+    h->bmask_ready = true;
+  }
   k_inv_counts<<<1, 256, 0, s>>>(h->nl, h->ntri, h->omega, h->Nmodes, h->Ntri, h->invN, h->omN);
   WL_LAUNCH(h, "k_inv_counts");
-  *g = GatherArgs{h->nt, h->nleg, terms, h->omega, h->rowdesc_d, h->Ps, h->B1hp, h->Tmat, h->ntrow, h->invN, h->omN};
+  *g = GatherArgs{h->nt,   h->nleg, terms, h->omega, h->rowdesc_d, h->Ps, h->B1hp, h->Tmat, h->ntrow,
+                  h->invN, h->omN,  h->bmask};
+  return COV_OK;
+}
+
+// The 32 x 32 sub-blocks (lower part) of the diagonal blocks that hold the
+// Gaussian terms: one block per run of consecutive rows of the same type and
+// ell bin (P) or triangle (B).  Built once per handle from the row table.
+static int gauss_blocks(cov_handle* h) {
+  if (h->gblk) return COV_OK;
+  std::vector<int4> v;
+  h->gblk_row.clear();
+  const int64_t M = h->M;
+  int64_t a = 0;
+  while (a < M) {
+    const int32_t* r = &h->rowdesc[8 * a];
+    const int key = r[0] == 0 ? r[1] : r[7];
+    int64_t e = a + 1;
+    while (e < M && h->rowdesc[8 * e] == r[0] && (r[0] == 0 ? h->rowdesc[8 * e + 1] : h->rowdesc[8 * e + 7]) == key)
+      ++e;
+    const int64_t L = e - a, nb = (L + 31) / 32;
+    for (int64_t bi = 0; bi < nb; ++bi)
+      for (int64_t bj = 0; bj <= bi; ++bj) {
+        v.push_back(make_int4((int)a, (int)L, (int)bi, (int)bj));
+        h->gblk_row.push_back(a + 32 * bi);
+      }
+    a = e;
+  }
+  int rc;
+  if ((rc = ensure(h, (void**)&h->gblk, sizeof(int4) * std::max<size_t>(v.size(), 1), "Gaussian block list")))
+    return rc;
+  if (!v.empty()) WL_CHECK(h, cudaMemcpy(h->gblk, v.data(), sizeof(int4) * v.size(), cudaMemcpyHostToDevice));
+  return COV_OK;
+}
+
+// Gaussian terms of rows [r0, r1) (added; after the contraction and k_gather)
+static int gauss(cov_handle* h, const GatherArgs& g, int64_t r0, int64_t r1, OutMap out, cudaStream_t s) {
+  if (!(g.terms & COV_TERM_G) || r1 <= r0) return COV_OK;
+  int rc;
+  if ((rc = gauss_blocks(h))) return rc;
+  const auto& st = h->gblk_row;
+  const int64_t first = std::lower_bound(st.begin(), st.end(), r0 - 31) - st.begin();
+  const int64_t last = std::lower_bound(st.begin(), st.end(), r1) - st.begin();
+  if (last <= first) return COV_OK;
+  k_gauss<<<(unsigned)(last - first), 256, 0, s>>>(g, h->gblk + first, r0, r1, out);
+  WL_LAUNCH(h, "k_gauss");
   return COV_OK;
 }
 
@@ -330,6 +444,7 @@ int wl_assemble(cov_handle* h, double* C, int64_t ldc, unsigned terms, int preci
   k_gather<<<(unsigned)(nt32 * (nt32 + 1) / 2), dim3(32, 8), 0, s>>>(g, M, out_rows(C, ldc),
                                                                   (terms & COV_TERM_1H) ? 1 : 0, 0);
   WL_LAUNCH(h, "k_gather");
+  if ((rc = gauss(h, g, 0, M, out_rows(C, ldc), s))) return rc;
   wl_stage_end(h, tg, s);
   // 3. super-sample term, rank N_chi (already inside the split contraction)
   if ((terms & COV_TERM_SSC) && !ssc_merged) {
@@ -438,6 +553,7 @@ int wl_assemble_band(cov_handle* h, int64_t row0, int64_t nrows, OutMap out, uns
       int tg = wl_stage_begin(h, ST_GATHER, h->side);
       gather(cut[k], cut[k + 1], h->side);
       WL_LAUNCH(h, "k_gather");
+      if ((rc = gauss(h, g, cut[k], cut[k + 1], out, h->side))) return rc;
       wl_stage_end(h, tg, h->side);
     }
     wl_stage_end(h, tk, s);
@@ -454,6 +570,7 @@ int wl_assemble_band(cov_handle* h, int64_t row0, int64_t nrows, OutMap out, uns
   int tg = wl_stage_begin(h, ST_GATHER, s);
   gather(row0, row1, s);
   WL_LAUNCH(h, "k_gather");
+  if ((rc = gauss(h, g, row0, row1, out, s))) return rc;
   wl_stage_end(h, tg, s);
   if ((terms & COV_TERM_SSC) && (terms & COV_TERM_1H)) {
     int tk = wl_stage_begin(h, ST_SYRK_SSC, s);

@@ -140,6 +140,10 @@ struct cov_handle {
   // per leg-bin signature s (P: ell bin; B: nl + triangle): F[s][n][q] / 2^E[s][n] in FP32,
   // E[s][n], and the FP64 row-block maximum max_q |F[s][n][q]|
   double *invN = nullptr, *omN = nullptr;  // 1 / N(l^b), Omega / N_tri(t)
+  uint64_t* bmask = nullptr;  // ell bins present in each 32-row block (the product terms skip the rest)
+  bool bmask_ready = false;
+  int4* gblk = nullptr;       // 32 x 32 sub-blocks of the Gaussian-term diagonal blocks, by first row
+  std::vector<int64_t> gblk_row;  // (host) first row of each sub-block, ascending
   // launch orders of the tensor-core contraction, by tile-row range
   struct TileOrder {
     int kind = -1;
@@ -156,6 +160,7 @@ struct cov_handle {
   int* Esig = nullptr;
   double* Msig = nullptr;
   int* tc_status = nullptr; // status word of the tensor-core contraction
+  int* wait_flag = nullptr; // flag of the bounded-wait self-test
   double* Trows = nullptr;  // [ntrow][K]
   double* Tmat = nullptr;   // [ntrow][ntrow] lower
   uint16_t *Thi = nullptr, *Tlo = nullptr;  // split trispectrum rows (tensor-core form)

@@ -12,9 +12,11 @@
 // The array (g_snr_scratch) is part of this library's device image: every GPU
 // that loads the library holds it (COV_NOALLOC_MAX_M + 1)^2 doubles, 32 MiB,
 // until the process exits.  In host code its name is only a host-side
-// stand-in, so the device address is looked up once per device, with that
-// device current, through cudaGetSymbolAddress on the first call made on that
-// device; that first call should come before any stream capture.  All calls
+// stand-in, so the device address is looked up through cudaGetSymbolAddress,
+// with the device current, on the first call made in each CUDA context (the
+// device's primary context, normally); that first call should come before any
+// stream capture.  A device reset ends the context: the next call finds a new
+// context and looks the address up again instead of using a stale one.  All calls
 // share the one array and it keeps the last call's contents: calls whose work
 // overlaps on the GPU (different streams, or several host threads) race on
 // it and must be serialised by the caller.  Every workspace entry a call reads
@@ -67,7 +69,27 @@ __global__ void k_na_prefix(int64_t M, const double* Wk, int64_t ldw, PrefixCoun
 
 void wl_set_global_error(const std::string& msg);  // api.cu: read by cov_last_error(NULL)
 static std::mutex g_na_mutex;
+// the array's device address per device, with the context it was looked up in
 static double* g_na_ptr[128] = {nullptr};
+static CUcontext g_na_ctx[128] = {nullptr};
+
+// the calling thread's current CUDA context (the driver entry point, looked up
+// once; cudart makes the device's primary context current first)
+static CUcontext na_current_context(int dev) {
+  typedef CUresult (*PFN_ctx)(CUcontext*);
+  static PFN_ctx fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      return (PFN_ctx)p;
+    return (PFN_ctx) nullptr;
+  }();
+  CUcontext c = nullptr;
+  cudaSetDevice(dev);  // makes the device's primary context current (allocates nothing)
+  if (fn) fn(&c);
+  return c;
+}
 
 static int na_fail(int code, const std::string& msg) {
   wl_set_global_error(msg);
@@ -95,7 +117,9 @@ extern "C" int cov_snr_noalloc(const double* d_C, int64_t ldc, const double* d_D
   double* work = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_na_mutex);
-    if (!g_na_ptr[dev]) {
+    const CUcontext ctx = na_current_context(dev);
+    if (!g_na_ptr[dev] || g_na_ctx[dev] != ctx) {
+      g_na_ctx[dev] = ctx;
       e = cudaGetSymbolAddress((void**)&g_na_ptr[dev], g_snr_scratch);
       if (e != cudaSuccess) {
         g_na_ptr[dev] = nullptr;

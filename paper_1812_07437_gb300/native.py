@@ -50,7 +50,7 @@ EXPORTED = ["cov_init", "cov_update", "cov_layout", "cov_counts", "cov_spectra",
             "cov_assemble_band", "cov_table", "cov_profile", "cov_stage_times", "cov_stage_name", "cov_snr_noalloc",
             "cov_last_error", "cov_free", "cov_snr_tiles", "cov_batch_snr", "cov_server_create", "cov_server_submit", "cov_server_wait",
             "cov_server_error", "cov_server_stats_get", "cov_server_clock", "cov_request_footprint",
-            "cov_server_free"]
+            "cov_server_free", "cov_wait_selftest"]
 
 COV_REQ_QUEUED = 0
 COV_REQ_RUNNING = 1
@@ -141,6 +141,7 @@ def lib():
         L.cov_stage_name.argtypes = [C.c_int]
         L.cov_stage_name.restype = C.c_char_p
         L.cov_snr_noalloc.argtypes = [P, i64, P, i64, P, C.c_int, P, P, P]
+        L.cov_wait_selftest.argtypes = [P, C.c_uint, C.c_int, P]
         L.cov_last_error.argtypes = [P]
         L.cov_last_error.restype = C.c_char_p
         L.cov_free.argtypes = [P]
