@@ -43,14 +43,17 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="cfg3_10bin")
     p.add_argument("--layout", default="auto", choices=["auto", "dense", "tiles"])
-    p.add_argument("--snr-workload", default="cfg2_5bin")
+    p.add_argument("--snr-workload", default="cfg3_5bin",
+                   help="dense workload of the S/N stage (its stored oracle S/N gives the error)")
+    p.add_argument("--no-snr-10bin", action="store_true",
+                   help="skip the default 10-bin joint S/N in place on packed tiles")
     p.add_argument("--no-snr-run", action="store_true")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--batch-bins", default="3,5", help="tomographic bin counts of the batched Fisher run")
     p.add_argument("--snr-10bin", action="store_true",
-                   help="also time the cumulative S/N of the workload itself, in place on its packed tiles "
-                        "(one extra assembly and FP64-accurate Cholesky per row set; minutes at 10 bins)")
+                   help="also time the P and B cumulative S/N of the workload itself (besides the joint one), "
+                        "in place on packed tiles, per --snr-rows")
     p.add_argument("--snr-rows", default="joint,B,P", help="row sets of --snr-10bin")
     p.add_argument("--snr-precision", default="auto", choices=["auto", "fp64", "split_bf16"],
                    help="covariance form of --snr-10bin (auto: the bench's own)")
@@ -66,6 +69,8 @@ def parse():
                    help="also run the concentration-scatter comparison (model A against model B)")
     p.add_argument("--model-a-workload", default="cfg3_5bin")
     p.add_argument("--model-a-nodes", type=int, default=8, help="concentration nodes of model A")
+    p.add_argument("--chol-kernel", default="auto", choices=["auto", "tile"],
+                   help="Cholesky trailing update: persistent (auto) or one CTA per 128 x 64 tile")
     p.add_argument("--paper-replica", action="store_true",
                    help="also run the S/N experiments of the paper's own set-up (Sec. 5)")
     return p.parse_args()
@@ -190,10 +195,10 @@ def oracle_rate(cov, a, b, seconds, workers):
 def cpu_baseline(name, seconds):
     r, t_build = oracle_run(name)
     model, cores = cpu_model()
-    a, b = oracle_elements(r, 4000000, 1234)
+    a, b = oracle_elements(r, 8000000, 1234)
     rate, n, dt = oracle_rate(r.cov, a, b, seconds, cores)
     return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": model,
-            "sample": f"{n} seeded lower-triangle elements of {name} (M={r.M}), every term, per-element "
+            "sample": f"{n} of 8M seeded lower-triangle elements of {name} (M={r.M}), every term, per-element "
                       f"oracle sums for {dt:.1f} s on {cores} host processes ({model}); oracle "
                       f"tables/spectra build {t_build:.1f} s not included"}
 
@@ -227,6 +232,29 @@ def run_reference(args):
                                       f"{t_build:.1f} s not timed"},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def stored_oracle_snr(name):
+    """The oracle's cumulative S/N of a workload as stored by
+    tests/golden/make_snr.py ({'P'|'B'|'J': [n_ell]}), or None (text only: no
+    oracle code runs here)."""
+    import numpy as np
+    path = os.path.join(ROOT, "tests", "golden", f"snr_{name}.txt")
+    if not os.path.exists(path):
+        return None
+    out = {}
+    for line in open(path):
+        p = line.split()
+        if p and not p[0].startswith("#"):
+            out.setdefault(p[0], {})[int(p[1])] = float(p[2])
+    return {k: np.array([v[c] for c in sorted(v)]) for k, v in out.items()}
+
+
+def max_rel(a, b):
+    import numpy as np
+    a, b = np.asarray(a, dtype=float), np.asarray(b, dtype=float)
+    m = np.isfinite(a) & np.isfinite(b)
+    return float(np.max(np.abs(a[m] / b[m] - 1.0))) if m.any() else None
 
 
 # ---------------------------------------------------------------- clocks
@@ -407,7 +435,7 @@ def contraction_roofline(stages, elements, K, prec, N, long_kernel, sm_mhz=None)
     return out
 
 
-def dense_run(h, wl, cosmo, prec, stream, steps, warmup, world, fp64_form):
+def dense_run(h, wl, cosmo, prec, stream, steps, warmup, world, fp64_form, fp64_steps=2):
     """The whole path on a workload whose dense M x M square fits: tables,
     counts, spectra, the dense covariance and the three cumulative S/N
     (P, B, joint) by FP64 Cholesky."""
@@ -432,9 +460,10 @@ def dense_run(h, wl, cosmo, prec, stream, steps, warmup, world, fp64_form):
         ms, stages, snr = timed(stream, step, steps, h, world)
         out = {"ms_per_step": ms / steps, "stages": stages, "snr": snr, "D": D, "C": C}
         if fp64_form and prec != N.COV_FP64:
-            step(N.COV_FP64)
-            ms64, st64, snr64 = timed(stream, lambda: step(N.COV_FP64), 2, h, 1)
-            out["fp64"] = {"ms_per_step": ms64 / 2, "stages": st64, "snr": snr64}
+            if fp64_steps > 1:
+                step(N.COV_FP64)
+            ms64, st64, snr64 = timed(stream, lambda: step(N.COV_FP64), fp64_steps, h, 1)
+            out["fp64"] = {"ms_per_step": ms64 / fp64_steps, "stages": st64, "snr": snr64}
             rel = max(float(np.nanmax(np.abs(a / b - 1))) for a, b in zip(snr, snr64))
             out["snr_rel_err_vs_fp64_form"] = rel
     return out
@@ -653,7 +682,7 @@ def paper_run(device):
     return out
 
 
-def snr_tiles_run(wl, prec, device, row_sets):
+def snr_tiles_run(wl, prec, device, row_sets, chol=0):
     """Cumulative S/N of the workload's own data vector without a dense square:
     a handle in cumulative row order assembles its lower-packed tiles (plus one
     row for D) and cov_snr_tiles factorises them in place."""
@@ -664,7 +693,7 @@ def snr_tiles_run(wl, prec, device, row_sets):
     dev = torch.device("cuda", device)
     out = {}
     for name, rows in row_sets:
-        h = Handle(wl, device=device, rows=rows, order=N.COV_ORDER_CUMULATIVE)
+        h = Handle(wl, device=device, rows=rows, order=N.COV_ORDER_CUMULATIVE, chol_kernel=chol)
         D = torch.zeros(h.M, dtype=torch.float64, device=dev)
         Ct = torch.empty(packed_tiles(h.M + 1) * 65536, dtype=torch.float64, device=dev)
         st = torch.cuda.Stream(device=dev)
@@ -720,7 +749,8 @@ def run_ours(args):
     wl = workloads.get(args.workload)
     cosmo = rank_cosmo(wl)
     wl = workloads.get(args.workload, cosmology=cosmo)
-    h = Handle(wl, device=local)
+    chol = N.COV_CHOL_TILE if args.chol_kernel == "tile" else N.COV_CHOL_AUTO
+    h = Handle(wl, device=local, chol_kernel=chol)
     M = h.M
     elements = M * (M + 1) // 2
     K = wl["bins"]["n_chi"] * wl["bins"]["n_mass"] * max(1, wl["bins"].get("n_conc", 0))
@@ -887,25 +917,46 @@ def run_ours(args):
         del Ct
     torch.cuda.empty_cache()
     if not args.no_snr_run and packed and rank == 0:
-        # the S/N stage (a dense FP64 Cholesky per vector) on the 5-bin workload,
-        # timed in the same run with its error against the FP64 form
+        # the S/N stage (a dense FP64-accurate Cholesky per vector, P, B and
+        # joint) on a workload whose dense square fits, timed in the same run,
+        # with its error against the FP64 form and against the oracle's stored S/N
         wl2 = workloads.get(args.snr_workload)
-        h2 = Handle(wl2, device=local)
+        h2 = Handle(wl2, device=local, chol_kernel=chol)
         s2 = torch.cuda.Stream(device=dev)
         with torch.cuda.stream(s2):
-            r2 = dense_run(h2, wl2, dict(wl2["cosmology"]), prec, s2, 3, 3, 1, True)
+            r2 = dense_run(h2, wl2, dict(wl2["cosmology"]), prec, s2, 3, 2, 1, True, fp64_steps=1)
         st = r2["stages"]
-        M2 = h2.M
+        M2 = h2.n_P + h2.n_B
         chol_ms = st["snr_cholesky"][0] / 3
         out["snr_stage"] = {
-            "workload": args.snr_workload, "M": M2, "ms_per_full_step": r2["ms_per_step"],
+            "workload": args.snr_workload, "M": M2, "n_P": h2.n_P, "n_B": h2.n_B,
+            "ms_per_full_step": r2["ms_per_step"],
             "full_step_elements_per_s": M2 * (M2 + 1) // 2 / (r2["ms_per_step"] / 1e3),
             "snr_ms_per_step": sum(st[k][0] for k in ("snr_pack", "snr_cholesky", "snr_prefix")) / 3,
             "cholesky_ms_per_step": chol_ms,
             "cholesky_fp64_equivalent_tflops": sum(m ** 3 / 3.0 for m in (h2.n_P, h2.n_B, M2)) / (chol_ms / 1e3) / 1e12,
             "snr_rel_err_vs_fp64_form": r2.get("snr_rel_err_vs_fp64_form"),
             "snr_joint_max": float(np.nanmax(r2["snr"][2]))}
+        ref = stored_oracle_snr(args.snr_workload)
+        if ref is not None:
+            out["snr_stage"]["snr_rel_err_vs_oracle"] = {
+                "split_bf16": max(max_rel(r2["snr"][k], ref[t]) for k, t in enumerate("PBJ")),
+                "fp64_form": (max(max_rel(r2["fp64"]["snr"][k], ref[t]) for k, t in enumerate("PBJ"))
+                              if "fp64" in r2 else None),
+                "oracle": "tests/golden/snr_%s.txt (oracle FP64 covariance, scipy Cholesky)" % args.snr_workload}
+        if "fp64" in r2:
+            out["snr_stage"]["fp64_form_ms_per_full_step"] = r2["fp64"]["ms_per_step"]
         h2.close()
+        del r2
+        torch.cuda.empty_cache()
+    if not args.no_snr_10bin and packed and rank == 0 and world == 1:
+        # the joint S/N of the bench's own workload: a cumulative-order handle
+        # assembles the packed tiles (plus the data row) and factorises them in place
+        res = snr_tiles_run(workloads.get(args.workload), prec, local, [("joint", N.COV_ROWS_JOINT)], chol)
+        j = res["joint"]
+        out["snr_10bin"] = dict(j, precision=prec_name, workload=args.workload,
+                                note="joint vector; P-only and B-only with --snr-10bin")
+        torch.cuda.empty_cache()
     if not args.no_batch and packed and rank == 0 and world == 1:
         out["fisher_batch"] = batch_run(prec, local, [int(x) for x in args.batch_bins.split(",") if x])
     if args.snr_10bin and rank == 0 and world == 1:
@@ -913,7 +964,7 @@ def run_ours(args):
         sp = prec if args.snr_precision == "auto" else (N.COV_FP64 if args.snr_precision == "fp64" else
                                                          N.COV_SPLIT_BF16)
         out["snr_tiles"] = snr_tiles_run(workloads.get(args.workload), sp, local,
-                                         [(r, sets[r]) for r in args.snr_rows.split(",") if r])
+                                         [(r, sets[r]) for r in args.snr_rows.split(",") if r], chol)
         out["snr_tiles"]["precision"] = "fp64" if sp == N.COV_FP64 else "split_bf16"
     # optional stages: a failure is recorded in the line instead of losing it
     if args.model_a and rank == 0 and world == 1:

@@ -120,9 +120,15 @@ typedef struct {
   int tc_kernel;     /* split-form contraction kernel: COV_TC_AUTO (CTA pairs */
                      /* where 2-CTA clusters fit) or COV_TC_SINGLE (one CTA   */
                      /* per 256 x 256 tile); both give the same sums          */
+  int chol_kernel;   /* Cholesky trailing update (cov_snr, cov_snr_tiles):    */
+                     /* COV_CHOL_AUTO (persistent, 128 x 32 tiles, epilogue   */
+                     /* overlapping the next tile's MMAs) or COV_CHOL_TILE    */
+                     /* (one CTA per 128 x 64 tile); bit-identical results    */
 } cov_opts;
 #define COV_TC_AUTO 0
 #define COV_TC_SINGLE 1
+#define COV_CHOL_AUTO 0
+#define COV_CHOL_TILE 1
 
 typedef struct cov_handle cov_handle;
 

@@ -310,7 +310,7 @@ int wl_request_bytes(const cov_nz* nz, const cov_bins* bins, int precision, unsi
       b += 2 * pad256(nt) * kpad(K) * 2 + nt * 8 +
            (size_t)h.nl * (h.nl + 1) / 2 * (K * 4 + nchi * 12);   // BF16 rows, pair signatures
   }
-  b += (M + 1) * (M + 1) * 8 + 2 * ((wl_chol_tc_bytes((int64_t)M + 1) + 255) / 256 * 256) + M * 4;
+  b += (M + 8) * (M + 1) * 8 + 2 * ((wl_chol_tc_bytes((int64_t)M + 1) + 255) / 256 * 256) + M * 4;
   size_t t = (std::max(M, nt) + 255) / 256 + 1;
   b += WL_TILE_CACHE * (t * (t + 1) / 2) * 8;                    // launch-order ring
   b += (size_t)64 << 20;                                         // small buffers, allocation granularity
@@ -338,6 +338,7 @@ extern "C" int cov_init(const cov_cosmology* cosmo, const cov_nz* nz, const cov_
   h->row_set = opts ? opts->rows : COV_ROWS_JOINT;
   h->row_order = opts ? opts->order : COV_ORDER_NATURAL;
   h->tc_kernel = (opts && opts->tc_kernel == COV_TC_SINGLE) ? 0 : -1;
+  h->chol_kernel = (opts && opts->chol_kernel == COV_CHOL_TILE) ? 1 : 0;
   if (h->row_set < 0 || h->row_set > 2 || h->row_order < 0 || h->row_order > 1) {
     g_init_err = "invalid row set or row order";
     delete h;

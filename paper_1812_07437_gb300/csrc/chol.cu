@@ -94,6 +94,53 @@ __global__ void k_potrf_diag(OutMap W, int64_t k0, int kb, int* status) {
     }
 }
 
+// The same factorisation with the rank-1 updates enumerated through a table:
+// the pairs (i, l), l <= i < 64, ordered by l descending, so that step j's
+// active pairs (l > j) are the first T_j = (63 - j)(64 - j) / 2 entries.  All
+// 256 threads work on active elements only (a warp-wide FP64 instruction
+// costs the same with idle lanes), with one shared-memory read to decode.
+__global__ void __launch_bounds__(256) k_potrf_table(OutMap W, int64_t k0, int kb, int* status) {
+  __shared__ double L[NB][NB + 1];
+  __shared__ uint16_t pr[NB * (NB + 1) / 2];
+  __shared__ double inv_sh;
+  // pair table: l = 63, 62, ..., 0; for each l, i = l .. 63
+  for (int l = 0; l < NB; ++l) {
+    const int base = (NB - 1 - l) * (NB - l) / 2;  // entries before column l (columns l+1..63)
+    for (int i = l + (int)threadIdx.x; i < NB; i += blockDim.x) pr[base + (i - l)] = (uint16_t)(i | (l << 8));
+  }
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int i = e >> 6, l = e & 63;
+    L[i][l] = (i < kb && l <= i) ? *W.at(k0 + i, k0 + l) : 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    if (threadIdx.x == 0) {
+      double d = L[j][j];
+      if (!(d > 0.0)) {
+        atomicExch(status, 1);
+        d = 1.0;
+      }
+      const double r = sqrt(d);
+      L[j][j] = r;
+      inv_sh = 1.0 / r;  // one FP64 division per step, shared by all threads
+    }
+    __syncthreads();
+    const double inv = inv_sh;
+    for (int i = j + 1 + (int)threadIdx.x; i < kb; i += blockDim.x) L[i][j] *= inv;
+    __syncthreads();
+    const int tj = (NB - 1 - j) * (NB - j) / 2;  // active pairs: l > j
+    for (int e = threadIdx.x; e < tj; e += blockDim.x) {
+      const int pe = pr[e], i = pe & 255, l = pe >> 8;
+      L[i][l] -= L[i][j] * L[l][j];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int i = e >> 6, l = e & 63;
+    if (i < kb && l <= i) *W.at(k0 + i, k0 + l) = L[i][l];
+  }
+}
+
 #define TRSM_ROWS 32
 // rows r in [r0, r1): x L11^T = a by forward substitution, one row per lane
 // (32 rows per block): every lane runs the whole recurrence of its own row in
@@ -238,7 +285,7 @@ static int factor_and_prefix(cov_handle* h, OutMap Wm, int64_t Ms, const int64_t
   uint8_t* bufs[2] = {(uint8_t*)h->chol_scratch, (uint8_t*)h->chol_scratch + one_buf};
   auto panel = [&](int64_t k0, cudaStream_t st_) -> int {
     int kb = (int)std::min<int64_t>(NB, Ms - k0);
-    k_potrf_diag<<<1, 256, 0, st_>>>(Wm, k0, kb, st);
+    k_potrf_table<<<1, 256, 0, st_>>>(Wm, k0, kb, st);
     int64_t r0 = k0 + kb, r1 = Ms + 1;
     if (r1 > r0)
       k_trsm_rows4<<<(unsigned)(((r1 - r0) * 4 + TR4_THREADS - 1) / TR4_THREADS), TR4_THREADS, 0, st_>>>(Wm, k0, kb,
@@ -340,8 +387,10 @@ int wl_snr(cov_handle* h, const double* C, int64_t ldc, const double* D, int whi
       for (int c = 0; c < h->nl; ++c) h_snr[c] = nan("");
     return COV_OK;
   }
-  int64_t ldw = Ms + 1;
-  int64_t need = ldw * ldw;
+  // rows padded to 8 doubles: the trailing update moves FP64 tiles by TMA,
+  // which needs 16-byte row strides
+  int64_t ldw = (Ms + 1 + 7) / 8 * 8;
+  int64_t need = ldw * (Ms + 1);
   if (need > h->work_n) {
     if (h->work) {
       cudaFree(h->work);

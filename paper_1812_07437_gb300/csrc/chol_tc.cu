@@ -97,6 +97,14 @@ __device__ __forceinline__ uint64_t cs_desc_sw128(uint32_t saddr) {
   return d;
 }
 
+// 32 lanes x 8 columns of TMEM into registers; the caller issues
+// tcgen05.wait::ld before using them
+__device__ __forceinline__ void cs_tmem_ld8_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+
 // 32 lanes x 16 columns of TMEM into registers; the caller issues
 // tcgen05.wait::ld before using them
 __device__ __forceinline__ void cs_tmem_ld16_nowait(uint32_t taddr, uint32_t* r) {
@@ -142,6 +150,27 @@ __device__ __forceinline__ double scaled_to_double(long long a, int ex) {
   int e = msb + ex + 1023;
   if (e <= 0 || e >= 2047) return ldexp((double)a, ex);
   return __longlong_as_double((long long)(sign | ((unsigned long long)e << 52) | (m & ((1ull << 52) - 1))));
+}
+
+// RN(a) 2^ex as an FP64 value for 0 < |a| < 2^63, without branches on the
+// value: normalise |a| so that its leading bit is bit 63, keep the 53 leading
+// bits rounded to nearest (ties to even), and add the rounded significand
+// (2^52 <= r <= 2^53) to the biased exponent field, which carries a rounding
+// overflow into the exponent by itself.  Results outside the normal range take
+// the FP64 path.
+__device__ __forceinline__ double scaled_to_double_rn(long long a, int ex) {
+  if (a == 0) return 0.0;
+  const unsigned long long sign = (unsigned long long)a & (1ull << 63);
+  const unsigned long long u = a < 0 ? 0ull - (unsigned long long)a : (unsigned long long)a;
+  const int lz = __clzll((long long)u);
+  const unsigned long long mn = u << lz;
+  const unsigned long long r0 = mn >> 11;
+  const unsigned long long rb = (mn >> 10) & 1ull;
+  const unsigned long long sticky = ((mn & 0x3FFull) != 0ull) | (r0 & 1ull);
+  const unsigned long long r = r0 + (rb & sticky);
+  const int e = (63 - lz) + ex + 1023;
+  if (e <= 0 || e >= 2046) return ldexp((double)a, ex);
+  return __longlong_as_double((long long)(sign | (((unsigned long long)(e - 1) << 52) + r)));
 }
 
 // Lower tiles of one update launch, row by row: tile row ti (128 rows, from
@@ -343,6 +372,344 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
+// ---------------------------------------------------------------- persistent update
+// The same exact-slicing update as k_chol_update, restructured so that the
+// tensor cores, the exact recombination and the FP64 read-modify-write of
+// different tiles overlap:
+//
+//  * tiles are 128 x 32, aligned to absolute multiples of 128 rows and 32
+//    columns of the workspace, so every tile lies inside one 256 x 256 storage
+//    tile of the lower-packed layout (or inside the dense rows): its FP64
+//    values move by TMA, in as two 128 x 16 boxes with the 128-byte swizzle
+//    (a thread then reads and writes its own row without bank conflicts), and
+//    back out by TMA stores.  The slices of the panel rows are stored from the
+//    128-aligned row sbase <= r0, with zero slices for rows outside [r0, r1),
+//    so rows and columns outside the trailing matrix get a zero update;
+//    elements above the diagonal are computed and stored into storage no
+//    kernel reads (the upper part of diagonal storage tiles, or of the dense
+//    rows);
+//  * one persistent CTA per SM takes a contiguous range of the launch's tiles
+//    (row block by row block, columns left to right), so the six 128 x 64
+//    slices of a row block (96 KB) load once per row block;
+//  * warp 0 / lane 0 loads (row-block slices, per tile the six 32 x 64 column
+//    slices and the FP64 tile, each double-buffered); warp 1 / lane 0 issues
+//    the 84 MMAs of a tile (M = 128, N = 32) into one of two TMEM accumulator
+//    sets (6 x 32 columns each); warps 2-5 recombine a finished set exactly,
+//    subtract from the FP64 tile in shared memory and store it, while the
+//    MMAs of the next tile run in the other set.
+// Every product is exact and so is every FP32 group sum, so the result is
+// bit for bit that of k_chol_update.
+#define PU_BJ 32                                   // tile columns
+#define PU_IBYTES (CS_BI * CS_K * 2)               // 16 KB: one 128 x 64 row-block slice
+#define PU_JBYTES (PU_BJ * CS_K * 2)               // 4 KB: one 32 x 64 column slice
+#define PU_CBOX (CS_BI * 16 * 8)                   // 16 KB: 128 rows x 16 FP64
+#define PU_OFF_J (CS_S * PU_IBYTES)                // 96 KB
+#define PU_OFF_C (PU_OFF_J + 2 * CS_S * PU_JBYTES) // 144 KB
+#define PU_SMEM (PU_OFF_C + 2 * 2 * PU_CBOX + 1024)
+#define PU_EPI 16         // epilogue warps: four per TMEM lane quarter, 8 columns each
+#define PU_THREADS (64 + 32 * PU_EPI)
+
+struct UpdRange {
+  int64_t sbase;       // first row of the slice buffer (a multiple of 128)
+  int64_t r0, r1;      // trailing rows [r0, r1) (r0 a multiple of 64)
+  int64_t ib0, ib1;    // row blocks [ib0, ib1) (absolute, 128 rows)
+  int64_t jc0, jc1;    // column tiles [jc0, jc1) (absolute, 32 columns)
+  int64_t padS;        // rows per slice in the slice buffer
+  int64_t ntiles;      // tiles of the launch
+  int64_t tile0;       // first storage tile of W (lower-packed layout)
+  int tiled;           // W layout: lower-packed 256 x 256 tiles (1) or dense rows (0)
+};
+
+// column tiles of row block ib: [jc0, min(jc1, last column tile at or below the
+// block's last row, last column tile of the trailing matrix) ]
+__device__ __forceinline__ int64_t pu_jhi(const UpdRange& u, int64_t ib) {
+  int64_t j = 4 * ib + 3;
+  const int64_t jr = (u.r1 - 1) >> 5;
+  if (j > jr) j = jr;
+  if (j > u.jc1 - 1) j = u.jc1 - 1;
+  return j;
+}
+
+__device__ __forceinline__ void pu_tma_load(const CUtensorMap* map, uint64_t* bar, void* dst, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          cs_smem_u32(dst)),
+      "l"((uint64_t)map), "r"(cs_smem_u32(bar)), "r"(c0), "r"(c1)
+      : "memory");
+}
+__device__ __forceinline__ void pu_tma_store(const CUtensorMap* map, const void* src, int c0, int c1) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"((uint64_t)map),
+               "r"(cs_smem_u32(src)), "r"(c0), "r"(c1)
+               : "memory");
+}
+__device__ __forceinline__ void pu_init(uint64_t* bar, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(cs_smem_u32(bar)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void pu_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cs_smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void pu_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(cs_smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void pu_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(cs_smem_u32(bar))
+               : "memory");
+}
+// bounded wait that also gives up once any CTA has raised the status word
+__device__ __forceinline__ bool pu_wait(uint64_t* bar, uint32_t parity, int* status) {
+  for (uint32_t i = 0; i < CS_SPIN; ++i) {
+    if (cs_try(bar, parity)) return true;
+    if ((i & 1023u) == 1023u && *(volatile int*)status) return false;
+  }
+  atomicExch(status, 1);
+  return false;
+}
+
+// storage coordinates of FP64 element (r, c) for the tile maps: x = column
+// inside the storage row, y = storage row
+__device__ __forceinline__ void pu_coord(const UpdRange& u, int64_t r, int64_t c, int* x, int* y) {
+  if (u.tiled) {
+    const int64_t ti = r >> 8, tj = c >> 8;
+    *x = (int)(c & 255);
+    *y = (int)(((ti * (ti + 1) / 2 + tj - u.tile0) << 8) + (r & 255));
+  } else {
+    *x = (int)c;
+    *y = (int)r;
+  }
+}
+
+__global__ void __launch_bounds__(PU_THREADS, 1)
+    k_chol_upd(const __grid_constant__ CUtensorMap map_i, const __grid_constant__ CUtensorMap map_j,
+               const __grid_constant__ CUtensorMap map_c, const int* __restrict__ rexp, UpdRange u, int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t i_full, i_empty, j_full[2], j_empty[2], c_full[2], c_empty[2], t_full[2],
+      t_empty[2], e_done[2], mma_done;
+  __shared__ uint32_t tmem_sh;
+  __shared__ int64_t start_ib, start_jb;
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // this CTA's tiles [x0, x1) of the launch, in row-block order
+  const int64_t x0 = u.ntiles * blockIdx.x / gridDim.x, x1 = u.ntiles * (blockIdx.x + 1) / gridDim.x;
+  if (threadIdx.x == 0) {
+    int64_t ib = u.ib0, x = 0;
+    for (;; ++ib) {
+      const int64_t n = pu_jhi(u, ib) - u.jc0 + 1;
+      if (n > 0 && x + n > x0) break;
+      if (n > 0) x += n;
+    }
+    start_ib = ib;
+    start_jb = u.jc0 + (x0 - x);
+    pu_init(&i_full, 1);
+    pu_init(&i_empty, 1);
+    for (int b = 0; b < 2; ++b) {
+      pu_init(&j_full[b], 1);
+      pu_init(&j_empty[b], 1);
+      pu_init(&c_full[b], 1);
+      pu_init(&c_empty[b], 1);
+      pu_init(&t_full[b], 1);
+      pu_init(&t_empty[b], PU_EPI);  // one arrival per epilogue warp
+      pu_init(&e_done[b], PU_EPI);   // one arrival per epilogue warp: the tile's values are in shared memory
+    }
+    pu_init(&mma_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(cs_smem_u32(&tmem_sh)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_sh;
+  const int64_t n_my = x1 - x0;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- producer
+    int64_t ib = start_ib, jb = start_jb, jh = pu_jhi(u, ib);
+    int64_t nib = 0;  // row blocks loaded so far
+    bool ok = true;
+    for (int64_t t = 0; t < n_my && ok; ++t) {
+      if (t == 0 || jb == u.jc0) {  // a new row block: its six slices
+        if (!pu_wait(&i_empty, (uint32_t)(nib & 1) ^ 1u, status)) break;
+        pu_expect(&i_full, CS_S * PU_IBYTES);
+        const int yi = (int)(ib * CS_BI - u.sbase);
+        for (int k = 0; k < CS_S; ++k)
+          pu_tma_load(&map_i, &i_full, smem + k * PU_IBYTES, 0, (int)(k * u.padS) + yi);
+        ++nib;
+      }
+      const int b = (int)(t & 1);
+      const uint32_t ph = (uint32_t)((t >> 1) & 1);
+      if (!pu_wait(&j_empty[b], ph ^ 1u, status)) break;
+      pu_expect(&j_full[b], CS_S * PU_JBYTES);
+      const int yj = (int)(jb * PU_BJ - u.sbase);
+      for (int k = 0; k < CS_S; ++k)
+        pu_tma_load(&map_j, &j_full[b], smem + PU_OFF_J + (b * CS_S + k) * PU_JBYTES, 0, (int)(k * u.padS) + yj);
+      if (!pu_wait(&c_empty[b], ph ^ 1u, status)) break;
+      pu_expect(&c_full[b], 2 * PU_CBOX);
+      for (int h = 0; h < 2; ++h) {
+        int x, y;
+        pu_coord(u, ib * CS_BI, jb * PU_BJ + 16 * h, &x, &y);
+        pu_tma_load(&map_c, &c_full[b], smem + PU_OFF_C + (2 * b + h) * PU_CBOX, x, y);
+      }
+      if (++jb > jh) {
+        ++ib;
+        jh = pu_jhi(u, ib);
+        jb = u.jc0;
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issue
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(PU_BJ >> 3) << 17) |
+                           ((uint32_t)(CS_BI >> 4) << 24);
+    const uint32_t base_i = cs_smem_u32(smem);
+    int64_t ib = start_ib, jb = start_jb, jh = pu_jhi(u, ib), nib = 0;
+    for (int64_t t = 0; t < n_my; ++t) {
+      if (t == 0 || jb == u.jc0) {
+        if (t > 0) pu_commit(&i_empty);  // the previous row block's slices are free once its MMAs finish
+        if (!pu_wait(&i_full, (uint32_t)(nib & 1), status)) break;
+        ++nib;
+      }
+      const int b = (int)(t & 1);
+      const uint32_t ph = (uint32_t)((t >> 1) & 1);
+      if (!pu_wait(&j_full[b], ph, status)) break;
+      if (!pu_wait(&t_empty[b], ph ^ 1u, status)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t base_j = cs_smem_u32(smem + PU_OFF_J + b * CS_S * PU_JBYTES);
+      const uint32_t tset = tmem + (uint32_t)(b * CS_S * PU_BJ);
+#pragma unroll 1
+      for (int k = 0; k < CS_K / 16; ++k)
+#pragma unroll
+        for (int r = 0; r < CS_S; ++r)
+#pragma unroll
+          for (int g = r; g < CS_S; ++g) {
+            const uint32_t dt = tset + (uint32_t)(g * PU_BJ);
+            const uint64_t ad = cs_desc_sw128(base_i + r * PU_IBYTES + k * 32);
+            const uint64_t bd = cs_desc_sw128(base_j + (g - r) * PU_JBYTES + k * 32);
+            const uint32_t acc = (k == 0 && r == 0) ? 0u : 1u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, "
+                "p;\n}\n" ::"r"(dt),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                : "memory");
+          }
+      pu_commit(&j_empty[b]);
+      pu_commit(&t_full[b]);
+      if (++jb > jh) {
+        ++ib;
+        jh = pu_jhi(u, ib);
+        jb = u.jc0;
+      }
+    }
+    // every MMA of this CTA has completed before its TMEM is released
+    pu_commit(&mma_done);
+    for (uint32_t i = 0; i < CS_SPIN && !cs_try(&mma_done, 0u); ++i) {
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue: warp w owns TMEM lanes / tile rows 32 (w % 4) ..
+    // and the 8-column quarter cq = (w - 2) / 4 of the tile.  Every wait is
+    // taken by lane 0 and its outcome shared with the warp, so a warp leaves
+    // its loop as a whole (the TMEM loads are warp-collective) and no wait is
+    // unbounded.
+    const int q = warp & 3, cq = (warp - 2) >> 2;
+    const int row = q * 32 + lane;
+    int64_t ib = start_ib, jb = start_jb, jh = pu_jhi(u, ib);
+    for (int64_t t = 0; t < n_my; ++t) {
+      const int b = (int)(t & 1);
+      const uint32_t ph = (uint32_t)((t >> 1) & 1);
+      int ok = 1;
+      if (lane == 0) ok = pu_wait(&t_full[b], ph, status) && pu_wait(&c_full[b], ph, status);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      __syncwarp();
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint32_t rr[CS_S][8];
+#pragma unroll
+      for (int g = 0; g < CS_S; ++g)
+        cs_tmem_ld8_nowait(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * CS_S * PU_BJ + g * PU_BJ + cq * 8),
+                           rr[g]);
+      const int64_t gr = ib * CS_BI + row;  // absolute row of this thread
+      const int ei = (gr >= u.r0 && gr < u.r1) ? rexp[gr - u.sbase] : 0;
+      const int64_t gj0 = jb * PU_BJ + 8 * cq;
+      // the 8 column exponents of this quarter, one per lane, shared by shuffles
+      const int64_t gcl = gj0 + (lane & 7);
+      const int ejl = (gcl >= u.r0 && gcl < u.r1) ? __ldg(rexp + (gcl - u.sbase)) : 0;
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int g = 0; g < CS_S; ++g)
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) asm volatile("" : "+r"(rr[g][jj]));
+      double* cb = (double*)(smem + PU_OFF_C + (2 * b + (cq >> 1)) * PU_CBOX);
+#pragma unroll
+      for (int jq = 0; jq < 4; ++jq) {
+        double v[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int jj = 2 * jq + e;
+          // the group sums are exact FP32 integers (|A_g| < 2^23): A_0 2^40 + ... + A_5
+          const int p0 = __float2int_rz(__uint_as_float(rr[0][jj])) * 256 + __float2int_rz(__uint_as_float(rr[1][jj]));
+          const int p1 = __float2int_rz(__uint_as_float(rr[2][jj])) * 256 + __float2int_rz(__uint_as_float(rr[3][jj]));
+          const int p2 = __float2int_rz(__uint_as_float(rr[4][jj])) * 256 + __float2int_rz(__uint_as_float(rr[5][jj]));
+          const long long a = ((long long)p0 << 32) + ((long long)p1 << 16) + (long long)p2;
+          const int ej = __shfl_sync(0xffffffffu, ejl, jj);
+          v[e] = scaled_to_double_rn(a, ei + ej - 54);
+        }
+        // 128-byte swizzle: 16-byte chunk jp of row `row` sits at chunk jp ^ (row & 7)
+        const int jp = 4 * (cq & 1) + jq;
+        double2* p = (double2*)(cb + row * 16) + (jp ^ (row & 7));
+        double2 c2 = *p;
+        c2.x -= v[0];
+        c2.y -= v[1];
+        *p = c2;
+      }
+      // the accumulator set is free for the MMAs of tile t + 2, and this
+      // warp's values are in shared memory, visible to the bulk copy
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        pu_arrive(&t_empty[b]);
+        pu_arrive(&e_done[b]);
+      }
+      if (warp == 2) {
+        // warp 2 stores the tile once every epilogue warp has written its values
+        int ok2 = 1;
+        if (lane == 0) ok2 = pu_wait(&e_done[b], ph, status);
+        ok2 = __shfl_sync(0xffffffffu, ok2, 0);
+        __syncwarp();
+        if (!ok2) break;
+        if (lane == 0) {
+          for (int hh = 0; hh < 2; ++hh) {
+            int x, y;
+            pu_coord(u, ib * CS_BI, jb * PU_BJ + 16 * hh, &x, &y);
+            if (u.tiled || x < u.r1) pu_tma_store(&map_c, smem + PU_OFF_C + (2 * b + hh) * PU_CBOX, x, y);
+          }
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // the buffer may be refilled now
+          pu_arrive(&c_empty[b]);
+        }
+        __syncwarp();
+      }
+      if (++jb > jh) {
+        ++ib;
+        jh = pu_jhi(u, ib);
+        jb = u.jc0;
+      }
+    }
+    if (warp == 2 && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // stores complete
+  }
+  __syncwarp();
+  // after an expired wait some copies may still be in flight: a bounded
+  // pause (~1 ms) lets them land before the CTA's shared memory is released
+  if (warp == 0 && lane == 0 && *(volatile int*)status != 0)
+    for (int i = 0; i < 1000; ++i) __nanosleep(1000);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
 static PFN_cuTensorMapEncodeTiled_v12000 cs_encode() { return wl_encode_tiled(); }
 
 static int cs_map(cov_handle* h, CUtensorMap* map, void* base, int64_t total_rows, int box_rows) {
@@ -359,16 +726,77 @@ static int cs_map(cov_handle* h, CUtensorMap* map, void* base, int64_t total_row
   return COV_OK;
 }
 
-// bytes of one slice buffer for up to n trailing rows
+// bytes of one slice buffer for up to n trailing rows (either kernel's layout:
+// the persistent kernel's rows start up to 64 rows before the trailing matrix)
 size_t wl_chol_tc_bytes(int64_t n) {
-  int64_t pad = (n + CS_BI - 1) / CS_BI * CS_BI;
+  int64_t pad = (n + 64 + CS_BI - 1) / CS_BI * CS_BI;
   return (size_t)CS_S * pad * CS_K * 2 + (size_t)pad * sizeof(int);
+}
+
+// slices of rows sbase + i (i < pad) of the panel columns k0..k0+kb-1, zero for
+// rows outside [r0, r1) (the persistent kernel's 128-aligned layout)
+__global__ void k_chol_slice_abs(const OutMap W, int64_t k0, int kb, int64_t sbase, int64_t r0, int64_t r1,
+                                 int64_t pad, __nv_bfloat16* slices, int* rexp) {
+  int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  int lane = threadIdx.x & 31;
+  if (i >= pad) return;
+  const int64_t r = sbase + i;
+  double x0 = 0.0, x1 = 0.0;
+  if (r >= r0 && r < r1) {
+    const double* row = W.at(r, k0);
+    if (lane < kb) x0 = row[lane];
+    if (lane + 32 < kb) x1 = row[lane + 32];
+  }
+  double mx = fmax(fabs(x0), fabs(x1));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  int e = 0;
+  if (mx > 0.0) frexp(mx, &e);
+  double s0 = ldexp(x0, 7 - e), s1 = ldexp(x1, 7 - e);  // |s| < 128
+  for (int t = 0; t < CS_S; ++t) {
+    double d0 = rint(s0), d1 = rint(s1);
+    s0 = (s0 - d0) * 256.0;
+    s1 = (s1 - d1) * 256.0;
+    __nv_bfloat16* out = slices + ((size_t)t * pad + i) * CS_K;
+    out[lane] = __float2bfloat16_rn((float)d0);
+    out[lane + 32] = __float2bfloat16_rn((float)d1);
+  }
+  if (lane == 0) rexp[i] = e;
+}
+
+// whether the persistent kernel serves this workspace: it addresses the FP64
+// tiles by TMA from the start of the workspace (rows from 0, 16-byte rows)
+static bool pu_usable(const cov_handle* h, const OutMap& W) {
+  if (h->chol_kernel == 1) return false;
+  if (W.row0 != 0 || W.tile0 != 0) return false;
+  return W.tiled || (W.ldc % 2 == 0);
+}
+
+static int pu_num_sms() {
+  static std::once_flag once[WL_MAX_DEVICES];
+  static int n[WL_MAX_DEVICES];
+  int d = 0;
+  cudaGetDevice(&d);
+  if (d < 0 || d >= WL_MAX_DEVICES) return 1;
+  std::call_once(once[d], [&] {
+    n[d] = 1;
+    cudaDeviceGetAttribute(&n[d], cudaDevAttrMultiProcessorCount, d);
+    if (n[d] < 1) n[d] = 1;
+  });
+  return n[d];
 }
 
 // slices of the panel rows r0..r1-1, columns k0..k0+kb-1 of the workspace
 int wl_chol_slice(cov_handle* h, OutMap W, int64_t k0, int kb, int64_t r0, int64_t r1, void* buf, cudaStream_t s) {
   int64_t n = r1 - r0;
   if (n <= 0) return COV_OK;
+  if (pu_usable(h, W)) {
+    const int64_t sbase = r0 / CS_BI * CS_BI, pad = (r1 - sbase + CS_BI - 1) / CS_BI * CS_BI;
+    __nv_bfloat16* slices = (__nv_bfloat16*)buf;
+    int* rexp = (int*)((uint8_t*)buf + (size_t)CS_S * pad * CS_K * 2);
+    k_chol_slice_abs<<<(unsigned)((pad + 7) / 8), 256, 0, s>>>(W, k0, kb, sbase, r0, r1, pad, slices, rexp);
+    WL_LAUNCH(h, "k_chol_slice_abs");
+    return COV_OK;
+  }
   int64_t pad = (n + CS_BI - 1) / CS_BI * CS_BI;
   __nv_bfloat16* slices = (__nv_bfloat16*)buf;
   int* rexp = (int*)((uint8_t*)buf + (size_t)CS_S * pad * CS_K * 2);
@@ -380,10 +808,77 @@ int wl_chol_slice(cov_handle* h, OutMap W, int64_t k0, int kb, int64_t r0, int64
 // Csub (rows/cols r0..r1-1 of the workspace) -= L21 L21^T over the column
 // tiles tj0 .. tj0+ntj-1 (64 columns each; ntj < 0: all remaining), lower
 // triangle only, from the slices in buf
+// The persistent update over the column tiles [jc0, jc1) (32 columns each,
+// absolute) of the trailing rows [r0, r1).
+static int pu_update(cov_handle* h, OutMap W, int64_t r0, int64_t r1, const void* buf, int64_t jc0, int64_t jc1,
+                     int* status, cudaStream_t s) {
+  UpdRange u;
+  u.sbase = r0 / CS_BI * CS_BI;
+  u.r0 = r0;
+  u.r1 = r1;
+  u.padS = (r1 - u.sbase + CS_BI - 1) / CS_BI * CS_BI;
+  u.ib0 = u.sbase / CS_BI;
+  u.ib1 = (r1 - 1) / CS_BI + 1;
+  u.jc0 = jc0;
+  u.jc1 = jc1;
+  u.tile0 = 0;
+  u.tiled = W.tiled;
+  int64_t nt = 0;
+  for (int64_t ib = u.ib0; ib < u.ib1; ++ib) {
+    int64_t j = std::min<int64_t>(std::min<int64_t>(4 * ib + 3, (r1 - 1) >> 5), jc1 - 1);
+    if (j >= jc0) nt += j - jc0 + 1;
+  }
+  u.ntiles = nt;
+  if (nt == 0) return COV_OK;
+  auto fn = cs_encode();
+  if (!fn) return wl_fail(h, COV_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  const int* rexp = (const int*)((const uint8_t*)buf + (size_t)CS_S * u.padS * CS_K * 2);
+  CUtensorMap mi, mj, mc;
+  int rc;
+  if ((rc = cs_map(h, &mi, (void*)buf, CS_S * u.padS, CS_BI))) return rc;
+  if ((rc = cs_map(h, &mj, (void*)buf, CS_S * u.padS, PU_BJ))) return rc;
+  {
+    cuuint64_t dims[2], strides[1];
+    if (W.tiled) {
+      const int64_t T = (r1 + 255) / 256;
+      dims[0] = 256;
+      dims[1] = (cuuint64_t)(T * (T + 1) / 2) * 256;
+      strides[0] = 256 * 8;
+    } else {
+      dims[0] = (cuuint64_t)r1;
+      dims[1] = (cuuint64_t)r1;
+      strides[0] = (cuuint64_t)W.ldc * 8;
+    }
+    cuuint32_t box[2] = {16, (cuuint32_t)CS_BI};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(&mc, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, W.C, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return wl_fail(h, COV_ERR_CUDA, "cuTensorMapEncodeTiled failed (Cholesky FP64 tiles)");
+  }
+  static std::once_flag attr_once[WL_MAX_DEVICES];
+  static int attr_rc[WL_MAX_DEVICES];
+  if (wl_once_per_device(attr_once, attr_rc, [] {
+        return (int)cudaFuncSetAttribute(k_chol_upd, cudaFuncAttributeMaxDynamicSharedMemorySize, PU_SMEM);
+      }) != 0)
+    return wl_fail(h, COV_ERR_CUDA, "cudaFuncSetAttribute(k_chol_upd) failed");
+  const int64_t grid = std::min<int64_t>(pu_num_sms(), nt);
+  k_chol_upd<<<(unsigned)grid, PU_THREADS, PU_SMEM, s>>>(mi, mj, mc, rexp, u, status);
+  WL_LAUNCH(h, "k_chol_upd");
+  return COV_OK;
+}
+
 int wl_chol_update(cov_handle* h, OutMap W, int64_t r0, int64_t r1, const void* buf, int tj0, int ntj, int* status,
                    cudaStream_t s) {
   int64_t n = r1 - r0;
   if (n <= 0) return COV_OK;
+  if (pu_usable(h, W)) {
+    // the 64-column tiles tj0 .. tj0 + ntj - 1 of the trailing matrix are the
+    // 32-column tiles from r0 / 32 + 2 tj0
+    const int64_t jc0 = r0 / PU_BJ + 2 * (int64_t)tj0;
+    const int64_t jc1 = ntj < 0 ? ((int64_t)1 << 40) : jc0 + 2 * (int64_t)ntj;
+    return pu_update(h, W, r0, r1, buf, jc0, jc1, status, s);
+  }
   int64_t pad = (n + CS_BI - 1) / CS_BI * CS_BI;
   int total_tj = (int)((n + CS_BJ - 1) / CS_BJ);
   if (ntj < 0 || tj0 + ntj > total_tj) ntj = total_tj - tj0;

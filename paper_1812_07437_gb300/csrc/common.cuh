@@ -178,6 +178,7 @@ struct cov_handle {
   cov_cosmology* cosmo_d = nullptr;  // the cosmology the kernels read (device copy of cosmo)
   bool deferred = false;  // inside a captured batch step: no host synchronisation, no host-side copies
   bool chol_lookahead = true;  // Cholesky panel look-ahead on the side stream
+  int chol_kernel = 0;         // Cholesky trailing update: 0 persistent (k_chol_upd), 1 one CTA per tile
   int tc_kernel = -1;          // contraction kernel: -1 automatic, 0 one CTA per tile, 1 CTA pairs
   struct Selection {           // cumulative S/N selections (P, B, joint; all rows in place)
     bool ready = false;

@@ -19,10 +19,10 @@ def _stream_ptr(stream):
 
 class Handle:
     def __init__(self, wl, device=0, hbm_budget=0, rows=N.COV_ROWS_JOINT, order=N.COV_ORDER_NATURAL,
-                 tc_kernel=N.COV_TC_AUTO):
+                 tc_kernel=N.COV_TC_AUTO, chol_kernel=N.COV_CHOL_AUTO):
         self.L = N.lib()
         cs, ns, bs = N.structs_from_workload(wl)
-        opts = N.cov_opts(int(device), int(hbm_budget), int(rows), int(order), int(tc_kernel))
+        opts = N.cov_opts(int(device), int(hbm_budget), int(rows), int(order), int(tc_kernel), int(chol_kernel))
         h = C.c_void_p()
         N.check(self.L.cov_init(C.byref(cs), C.byref(ns), C.byref(bs), C.byref(opts), C.byref(h)))
         self.h = h

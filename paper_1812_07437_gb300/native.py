@@ -42,6 +42,8 @@ COV_ORDER_NATURAL = 0
 COV_ORDER_CUMULATIVE = 1
 COV_TC_AUTO = 0
 COV_TC_SINGLE = 1
+COV_CHOL_AUTO = 0
+COV_CHOL_TILE = 1
 
 COV_CONC_DUFFY = 0
 COV_CONC_BULLOCK = 1
@@ -79,7 +81,7 @@ class cov_bins(C.Structure):
 
 class cov_opts(C.Structure):
     _fields_ = [("device", C.c_int), ("hbm_budget", C.c_size_t), ("rows", C.c_int), ("order", C.c_int),
-                ("tc_kernel", C.c_int)]
+                ("tc_kernel", C.c_int), ("chol_kernel", C.c_int)]
 
 
 COV_BATCH_TUNE = 1

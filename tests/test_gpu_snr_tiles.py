@@ -81,3 +81,41 @@ def test_snr_tiles_matches_dense(rows, which, precision):
     assert np.max(np.abs(got[m] / ref[m] - 1)) <= 1e-10
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("rows", [N.COV_ROWS_JOINT, N.COV_ROWS_P])
+def test_snr_tiles_persistent_update_is_bit_identical(rows):
+    """The persistent trailing update (128 x 32 tiles moved by TMA, epilogue
+    overlapping the next tile's MMAs) and the one-CTA-per-tile update form the
+    same exact integer group sums: on the packed tiles of cfg2 (every other
+    panel starts half-way into a 128-row block; a ragged last block) the S/N
+    agree bit for bit."""
+    from paper_1812_07437_gb300.handle import Handle, packed_tiles
+    name = "cfg2_5bin"
+    b = Handle(workloads.get(name), rows=rows, order=N.COV_ORDER_CUMULATIVE)
+    c = Handle(workloads.get(name), rows=rows, order=N.COV_ORDER_CUMULATIVE, chol_kernel=N.COV_CHOL_TILE)
+    Db = torch.zeros(b.M, dtype=torch.float64, device=DEV)
+    b.spectra(Db)
+    Ct = torch.full((packed_tiles(b.M + 1) * 65536,), float("nan"), dtype=torch.float64, device=DEV)
+    b.assemble_band(0, b.M, Ct, N.COV_LAYOUT_TILES, N.COV_TERMS_ALL, N.COV_FP64)
+    Ct2 = Ct.clone()
+    got = b.snr_tiles(Ct, Db)
+    ref = c.snr_tiles(Ct2, Db)
+    assert np.array_equal(got, ref, equal_nan=True)
+    # the factor itself (lower triangle, rows up to the D row) bit for bit
+    T = (b.M + 1 + 255) // 256
+    rr = torch.arange(256, device=DEV)
+    lower_of_diag = rr[:, None] >= rr[None, :]
+    A1, A2 = Ct.view(-1, 256, 256), Ct2.view(-1, 256, 256)
+    for ti in range(T):
+        nr = min(256, b.M + 1 - 256 * ti)
+        for tj in range(ti + 1):
+            k = ti * (ti + 1) // 2 + tj
+            x, y = A1[k, :nr], A2[k, :nr]
+            if tj == ti:
+                x, y = torch.where(lower_of_diag[:nr], x, 0.0), torch.where(lower_of_diag[:nr], y, 0.0)
+            # (M, M), the data row's own diagonal, is never initialised or read
+            nan = torch.isnan(x)
+            assert torch.equal(nan, torch.isnan(y)) and torch.equal(x[~nan], y[~nan]), (ti, tj)
+    b.close()
+    c.close()

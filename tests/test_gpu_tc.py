@@ -144,6 +144,18 @@ def test_cfg2_pair_kernel_equals_one_cta_kernel(cfg2):
     assert float(err.max()) <= 1e-6, f"pair vs one-CTA max normalised diff {float(err.max()):.3e}"
 
 
+def test_cfg2_persistent_cholesky_update_is_bit_identical(cfg2):
+    """Dense cov_snr with the persistent trailing update (the default) and with
+    the one-CTA-per-tile update: the same exact group sums, so the three
+    cumulative S/N are equal bit for bit."""
+    from paper_1812_07437_gb300.handle import Handle
+    h, r, C64, D = cfg2
+    h1 = Handle(workloads.get("cfg2_5bin"), chol_kernel=N.COV_CHOL_TILE)
+    for w in (N.COV_WHICH_P, N.COV_WHICH_B, N.COV_WHICH_JOINT):
+        assert np.array_equal(h.snr(C64, D, w), h1.snr(C64, D, w), equal_nan=True), w
+    h1.close()
+
+
 WHICH = (("P", N.COV_WHICH_P), ("B", N.COV_WHICH_B), ("J", N.COV_WHICH_JOINT))
 
 
