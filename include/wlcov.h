@@ -76,8 +76,9 @@ typedef struct {
 /* Median concentration c(m, z) of the NFW profiles (Sec. 4.1, Sec. 5.4). */
 #define COV_CONC_DUFFY 0   /* Duffy et al. (2008), 200 x mean density: 10.14 (m/2e12)^-0.081 (1+z)^-1.01 */
 #define COV_CONC_BULLOCK 1 /* Bullock et al. (2001), the paper's choice: K a(z)/a_c with nu(F m, a_c) = 1, */
-                           /* F = 0.01, K = 4 (a_c capped at a = 100 where F m never collapses), floored  */
-                           /* at c = 1                                                                    */
+                           /* F = 0.01, K = 4 (a_c capped at a = 100 where F m never collapses); c < 1   */
+                           /* (late-collapsing masses) is allowed: u is then the quadrature of its      */
+                           /* defining integral                                                          */
 
 /* n_ell log-spaced ell bins on [ell_min, ell_max] (Sec. 3.2.1, App. A), sky
  * fraction f_sky, n_chi Gauss-Legendre line-of-sight nodes, n_mass log mass

@@ -17,10 +17,18 @@
   which D(a_c) sigma(F m, z=0) = delta_c (D(1) = 1), F = 0.01, K = 4.0.  a_c
   is the root of the growth ODE's solution on [1e-3, 100]; where F m has not
   collapsed by a = 100 (the growth is then within 0.4% of its asymptote) a_c
-  is taken as 100.  The median is floored at c = 1 (scale radius inside the
-  virial radius): below it the fit is far outside the masses it was calibrated
-  on and the Si/Ci form of u loses ~1/c^2 of its digits.
-* NFW Fourier profile u(k, m, c) in sine/cosine integrals, u(0) = 1.
+  is taken as 100.  No floor: where F m collapses late the median falls far
+  below 1 (to ~0.01 for a_c = 100), which the profile below handles.
+* NFW Fourier profile u(k, m, c), u(0) = 1: the truncated NFW density
+  rho ~ 1/(y (1 + y)^2), y = r/r_s, r <= r_vir = c r_s, transformed with the
+  kernel sin(kr)/(kr) and divided by its mass.  For c >= 1 the closed form in
+  sine/cosine integrals; for c < 1, where that form divides terms that cancel
+  to O(c^2) by ln(1+c) - c/(1+c) ~ c^2/2, the defining integral itself in
+  t = r/r_vir: u = int_0^1 w(t) sinc(K t) dt / int_0^1 w(t) dt with
+  w(t) = t/(1 + c t)^2 and K = k r_vir, both integrals on one composite
+  16-point Gauss-Legendre rule of ceil(K/(2 pi)) equal panels (at least one):
+  every panel spans at most one period of sin(K t) and w is analytic well
+  beyond [0, 1] for c < 1, so the rule is exact to rounding.
 * Concentration scatter (Eq. LogNormC, the paper's "model A"): ln c is
   normal about ln c_bar(m, z) with sigma_lnc (0.18 in the paper).  The c
   integral of Eq. ImunuHalos is taken with an N_c-point Gauss-Hermite rule
@@ -51,7 +59,7 @@ DUFFY_MPIVOT = 2.0e12
 DELTA_VIR = 200.0
 BULLOCK_F = 0.01
 BULLOCK_K = 4.0
-BULLOCK_C_MIN = 1.0
+NFW_C_INTEGRAL = 1.0  # below this concentration u is the quadrature of its defining integral
 A_COLLAPSE_MAX = 100.0
 CONC_DUFFY = 0
 CONC_BULLOCK = 1
@@ -156,8 +164,8 @@ def collapse_epoch(sigma_Fm, cosmo):
 
 
 def bullock_concentration(a_c, z):
-    """Bullock et al. (2001) median c_bar = K a(z) / a_c, floored at BULLOCK_C_MIN."""
-    return np.maximum(BULLOCK_K / ((1.0 + z) * np.asarray(a_c)), BULLOCK_C_MIN)
+    """Bullock et al. (2001) median c_bar = K a(z) / a_c (Sec. 5.4)."""
+    return BULLOCK_K / ((1.0 + z) * np.asarray(a_c))
 
 
 def conc_rule(n_conc, sigma_lnc):
@@ -179,15 +187,43 @@ def nfw_u(k, m, z, rho, c=None):
     """Normalised Fourier transform u(k|m, c) of a truncated NFW profile
     (c defaults to the median concentration c_bar(m, z)).
 
-    u = [sin x (Si((1+c)x) - Si(x)) - sin(cx)/((1+c)x)
-         + cos x (Ci((1+c)x) - Ci(x))] / (ln(1+c) - c/(1+c)),  x = k r_s.
-    scipy.special.sici is the Si/Ci step.
+    c >= 1: u = [sin x (Si((1+c)x) - Si(x)) - sin(cx)/((1+c)x)
+                 + cos x (Ci((1+c)x) - Ci(x))] / (ln(1+c) - c/(1+c)),  x = k r_s,
+    with scipy.special.sici as the Si/Ci step.  c < 1: nfw_u_integral.
     """
     if c is None:
         c = concentration(m, z)
-    rs = r_vir(m, rho) / c
-    x = np.asarray(k, dtype=np.float64) * rs
-    si1, ci1 = sici(x)
-    si2, ci2 = sici((1.0 + c) * x)
-    num = np.sin(x) * (si2 - si1) - np.sin(c * x) / ((1.0 + c) * x) + np.cos(x) * (ci2 - ci1)
-    return num / (np.log(1.0 + c) - c / (1.0 + c))
+    k = np.asarray(k, dtype=np.float64)
+    m = np.asarray(m, dtype=np.float64)
+    c = np.asarray(c, dtype=np.float64)
+    k, m, c = np.broadcast_arrays(k, m, c)
+    scalar = k.ndim == 0
+    k, m, c = np.atleast_1d(k), np.atleast_1d(m), np.atleast_1d(c)
+    rv = r_vir(m, rho)
+    out = np.empty(k.shape)
+    big = c >= NFW_C_INTEGRAL
+    if np.any(big):
+        cb = c[big]
+        x = k[big] * rv[big] / cb
+        si1, ci1 = sici(x)
+        si2, ci2 = sici((1.0 + cb) * x)
+        num = np.sin(x) * (si2 - si1) - np.sin(cb * x) / ((1.0 + cb) * x) + np.cos(x) * (ci2 - ci1)
+        out[big] = num / (np.log(1.0 + cb) - cb / (1.0 + cb))
+    for idx in zip(*np.nonzero(~big)):
+        out[idx] = nfw_u_integral(float(k[idx] * rv[idx]), float(c[idx]))
+    return float(out[0]) if scalar else out
+
+
+_GL16 = np.polynomial.legendre.leggauss(16)
+
+
+def nfw_u_integral(K, c):
+    """u = int_0^1 w(t) sinc(K t) dt / int_0^1 w(t) dt, w(t) = t/(1 + c t)^2:
+    the truncated NFW transform with r = t r_vir (K = k r_vir), on the
+    composite 16-point Gauss-Legendre rule of ceil(K/(2 pi)) panels."""
+    P = max(1, int(math.ceil(K / (2.0 * math.pi))))
+    x, w = _GL16
+    t = ((np.arange(P)[:, None] + 0.5 * (x[None, :] + 1.0)) / P).ravel()
+    wt = np.tile(w, P) * (0.5 / P) * t / (1.0 + c * t) ** 2
+    Kt = K * t
+    return float(np.sum(wt * np.sin(Kt) / Kt) / np.sum(wt))

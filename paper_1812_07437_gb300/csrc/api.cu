@@ -216,7 +216,7 @@ static void free_all(cov_handle* h) {
   if (h->batch_ev) cudaEventDestroy(h->batch_ev);
   h->pending.clear();
   h->pool.clear();
-  void* ptrs[] = {h->gl64x, h->gl64w, h->glkx,    h->glkw,    h->glcx,   h->glcw,   h->scal,      h->chi,
+  void* ptrs[] = {h->gl64x, h->gl64w, h->gl16x,   h->gl16w,   h->glkx,    h->glkw,    h->glcx,   h->glcw,   h->scal,      h->chi,
                   h->wchi,  h->z,     h->D,       h->ell_d,   h->m,      h->om,     h->sig0,      h->dlns,
                   h->f,     h->b1,    h->b2,      h->U,       h->Pl,     h->dPl,    h->Psh,       h->zedges,
                   h->norms, h->W,     h->sigw2,   h->slo_d,   h->shi_d,  h->Nmodes, h->Ntri,      h->rowtab,
@@ -248,6 +248,7 @@ static void init_allocs(cov_handle* h, std::vector<std::pair<void**, size_t>>& a
       {(void**)&h->gl64x, d * WL_N_GL_CHI}, {(void**)&h->gl64w, d * WL_N_GL_CHI},
       {(void**)&h->glkx, d * WL_N_K},       {(void**)&h->glkw, d * WL_N_K},
       {(void**)&h->glcx, d * nchi},         {(void**)&h->glcw, d * nchi},
+      {(void**)&h->gl16x, d * 16},          {(void**)&h->gl16w, d * 16},
       {(void**)&h->scal, d * SC_N},         {(void**)&h->chi, d * nchi},
       {(void**)&h->wchi, d * nchi},         {(void**)&h->z, d * nchi},
       {(void**)&h->D, d * nchi},            {(void**)&h->ell_d, d * nl},

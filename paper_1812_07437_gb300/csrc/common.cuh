@@ -32,7 +32,7 @@
 #define WL_A_INIT 1.0e-3
 #define WL_BULLOCK_F 0.01        // Bullock et al. median: nu(F m, a_c) = 1, c = K a / a_c
 #define WL_BULLOCK_K 4.0
-#define WL_BULLOCK_C_MIN 1.0     // floor of that median: scale radius inside the virial radius
+#define WL_NFW_C_INTEGRAL 1.0    // below this concentration u is the quadrature of its defining integral
 #define WL_A_COLLAPSE_MAX 100.0  // a_c where F m has not collapsed by then
 #define WL_N_K 4096        // nodes of the sigma(R) and sigma_W^2 rules
 #define WL_LNK_MIN (-11.512925464970229)  // ln 1e-5
@@ -116,6 +116,7 @@ struct cov_handle {
   std::vector<int32_t> rowdesc;   // 8 per row
   // device: quadrature nodes on [-1, 1]
   double *gl64x = nullptr, *gl64w = nullptr, *glkx = nullptr, *glkw = nullptr, *glcx = nullptr, *glcw = nullptr;
+  double *gl16x = nullptr, *gl16w = nullptr;  // 16-point rule of the small-concentration profiles
   // device: tables
   double* scal = nullptr;
   double *chi = nullptr, *wchi = nullptr, *z = nullptr, *D = nullptr;
@@ -391,9 +392,33 @@ __device__ __forceinline__ double dev_conc(double m, double z) {
   return WL_DUFFY_A * pow(m / WL_DUFFY_MPIVOT, WL_DUFFY_B) * pow(1.0 + z, WL_DUFFY_C);
 }
 
-// normalised Fourier transform u(k | m, c) of the truncated NFW profile
-__device__ __forceinline__ double dev_nfw_u(double k, double m, double c, double rho) {
+// u(k | m, c) for c < 1 from its defining integral in t = r / r_vir:
+// int_0^1 w(t) sinc(K t) dt / int_0^1 w(t) dt, w(t) = t / (1 + c t)^2,
+// K = k r_vir, both on one composite 16-point Gauss-Legendre rule (x16, w16
+// on [-1, 1]) of ceil(K / (2 pi)) panels: no term cancels, so the result is
+// good to rounding where the closed form loses ~1/c^2 of its digits.
+__device__ __forceinline__ double dev_nfw_u_integral(double K, double c, const double* x16, const double* w16) {
+  const int P = K > 2.0 * WL_PI ? (int)ceil(K / (2.0 * WL_PI)) : 1;
+  const double hp = 1.0 / P;
+  double num = 0.0, den = 0.0;
+  for (int p = 0; p < P; ++p)
+    for (int i = 0; i < 16; ++i) {
+      const double t = (p + 0.5 * (x16[i] + 1.0)) * hp;
+      const double ct = 1.0 + c * t;
+      const double wt = w16[i] * t / (ct * ct);
+      const double Kt = K * t;
+      num += wt * sin(Kt) / Kt;
+      den += wt;
+    }
+  return num / den;
+}
+
+// normalised Fourier transform u(k | m, c) of the truncated NFW profile: the
+// closed form in sine/cosine integrals for c >= 1, the defining integral below
+__device__ __forceinline__ double dev_nfw_u(double k, double m, double c, double rho, const double* x16,
+                                           const double* w16) {
   double rv = cbrt(3.0 * m / (4.0 * WL_PI * WL_DELTA_VIR * rho));
+  if (c < WL_NFW_C_INTEGRAL) return dev_nfw_u_integral(k * rv, c, x16, w16);
   double x = k * rv / c;
   double s1, c1, s2, c2;
   dev_sici(x, &s1, &c1);

@@ -352,11 +352,17 @@ __global__ void k_halo(const cov_cosmology* __restrict__ cosmo_p, int nm, int nc
 
 // NFW profiles on the Limber grid and P_lin, dP_lin/dln k at k = l_b/chi_n
 // at every (mass, concentration) node: u(k | m_q, c_bar(m_q, z_n) exp(cs[j])),
-// c_bar the Duffy fit or the Bullock median max(K / ((1 + z) a_c(m_q)), 1)
+// c_bar the Duffy fit or the Bullock median K / ((1 + z) a_c(m_q))
 __global__ void k_profiles(const cov_cosmology* __restrict__ cosmo_p, cov_bins b, int nm, int nc, const double* cs,
                            const double* ac, const double* ell, const double* chi, const double* z,
-                           const double* D, const double* m, const double* scal, double* U, double* Pl,
-                           double* dPl, double* Psh) {
+                           const double* D, const double* m, const double* scal, const double* gl16x,
+                           const double* gl16w, double* U, double* Pl, double* dPl, double* Psh) {
+  __shared__ double x16[16], w16[16];
+  if (threadIdx.x < 16) {
+    x16[threadIdx.x] = gl16x[threadIdx.x];
+    w16[threadIdx.x] = gl16w[threadIdx.x];
+  }
+  __syncthreads();
   const cov_cosmology c = *cosmo_p;
   int bn = blockIdx.x;  // b * nchi + n
   int nchi = b.n_chi;
@@ -365,10 +371,9 @@ __global__ void k_profiles(const cov_cosmology* __restrict__ cosmo_p, cov_bins b
   bool valid = k <= b.k_max;
   double rho = WL_RHO_CRIT0 * c.Om;
   for (int q = threadIdx.x; q < nm; q += blockDim.x) {
-    double cq = b.conc_model == COV_CONC_BULLOCK ? fmax(WL_BULLOCK_K / ((1.0 + z[n]) * ac[q / nc]), WL_BULLOCK_C_MIN)
-                                                 : dev_conc(m[q], z[n]);
+    double cq = b.conc_model == COV_CONC_BULLOCK ? WL_BULLOCK_K / ((1.0 + z[n]) * ac[q / nc]) : dev_conc(m[q], z[n]);
     if (nc > 1) cq *= exp(cs[q % nc]);
-    U[(size_t)bn * nm + q] = valid ? dev_nfw_u(k, m[q], cq, rho) : 0.0;
+    U[(size_t)bn * nm + q] = valid ? dev_nfw_u(k, m[q], cq, rho, x16, w16) : 0.0;
   }
   if (threadIdx.x < 4) {
     // P_lin at k exp(s), s = -2h, -h, +h, +2h (the 4th-order differences in ln k)
@@ -508,6 +513,7 @@ __global__ void k_sigw2(const cov_cosmology* __restrict__ cosmo_p, double theta,
 // quadrature nodes depend on no cosmology: built once per handle
 int wl_quadrature(cov_handle* h, cudaStream_t s) {
   k_gauss_legendre<<<1, 64, 0, s>>>(WL_N_GL_CHI, h->gl64x, h->gl64w);
+  k_gauss_legendre<<<1, 32, 0, s>>>(16, h->gl16x, h->gl16w);
   k_gauss_legendre<<<(WL_N_K + 127) / 128, 128, 0, s>>>(WL_N_K, h->glkx, h->glkw);
   k_gauss_legendre<<<(h->nchi + 127) / 128, 128, 0, s>>>(h->nchi, h->glcx, h->glcw);
   k_gauss_hermite<<<1, 256, 0, s>>>(h->nc, h->bins.sigma_lnc, h->cs, h->cw);
@@ -529,7 +535,7 @@ int wl_tables(cov_handle* h, cudaStream_t s) {
   if (b.conc_model == COV_CONC_BULLOCK) k_collapse<<<h->nmb, 32, 0, s>>>(c, h->scal, h->sigF, h->ac);
   k_halo<<<h->nchi, 128, 0, s>>>(c, h->nmb, h->nc, h->D, h->mb, h->omb, h->sig0, h->dlns, h->f, h->b1, h->b2);
   k_profiles<<<h->nl * h->nchi, 128, 0, s>>>(c, b, h->nm, h->nc, h->cs, h->ac, h->ell_d, h->chi, h->z, h->D, h->m,
-                                             h->scal, h->U, h->Pl, h->dPl, h->Psh);
+                                             h->scal, h->gl16x, h->gl16w, h->U, h->Pl, h->dPl, h->Psh);
   k_edges<<<1, 64, 0, s>>>(nz, h->zedges, h->scal);
   k_norms<<<h->nt, 64, 0, s>>>(nz, h->zedges, h->gl64x, h->gl64w, h->norms);
   k_kernels<<<h->nchi, 64, 0, s>>>(c, nz, h->nchi, h->chi, h->z, h->zedges, h->norms, h->gl64x, h->gl64w, h->W);
