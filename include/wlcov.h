@@ -285,6 +285,40 @@ const char* cov_stage_name(int stage);
 int cov_snr_noalloc(const double* d_C, int64_t ldc, const double* d_D, int64_t M, const int64_t* prefix,
                     int n_prefix, double* d_snr, int* d_status, void* stream);
 
+/* ---- Principal components of the joint covariance (Sec. 6) ---------------
+ *
+ * Eigen-pairs of the handle's covariance C (Eq. SNPCA: C = sum_a lambda_a v_a
+ * v_a^T), the signal-to-noise of each uncorrelated mode (Eqs. NewObs,
+ * SNperEign: (S/N)^2_a = (v_a . D)^2 / lambda_a) and its cumulative forms
+ * (Eq. CumulSN).  The eigenvalues of these covariances span ~23 decades, so
+ * they come from one-sided Jacobi on the Cholesky factor, which keeps every
+ * eigenvalue to high relative accuracy (in FP64, on the GPU): the factor of
+ * cov_snr (FP64-accurate), then sweeps of plane rotations of column pairs of
+ * L^T in round-robin order until a sweep rotates no pair (at most 60 sweeps).
+ *
+ * d_C: device, M x M FP64 with the lower triangle (the upper is not read),
+ * leading dimension ldc >= M, rows in the handle's order; d_D: device, M.
+ * Host outputs of M values, each optional (NULL): h_lam the eigenvalues in
+ * ascending order; h_snr2 the (S/N)^2 of the mode of each eigenvalue, same
+ * order; h_cum_var the cumulative (S/N)^2 with modes by increasing variance
+ * lambda; h_cum_info the cumulative (S/N)^2 with modes by decreasing (S/N)_a.
+ * *info: M, sweeps, convergence, the total (S/N)^2 (= D^T C^-1 D), the fewest
+ * modes, by decreasing (S/N)_a, whose cumulative S/N reaches 90/95/99% of the
+ * total S/N, and host-clock timings.  The eigenvectors are not returned: the
+ * per-mode S/N comes from the rotated factor and the solved data vector.
+ * Allocates the handle's Cholesky workspace (as cov_snr) and M^2 + 9 M
+ * doubles.  Synchronous.  COV_ERR_NOT_PD as cov_snr; COV_ERR_TIMEOUT if the
+ * sweeps did not converge; COV_ERR_NOMEM beyond hbm_budget. */
+typedef struct {
+  int64_t M;
+  int sweeps, converged;
+  double total_snr2;
+  int modes_90, modes_95, modes_99;
+  double ms_cholesky, ms_jacobi;
+} cov_pca_info;
+int cov_pca(cov_handle* h, const double* d_C, int64_t ldc, const double* d_D, double* h_lam, double* h_snr2,
+            double* h_cum_var, double* h_cum_info, cov_pca_info* info, void* stream);
+
 /* ---- Batched cosmologies: one survey set-up, many cosmologies -------------
  *
  * For each of n cosmologies (cosmos, host array), the data vector (Eq.

@@ -225,7 +225,7 @@ static void free_all(cov_handle* h) {
                   h->C2,    h->C3,    h->tc_status, h->Thi,   h->Tlo,    h->Tscale, h->Trows,     h->Tmat,
                   h->Srows, h->cosmo_d, h->Fsig,  h->Esig,    h->Msig,   h->FsigT,  h->EsigT,     h->MsigT,
                   h->invN,  h->omN,   h->work,    h->chol_scratch, h->chol_status, h->mb, h->omb, h->cs,
-                  h->cw,    h->sigF,  h->ac,      h->bmask,   h->gblk,   h->wait_flag};
+                  h->cw,    h->sigF,  h->ac,      h->bmask,   h->gblk,   h->wait_flag, h->pca_buf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->tile_ring) cudaFree(h->tile_ring);

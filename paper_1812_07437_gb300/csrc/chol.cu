@@ -404,6 +404,7 @@ int wl_snr(cov_handle* h, const double* C, int64_t ldc, const double* D, int whi
     h->work_n = need;
     h->allocated += sizeof(double) * need;
   }
+  h->work_ld = ldw;
   dim3 gp((unsigned)(Ms + 1), (unsigned)((Ms + 1 + 255) / 256));
   int tk = wl_stage_begin(h, ST_SNR_PACK, s);
   k_snr_pack<<<gp, 256, 0, s>>>(Ms, z.perm, C, ldc, D, h->work, ldw);

@@ -167,8 +167,11 @@ struct cov_handle {
   uint16_t *Thi = nullptr, *Tlo = nullptr;  // split trispectrum rows (tensor-core form)
   double* Tscale = nullptr;
   double* Srows = nullptr;  // [M][nchi]
-  double* work = nullptr;   // Cholesky workspace (M+1)^2
+  double* work = nullptr;   // Cholesky workspace (M+1) rows
   int64_t work_n = 0;
+  int64_t work_ld = 0;      // its row length (the last dense cov_snr)
+  void* pca_buf = nullptr;  // PCA: G, y and the per-mode arrays
+  size_t pca_bytes = 0;
   void* chol_scratch = nullptr;  // two slice buffers of the tensor-core trailing update
   size_t chol_scratch_n = 0;
   cudaStream_t side = nullptr;   // look-ahead stream of the Cholesky panel kernels

@@ -106,6 +106,18 @@ class Handle:
                                which, out.ctypes.data_as(C.c_void_p), _stream_ptr(stream)), self.h)
         return out
 
+    def pca(self, Cmat, D, stream=None):
+        """Principal components (Sec. 6): eigenvalues ascending, (S/N)^2 per mode in that order, cumulative
+        (S/N)^2 by increasing variance and by decreasing (S/N)_a, and the info fields (dict)."""
+        M = self.M
+        lam, snr2, cv, ci = (np.zeros(M, dtype=np.float64) for _ in range(4))
+        info = N.cov_pca_info()
+        N.check(self.L.cov_pca(self.h, C.c_void_p(Cmat.data_ptr()), Cmat.stride(0), C.c_void_p(D.data_ptr()),
+                               *(x.ctypes.data_as(C.c_void_p) for x in (lam, snr2, cv, ci)), C.byref(info),
+                               _stream_ptr(stream)), self.h)
+        d = {f: getattr(info, f) for f, _ in N.cov_pca_info._fields_}
+        return {"lam": lam, "snr2": snr2, "cum_var": cv, "cum_info": ci, **d}
+
     def snr_tiles(self, Ct, D, stream=None):
         """In-place cumulative S/N of the handle's rows on its lower-packed tiles (cumulative-order handles)."""
         out = np.zeros(self.n_ell, dtype=np.float64)

@@ -52,7 +52,7 @@ EXPORTED = ["cov_init", "cov_update", "cov_layout", "cov_counts", "cov_spectra",
             "cov_assemble_band", "cov_table", "cov_profile", "cov_stage_times", "cov_stage_name", "cov_snr_noalloc",
             "cov_last_error", "cov_free", "cov_snr_tiles", "cov_batch_snr", "cov_server_create", "cov_server_submit", "cov_server_wait",
             "cov_server_error", "cov_server_stats_get", "cov_server_clock", "cov_request_footprint",
-            "cov_server_free", "cov_wait_selftest"]
+            "cov_server_free", "cov_wait_selftest", "cov_pca"]
 
 COV_REQ_QUEUED = 0
 COV_REQ_RUNNING = 1
@@ -90,6 +90,12 @@ COV_BATCH_TUNE = 1
 class cov_batch_info(C.Structure):
     _fields_ = [("tc_kernel", C.c_int), ("chol_lookahead", C.c_int), ("candidate_ms", C.c_double * 4),
                 ("first_ms", C.c_double), ("capture_ms", C.c_double), ("replay_ms", C.c_double)]
+
+
+class cov_pca_info(C.Structure):
+    _fields_ = [("M", C.c_int64), ("sweeps", C.c_int), ("converged", C.c_int), ("total_snr2", C.c_double),
+                ("modes_90", C.c_int), ("modes_95", C.c_int), ("modes_99", C.c_int), ("ms_cholesky", C.c_double),
+                ("ms_jacobi", C.c_double)]
 
 
 class cov_server_opts(C.Structure):
@@ -144,6 +150,7 @@ def lib():
         L.cov_stage_name.restype = C.c_char_p
         L.cov_snr_noalloc.argtypes = [P, i64, P, i64, P, C.c_int, P, P, P]
         L.cov_wait_selftest.argtypes = [P, C.c_uint, C.c_int, P]
+        L.cov_pca.argtypes = [P, P, i64, P, P, P, P, P, C.POINTER(cov_pca_info), P]
         L.cov_last_error.argtypes = [P]
         L.cov_last_error.restype = C.c_char_p
         L.cov_free.argtypes = [P]
