@@ -57,9 +57,12 @@ def parse():
     p.add_argument("--snr-rows", default="joint,B,P", help="row sets of --snr-10bin")
     p.add_argument("--snr-precision", default="auto", choices=["auto", "fp64", "split_bf16"],
                    help="covariance form of --snr-10bin (auto: the bench's own)")
-    p.add_argument("--serve-requests", type=int, default=24)
+    p.add_argument("--serve-requests", type=int, default=200)
     p.add_argument("--serve-rate", type=float, default=200.0)
-    p.add_argument("--serve-budget-gb", type=float, default=64.0)
+    p.add_argument("--serve-budget-gb", type=float, default=160.0)
+    p.add_argument("--serve-search", action="store_true",
+                   help="binary search for the sustainable arrival rate on the same mix and seed")
+    p.add_argument("--serve-search-requests", type=int, default=100)
     p.add_argument("--serve-slots", type=int, default=4)
     p.add_argument("--precision", default="auto", choices=["auto", "fp64", "split_bf16"])
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -493,6 +496,7 @@ def serving_run(prec, n_req, rate, budget_gb, slots, device, seed=2024):
     srv.close()
     done = [x for x in infos if x["state"] == N.COV_REQ_DONE]
     lat = np.array([x["t_done"] - x["t_submit"] for x in done]) if done else np.array([np.nan])
+    wait = np.array([x["t_start"] - x["t_submit"] for x in done]) if done else np.array([np.nan])
     span = (max(x["t_done"] for x in done) - min(x["t_submit"] for x in infos)) if done else float("nan")
     el = sum(x["M"] * (x["M"] + 1) // 2 for x in done)
     return {"requests": n_req, "offered_rate_hz": rate, "completed": len(done),
@@ -500,10 +504,34 @@ def serving_run(prec, n_req, rate, budget_gb, slots, device, seed=2024):
             "failed": sum(1 for x in infos if x["state"] == N.COV_REQ_FAILED),
             "achieved_rate_hz": len(done) / span, "elements_per_s": el / span, "makespan_s": span,
             "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
-            "latency_max_s": float(np.max(lat)),
+            "latency_max_s": float(np.max(lat)), "queue_wait_p50_s": float(np.percentile(wait, 50)),
+            "queue_wait_p90_s": float(np.percentile(wait, 90)),
             "M_served_max": max((x["M"] for x in done), default=0),
             "reused_resident": sum(x["reused"] for x in done), "max_running": st["max_running"],
             "peak_reserved_gb": st["peak_reserved"] / 1e9, "budget_gb": st["budget"] / 1e9, "slots": slots}
+
+
+def serving_search(prec, n_req, budget_gb, slots, device, lo=0.25, hi=16.0, probes=6):
+    """The highest arrival rate the server sustains on the serving mix (same
+    seed): a rate is sustained when 90% of its requests start within 2 s of
+    their arrival (the queue does not grow); bisection in log rate between lo
+    and hi, each probe a fresh stream of n_req requests."""
+    import math
+    trials = []
+    ok_rate = None
+    for _ in range(probes):
+        r = math.sqrt(lo * hi)
+        sv = serving_run(prec, n_req, r, budget_gb, slots, device)
+        good = sv["completed"] > 0 and sv["queue_wait_p90_s"] <= 2.0 and sv["failed"] == 0
+        trials.append({"offered_rate_hz": r, "sustained": good, "achieved_rate_hz": sv["achieved_rate_hz"],
+                       "queue_wait_p90_s": sv["queue_wait_p90_s"], "latency_p50_s": sv["latency_p50_s"],
+                       "latency_p99_s": sv["latency_p99_s"], "completed": sv["completed"]})
+        if good:
+            lo, ok_rate = r, r
+        else:
+            hi = r
+    return {"sustainable_rate_hz": ok_rate, "criterion": "p90 queue wait <= 2 s", "requests_per_probe": n_req,
+            "probes": trials}
 
 
 def batch_run(prec, device, bins_list):
@@ -530,9 +558,12 @@ def batch_run(prec, device, bins_list):
         total = time.perf_counter() - t0
         el = h.M * (h.M + 1) // 2
         r = {"M": h.M, "total_s": total, "first_ms": info["first_ms"], "capture_ms": info["capture_ms"],
-             "replay_ms_per_cosmology": info["replay_ms"], "tuned": {"tc_kernel": info["tc_kernel"],
-                                                                      "chol_lookahead": info["chol_lookahead"],
-                                                                      "candidate_ms": info["candidate_ms"]},
+             "replay_ms_per_cosmology": info["replay_ms"], "single_graph_launch": bool(info["single_launch"]),
+             "tuned": {"candidate": info["tuned"], "tc_kernel": info["tc_kernel"], "pr_group": info["pr_group"],
+                       "chol_lookahead": info["chol_lookahead"], "chol_kernel": info["chol_kernel"],
+                       "candidate_ms": info["candidate_ms"],
+                       "candidates": ["pairs g8 look-ahead persistent", "pairs g4", "pairs g16", "one CTA per tile",
+                                      "no look-ahead", "one-tile Cholesky update"]},
              "elements_per_s_replays": el / (info["replay_ms"] / 1e3), "snr_joint_fiducial": float(snr[0, 2, -1])}
         if k == 0:
             D = torch.zeros(h.M, dtype=torch.float64, device=dev)
@@ -1027,13 +1058,13 @@ def run_ours(args):
             out["paper_replica"] = {"error": f"{type(e).__name__}: {e}"}
     if not args.no_serve and packed and rank == 0 and world == 1:
         sv = serving_run(prec, args.serve_requests, args.serve_rate, args.serve_budget_gb, args.serve_slots, local)
-        # the same mix offered at about half the rate the first run achieved
-        rate2 = max(0.05, 0.5 * sv["achieved_rate_hz"])
-        sv2 = serving_run(prec, 8, rate2, args.serve_budget_gb, args.serve_slots, local, seed=2025)
-        out["serving"] = {"workload": "Poisson stream, n_t uniform 1..10, n_ell uniform 8..24 on [10, 5000], "
-                                      "cosmology within +-5% of the fiducial, N_chi=128, N_M=96, every term, "
-                                      "covariance + 3 cumulative S/N per request",
-                          "offered": sv, "half_load": sv2}
+        out["serving"] = {"workload": "Poisson stream (seed 2024), n_t uniform 1..10, n_ell uniform 8..24 on "
+                                      "[10, 5000], cosmology within +-5% of the fiducial, N_chi=128, N_M=96, every "
+                                      "term, covariance + 3 cumulative S/N per request",
+                          "offered": sv}
+        if args.serve_search:
+            out["serving"]["search"] = serving_search(prec, args.serve_search_requests, args.serve_budget_gb,
+                                                      args.serve_slots, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
     if rank == 0:

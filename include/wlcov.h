@@ -328,23 +328,34 @@ int cov_pca(cov_handle* h, const double* d_C, int64_t ldc, const double* d_D, do
  * `terms` in `precision`: the Fisher pattern (finite-difference steps around a
  * fiducial cosmology) and emulator training sets.  The first cosmology runs
  * eagerly and prepares everything; with COV_BATCH_TUNE it first runs once per
- * candidate launch configuration (tensor-core contraction in CTA pairs or
- * one CTA per tile; Cholesky with or without panel look-ahead), keeps the
- * fastest for this handle and reports the candidate times in *info.  The
+ * candidate launch configuration (tensor-core contraction in CTA pairs with
+ * three launch-order groupings, or one CTA per tile; Cholesky with or without
+ * panel look-ahead, persistent or one-tile trailing update), keeps the fastest
+ * for this handle and reports the candidate times in *info.  The
  * cosmology-dependent step (tables, spectra, dense covariance, three S/N) is
- * then captured once as a CUDA graph and replayed for the other cosmologies,
- * each after a copy of its parameters to the device; the exact counts are
- * computed once.  Results equal those of cov_update + cov_spectra +
+ * then captured once into the body of a CUDA graph "while" node, between a
+ * kernel that loads cosmology k from a device copy of the list and one that
+ * stores its S/N (and D) and advances k: the other cosmologies run as one
+ * graph launch, a loop on the device.  Where the driver cannot build that
+ * graph, the step is captured alone and replayed once per cosmology
+ * (info->single_launch tells which).  The exact counts are computed once.  Results equal those of cov_update + cov_spectra +
  * cov_assemble + cov_snr for each cosmology.  The handle keeps a dense M x M
  * covariance and the (M + 1)^2 Cholesky workspace.  A non-positive pivot or an
  * expired wait in any cosmology fails the whole batch (COV_ERR_NOT_PD /
  * COV_ERR_TIMEOUT).  Afterwards the handle holds the last cosmology. */
 #define COV_BATCH_TUNE 1u
 
+#define COV_BATCH_CANDIDATES 6
 typedef struct {
   int tc_kernel;          /* contraction kernel used: 1 = CTA pairs, 0 = one CTA per tile, -1 = automatic       */
   int chol_lookahead;     /* 1: Cholesky panel look-ahead on a side stream                                    */
-  double candidate_ms[4]; /* tuning: (pairs, look-ahead), (pairs, none), (one CTA, look-ahead), (one CTA, none) */
+  double candidate_ms[COV_BATCH_CANDIDATES]; /* tuning, eager step per candidate: (pairs, group 8, look-ahead,
+                             persistent update) = the default, then group 4, group 16, one CTA per tile, no
+                             look-ahead, one-tile Cholesky update                                              */
+  int tuned;              /* index of the candidate kept (0 without tuning)                                   */
+  int pr_group;           /* tile rows per group of the pair-tile launch order                                */
+  int chol_kernel;        /* Cholesky trailing update: 0 persistent, 1 one CTA per tile                       */
+  int single_launch;      /* 1: the other cosmologies ran as one graph launch (a device-side loop)            */
   double first_ms;        /* the first cosmology, tuning included                                             */
   double capture_ms;      /* capture and instantiation of the step                                            */
   double replay_ms;       /* per further cosmology (host clock, copies included)                              */

@@ -365,25 +365,33 @@ extern "C" int cov_init(const cov_cosmology* cosmo, const cov_nz* nz, const cov_
   }
   const size_t d = sizeof(double);
   int nl = h->nl;
-  cudaStream_t s = 0;
-  cudaMemcpy(h->ell_d, h->ell.data(), d * nl, cudaMemcpyHostToDevice);
-  cudaMemcpy(h->slo_d, h->s_lo.data(), 8 * nl, cudaMemcpyHostToDevice);
-  cudaMemcpy(h->shi_d, h->s_hi.data(), 8 * nl, cudaMemcpyHostToDevice);
-  if (h->ntri) cudaMemcpy(h->tris_d, h->tris.data(), 4 * h->tris.size(), cudaMemcpyHostToDevice);
-  e = cudaMemcpy(h->rowdesc_d, h->rowdesc.data(), 4 * h->rowdesc.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemset(h->scal, 0, d * SC_N);
-  if (e == cudaSuccess) e = cudaMemcpy(h->cosmo_d, &h->cosmo, sizeof(cov_cosmology), cudaMemcpyHostToDevice);
+  // a private non-blocking stream: the set-up neither waits for nor holds up
+  // work that other threads have on the legacy default stream
+  cudaStream_t s = nullptr;
+  e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->ell_d, h->ell.data(), d * nl, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->slo_d, h->s_lo.data(), 8 * nl, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->shi_d, h->s_hi.data(), 8 * nl, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && h->ntri)
+    e = cudaMemcpyAsync(h->tris_d, h->tris.data(), 4 * h->tris.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->rowdesc_d, h->rowdesc.data(), 4 * h->rowdesc.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->scal, 0, d * SC_N, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->cosmo_d, &h->cosmo, sizeof(cov_cosmology), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) {
     g_init_err = std::string("upload: ") + cudaGetErrorString(e);
+    if (s) {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
     free_all(h);
     delete h;
     return COV_ERR_CUDA;
   }
   if ((rc = wl_quadrature(h, s)) == COV_OK && (rc = wl_tables(h, s)) == COV_OK) rc = wl_counts(h, s);
-  if (rc == COV_OK) {
-    e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) rc = wl_cuda(h, e, "cov_init tables");
-  }
+  e = cudaStreamSynchronize(s);
+  if (rc == COV_OK && e != cudaSuccess) rc = wl_cuda(h, e, "cov_init tables");
+  cudaStreamDestroy(s);
   if (rc != COV_OK) {
     g_init_err = h->err;
     free_all(h);

@@ -320,9 +320,16 @@ static int gather_args(cov_handle* h, unsigned terms, GatherArgs* g, cudaStream_
 
 // The 32 x 32 sub-blocks (lower part) of the diagonal blocks that hold the
 // Gaussian terms: one block per run of consecutive rows of the same type and
-// ell bin (P) or triangle (B).  Built once per handle from the row table.
-static int gauss_blocks(cov_handle* h) {
+// ell bin (P) or triangle (B).  Built once per handle from the row table and
+// uploaded on the stream of the kernel that reads it.
+static int gauss_blocks(cov_handle* h, cudaStream_t s) {
   if (h->gblk) return COV_OK;
+  // a captured step reuses the list of its eager first run: a copy from host
+  // memory cannot become part of a graph
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  WL_CHECK(h, cudaStreamIsCapturing(s, &cap));
+  if (cap != cudaStreamCaptureStatusNone)
+    return wl_fail(h, COV_ERR_INVALID, "Gaussian block list not built before stream capture");
   std::vector<int4> v;
   h->gblk_row.clear();
   const int64_t M = h->M;
@@ -344,7 +351,11 @@ static int gauss_blocks(cov_handle* h) {
   int rc;
   if ((rc = ensure(h, (void**)&h->gblk, sizeof(int4) * std::max<size_t>(v.size(), 1), "Gaussian block list")))
     return rc;
-  if (!v.empty()) WL_CHECK(h, cudaMemcpy(h->gblk, v.data(), sizeof(int4) * v.size(), cudaMemcpyHostToDevice));
+  // (a synchronous copy would go through the legacy default stream, which a
+  // non-blocking stream does not wait for; the pageable source is staged
+  // before the call returns, so v may go)
+  if (!v.empty())
+    WL_CHECK(h, cudaMemcpyAsync(h->gblk, v.data(), sizeof(int4) * v.size(), cudaMemcpyHostToDevice, s));
   return COV_OK;
 }
 
@@ -352,7 +363,7 @@ static int gauss_blocks(cov_handle* h) {
 static int gauss(cov_handle* h, const GatherArgs& g, int64_t r0, int64_t r1, OutMap out, cudaStream_t s) {
   if (!(g.terms & COV_TERM_G) || r1 <= r0) return COV_OK;
   int rc;
-  if ((rc = gauss_blocks(h))) return rc;
+  if ((rc = gauss_blocks(h, s))) return rc;
   const auto& st = h->gblk_row;
   const int64_t first = std::lower_bound(st.begin(), st.end(), r0 - 31) - st.begin();
   const int64_t last = std::lower_bound(st.begin(), st.end(), r1) - st.begin();

@@ -147,7 +147,7 @@ struct cov_handle {
   std::vector<int64_t> gblk_row;  // (host) first row of each sub-block, ascending
   // launch orders of the tensor-core contraction, by tile-row range
   struct TileOrder {
-    int kind = -1;
+    int kind = -1, group = 0;
     int64_t t0 = -1, t1 = -1, n = 0;
     int2* p = nullptr;  // a slot of tile_ring
   } tile_cache[WL_TILE_CACHE];
@@ -184,6 +184,7 @@ struct cov_handle {
   bool chol_lookahead = true;  // Cholesky panel look-ahead on the side stream
   int chol_kernel = 0;         // Cholesky trailing update: 0 persistent (k_chol_upd), 1 one CTA per tile
   int tc_kernel = -1;          // contraction kernel: -1 automatic, 0 one CTA per tile, 1 CTA pairs
+  int pr_group = 8;            // tile rows per group of the pair-tile launch order
   struct Selection {           // cumulative S/N selections (P, B, joint; all rows in place)
     bool ready = false;
     int64_t Ms = 0;

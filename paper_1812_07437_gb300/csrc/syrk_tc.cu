@@ -455,6 +455,10 @@ __global__ void __launch_bounds__(128, 1)
     ti = t.x;
     tj = t.y;
   }
+  if (tj < 0 || tj > ti || ti * TW_BM >= M) {  // outside the lower triangle: reported, skipped
+    if (threadIdx.x == 0) atomicExch(status, 2);
+    return;
+  }
   int row_i = (int)(ti * TW_BM), row_j = (int)(tj * TW_BM);
 
   if (threadIdx.x == 0) {
@@ -673,6 +677,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(128, 1)
   const uint32_t p = cluster_rank() & 1u;  // 0: the CTA that issues the MMAs
   const int2 pt = pairs[blockIdx.x >> 1];
   const int64_t ti = pt.x, tj = pt.y;
+  // an entry of the launch order outside the lower triangle is reported
+  // (status 2) and skipped before any barrier, copy or allocation; both CTAs
+  // of the pair read the same entry and leave together
+  if (tj < 0 || tj > ti || ti * TW_BM >= M) {
+    if (threadIdx.x == 0) atomicExch(status, 2);
+    return;
+  }
   const bool two = tj + 1 <= ti;  // the second tile (ti, tj + 1) is a lower tile
   const int row_i = (int)(ti * TW_BM), row_j = (int)(tj * TW_BM);
 
@@ -931,9 +942,10 @@ int wl_trows_split(cov_handle* h, cudaStream_t s) {
 // (ti, tj), tj <= ti, of tile rows [t0, t1), row by row.  kind 1: the pair
 // tiles (ti, tj), tj even, each covering the lower tiles (ti, tj) and
 // (ti, tj + 1) (the second only when tj + 1 <= ti).
-int wl_tile_order(cov_handle* h, int kind, int64_t t0, int64_t t1, const int2** tiles, int64_t* n) {
+int wl_tile_order(cov_handle* h, int kind, int64_t t0, int64_t t1, const int2** tiles, int64_t* n, cudaStream_t s) {
+  const int group = kind == 1 ? h->pr_group : 0;
   for (auto& c : h->tile_cache)
-    if (c.p && c.kind == kind && c.t0 == t0 && c.t1 == t1) {
+    if (c.p && c.kind == kind && c.group == group && c.t0 == t0 && c.t1 == t1) {
       *tiles = c.p;
       *n = c.n;
       return COV_OK;
@@ -943,10 +955,11 @@ int wl_tile_order(cov_handle* h, int kind, int64_t t0, int64_t t1, const int2** 
     for (int64_t ti = t0; ti < t1; ++ti)
       for (int64_t tj = 0; tj <= ti; ++tj) v.push_back(make_int2((int)ti, (int)tj));
   } else {
-    // groups of PR_GROUP tile rows; inside a group, column pair by column
-    // pair, so the ~76 pairs of one wave share a few row and column panels in L2
-    for (int64_t g0 = t0; g0 < t1; g0 += PR_GROUP) {
-      int64_t g1 = std::min<int64_t>(g0 + PR_GROUP, t1);
+    // groups of `group` tile rows (PR_GROUP unless tuned); inside a group,
+    // column pair by column pair, so the ~76 pairs of one wave share a few row
+    // and column panels in L2
+    for (int64_t g0 = t0; g0 < t1; g0 += group) {
+      int64_t g1 = std::min<int64_t>(g0 + group, t1);
       for (int64_t j0 = 0; j0 < g1; j0 += 2)
         for (int64_t i = g0; i < g1; ++i)
           if (j0 <= i) v.push_back(make_int2((int)i, (int)j0));
@@ -965,12 +978,24 @@ int wl_tile_order(cov_handle* h, int kind, int64_t t0, int64_t t1, const int2** 
     for (int k = 0; k < WL_TILE_CACHE; ++k) h->tile_cache[k].p = nullptr;
   }
   if (v.size() > h->tile_ring_cap) return wl_fail(h, COV_ERR_INVALID, "launch order larger than its ring slot");
+  // a captured step reuses the orders of its eager first run: a copy from
+  // host memory cannot become part of a graph
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  WL_CHECK(h, cudaStreamIsCapturing(s, &cap));
+  if (cap != cudaStreamCaptureStatusNone)
+    return wl_fail(h, COV_ERR_INVALID, "contraction launch order not built before stream capture");
   int slot = h->tile_cache_next;
   h->tile_cache_next = (h->tile_cache_next + 1) % WL_TILE_CACHE;
   auto& c = h->tile_cache[slot];
   c.p = h->tile_ring + (size_t)slot * h->tile_ring_cap;
-  WL_CHECK(h, cudaMemcpy(c.p, v.data(), sizeof(int2) * v.size(), cudaMemcpyHostToDevice));
+  // On the stream of the launches that read it: ordered after the earlier
+  // readers of this slot and before the next ones.  (A synchronous copy goes
+  // through the legacy default stream, which a non-blocking stream does not
+  // wait for: a kernel could read the slot before the copy lands.)  The copy
+  // from pageable memory is staged before the call returns, so v may go.
+  WL_CHECK(h, cudaMemcpyAsync(c.p, v.data(), sizeof(int2) * v.size(), cudaMemcpyHostToDevice, s));
   c.kind = kind;
+  c.group = group;
   c.t0 = t0;
   c.t1 = t1;
   c.n = (int64_t)v.size();
@@ -1018,7 +1043,7 @@ static int launch_tc(cov_handle* h, const void* hi, const void* lo, const double
     CUtensorMap mhi, mlo;
     if ((rc = make_map(h, &mhi, (void*)hi, rows, Kp, 128))) return rc;
     if ((rc = make_map(h, &mlo, (void*)lo, rows, Kp, 128))) return rc;
-    if ((rc = wl_tile_order(h, 1, t0, t1, &tiles, &nblk))) return rc;
+    if ((rc = wl_tile_order(h, 1, t0, t1, &tiles, &nblk, s))) return rc;
     k_syrk_pair<<<(unsigned)(2 * nblk), 128, PR_SMEM, s>>>(mhi, mlo, rows, Kp / TW_BK, rscale, out, h->tc_status,
                                                            tiles);
     WL_LAUNCH(h, "k_syrk_pair");
@@ -1032,7 +1057,7 @@ static int launch_tc(cov_handle* h, const void* hi, const void* lo, const double
           return (int)cudaFuncSetAttribute(k_syrk_tc256, cudaFuncAttributeMaxDynamicSharedMemorySize, TW_SMEM);
         }) != 0)
       return wl_fail(h, COV_ERR_CUDA, "cudaFuncSetAttribute(k_syrk_tc256) failed");
-    if ((rc = wl_tile_order(h, 0, t0, t1, &tiles, &nblk))) return rc;
+    if ((rc = wl_tile_order(h, 0, t0, t1, &tiles, &nblk, s))) return rc;
     k_syrk_tc256<<<(unsigned)nblk, 128, TW_SMEM, s>>>(mhi, mlo, rows, Kp / TW_BK, rscale, out, h->tc_status, tiles);
     WL_LAUNCH(h, "k_syrk_tc256");
   }
@@ -1056,6 +1081,7 @@ int wl_tc_status_check(cov_handle* h, cudaStream_t s) {
   int st = 0;
   WL_CHECK(h, cudaMemcpyAsync(&st, h->tc_status, sizeof(int), cudaMemcpyDeviceToHost, s));
   WL_CHECK(h, cudaStreamSynchronize(s));
+  if (st == 2) return wl_fail(h, COV_ERR_CUDA, "tensor-core contraction: launch order entry out of range");
   if (st) return wl_fail(h, COV_ERR_TIMEOUT, "tensor-core contraction: a bounded mbarrier wait expired");
   return COV_OK;
 }

@@ -87,9 +87,14 @@ class cov_opts(C.Structure):
 COV_BATCH_TUNE = 1
 
 
+COV_BATCH_CANDIDATES = 6
+
+
 class cov_batch_info(C.Structure):
-    _fields_ = [("tc_kernel", C.c_int), ("chol_lookahead", C.c_int), ("candidate_ms", C.c_double * 4),
-                ("first_ms", C.c_double), ("capture_ms", C.c_double), ("replay_ms", C.c_double)]
+    _fields_ = [("tc_kernel", C.c_int), ("chol_lookahead", C.c_int),
+                ("candidate_ms", C.c_double * COV_BATCH_CANDIDATES), ("tuned", C.c_int), ("pr_group", C.c_int),
+                ("chol_kernel", C.c_int), ("single_launch", C.c_int), ("first_ms", C.c_double),
+                ("capture_ms", C.c_double), ("replay_ms", C.c_double)]
 
 
 class cov_pca_info(C.Structure):

@@ -1,10 +1,12 @@
 """GPU checks of the batched cosmologies entry point (cov_batch_snr).
 
-The batch captures the cosmology-dependent step once as a CUDA graph and
-replays it; every cosmology's data vector and cumulative S/N must equal those
-of the plain calls (cov_update, cov_spectra, cov_assemble, cov_snr) for that
-cosmology, to 1e-10 relative, with and without the launch-configuration
-tuning, in both precisions.
+The batch captures the cosmology-dependent step once, into the body of a
+graph "while" node, and runs the other cosmologies as one graph launch (a
+loop on the device); every cosmology's data vector and cumulative S/N must
+equal those of the plain calls (cov_update, cov_spectra, cov_assemble,
+cov_snr) for that cosmology, to 1e-10 relative, with and without the
+launch-configuration tuning (the reference handle uses the contraction and
+Cholesky kernels the tuner kept), in both precisions.
 """
 import numpy as np
 import pytest
@@ -55,9 +57,11 @@ def test_batch_equals_plain_calls(name, precision, tune):
     h = Handle(workloads.get(name))
     snr, D, info = h.batch_snr(cos, precision=precision, with_D=True, tune=tune)
     assert info["replay_ms"] > 0 and info["capture_ms"] > 0
+    assert info["single_launch"] == 1
     if tune:
         assert all(t > 0 for t in info["candidate_ms"])
-    ref = Handle(workloads.get(name))
+    ref = Handle(workloads.get(name), tc_kernel=N.COV_TC_SINGLE if info["tc_kernel"] == 0 else N.COV_TC_AUTO,
+                 chol_kernel=info["chol_kernel"])
     for k, c in enumerate(cos):
         Dk, sk = _plain(ref, c, precision)
         assert np.max(np.abs(D[k] / Dk - 1.0)) <= TOL, k

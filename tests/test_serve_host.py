@@ -133,3 +133,24 @@ def test_concentration_model_is_part_of_the_resident_key(Server):
         reused.append(info["reused"])
     s.close()
     assert reused == [0, 0, 0, 0, 1, 1, 1]
+
+
+def test_library_work_is_stream_ordered():
+    """The server runs requests on several non-blocking streams from several
+    threads.  A synchronous cudaMemcpy/cudaMemset goes through the legacy
+    default stream, which non-blocking streams do not wait for, and a copy
+    from pageable memory may return before its DMA lands: a kernel on the
+    request's stream could then read the buffer first.  Every copy, fill and
+    launch of the library names its stream."""
+    import pathlib
+    import re
+    src = pathlib.Path(__file__).resolve().parents[1] / "paper_1812_07437_gb300" / "csrc"
+    bad = []
+    for f in sorted(src.glob("*.cu")) + sorted(src.glob("*.cuh")):
+        for n, line in enumerate(f.read_text().splitlines(), 1):
+            code = line.split("//")[0]
+            if re.search(r"\bcudaMem(cpy|set|cpy2D|cpyToSymbol)\s*\(", code):
+                bad.append(f"{f.name}:{n}: {line.strip()}")
+            if re.search(r"<<<[^>]*>>>", code) and len(re.search(r"<<<([^>]*)>>>", code).group(1).split(",")) < 4:
+                bad.append(f"{f.name}:{n}: {line.strip()}")
+    assert not bad, "\n".join(bad)
