@@ -13,7 +13,9 @@ Element-by-element forms, each the paper's expression written out:
                P^s_{t_x t'_y}(l_x) T_{t_rest, t'_rest}(rest legs);
              the paper's prefactor 2 pi/(Omega l Delta l) is its continuum
              value of 1/N(l); the integer N(l^b) is used, as in the Gauss
-             term.  B and T are the 1-halo polyspectra (Sec. 4.1).
+             term.  B and T are the 1-halo polyspectra (Sec. 4.1).  With a
+             `kappa` function (oracle/coupling.py) the exact lattice coupling
+             kappa(tau, x; tau', y) replaces 1/N(l_x).
   PB         Eq. Covpb: for each leg y of the bispectrum in the bin of P,
              1/N(l) [P^s_{i t'_y} B_{j, t'_rest} + P^s_{j t'_y} B_{i, t'_rest}]
              (the printed tomographic indices are garbled; this is the Wick
@@ -51,10 +53,11 @@ def row_tomos(row):
 
 
 class Covariance:
-    def __init__(self, T, S, rows, tris, Nmodes, Ntri):
+    def __init__(self, T, S, rows, tris, Nmodes, Ntri, kappa=None):
         self.T, self.S, self.rows, self.tris = T, S, rows, tris
         self.N = np.asarray(Nmodes, dtype=np.float64)
         self.Ntri = np.asarray(Ntri, dtype=np.float64)
+        self.kappa = kappa  # exact BB+PT coupling (t, x, t', y) -> value, or None for 1/N(l)
         self._icache = {}
 
     # -- helpers -----------------------------------------------------------
@@ -125,7 +128,10 @@ class Covariance:
                 bb = B1h[r1[1], t2[y], t1[rx[0]], t1[rx[1]]] * B1h[r2[1], t1[x], t2[ry[0]], t2[ry[1]]]
                 tt = self.polyspec_1h([bins1[rx[0]], bins1[rx[1]], bins2[ry[0]], bins2[ry[1]]],
                                       [t1[rx[0]], t1[rx[1]], t2[ry[0]], t2[ry[1]]])
-                tot += (bb + Ps[bins1[x], t1[x], t2[y]] * tt) / nN
+                if self.kappa is None:
+                    tot += (bb + Ps[bins1[x], t1[x], t2[y]] * tt) / nN
+                else:
+                    tot += (bb + Ps[bins1[x], t1[x], t2[y]] * tt) * self.kappa(r1[1], x, r2[1], y)
         return tot
 
     def pb(self, r1, r2):

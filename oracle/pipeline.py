@@ -5,17 +5,21 @@ Workload keys (plain parameters, no arithmetic):
   nz:        n_tomo, z0, alpha, zmin, zmax, photoz_sigma0, n_gal_arcmin2, sigma_e
   bins:      n_ell, ell_min, ell_max, f_sky, n_chi, n_mass, m_min, m_max, k_max
   terms:     bitmask of covariance terms (G=1, 1H=2, BBPT=4, PB=8, SSC=16)
+
+coupling="exact" takes the BB+PT couplings as the exact lattice sums of
+oracle/coupling.py (Eq. CovBB) instead of 1/N(l).
 """
 import numpy as np
 
 from . import counts as cnt
+from . import coupling as cpl
 from .covariance import Covariance
 from .layout import data_layout
 from .spectra import Spectra, Tables
 
 
 class OracleRun:
-    def __init__(self, wl, ntri=None, workers=None):
+    def __init__(self, wl, ntri=None, workers=None, coupling="modes"):
         self.wl = wl
         self.T = Tables(wl)
         nt = wl["nz"]["n_tomo"]
@@ -26,7 +30,13 @@ class OracleRun:
             ntri = cnt.triangle_counts(self.s_lo, self.s_hi, self.tris, workers=workers)
         self.Ntri = np.asarray(ntri, dtype=np.int64)
         self.S = Spectra(self.T, self.tris)
-        self.cov = Covariance(self.T, self.S, self.rows, self.tris, self.Nmodes, self.Ntri)
+        kappa = None
+        if coupling == "exact":
+            _, self.col, self.G = cpl.grams(self.s_lo, self.s_hi, self.tris, workers=workers)
+            kappa = cpl.kappa_table(self.col, self.G, self.Ntri, self.tris)
+        elif coupling != "modes":
+            raise ValueError(coupling)
+        self.cov = Covariance(self.T, self.S, self.rows, self.tris, self.Nmodes, self.Ntri, kappa=kappa)
         self.D = np.array([self.S.data_value(r) for r in self.rows])
 
     @property
