@@ -57,12 +57,12 @@ def parse():
     p.add_argument("--snr-rows", default="joint,B,P", help="row sets of --snr-10bin")
     p.add_argument("--snr-precision", default="auto", choices=["auto", "fp64", "split_bf16"],
                    help="covariance form of --snr-10bin (auto: the bench's own)")
-    p.add_argument("--serve-requests", type=int, default=200)
+    p.add_argument("--serve-requests", type=int, default=250)
     p.add_argument("--serve-rate", type=float, default=200.0)
     p.add_argument("--serve-budget-gb", type=float, default=160.0)
     p.add_argument("--serve-search", action="store_true",
                    help="binary search for the sustainable arrival rate on the same mix and seed")
-    p.add_argument("--serve-search-requests", type=int, default=100)
+    p.add_argument("--serve-search-requests", type=int, default=40)
     p.add_argument("--serve-slots", type=int, default=4)
     p.add_argument("--precision", default="auto", choices=["auto", "fp64", "split_bf16"])
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -73,6 +73,7 @@ def parse():
     p.add_argument("--model-a-workload", default="cfg3_5bin")
     p.add_argument("--model-a-nodes", type=int, default=8, help="concentration nodes of model A")
     p.add_argument("--no-pca", action="store_true", help="skip the principal components of the paper's set-up")
+    p.add_argument("--no-coupling", action="store_true", help="skip the exact BB+PT couplings key")
     p.add_argument("--pca-bins", default="1,2", help="tomographic bin counts of the paper's set-up for the PCA key")
     p.add_argument("--chol-kernel", default="auto", choices=["auto", "tile"],
                    help="Cholesky trailing update: persistent (auto) or one CTA per 128 x 64 tile")
@@ -511,7 +512,7 @@ def serving_run(prec, n_req, rate, budget_gb, slots, device, seed=2024):
             "peak_reserved_gb": st["peak_reserved"] / 1e9, "budget_gb": st["budget"] / 1e9, "slots": slots}
 
 
-def serving_search(prec, n_req, budget_gb, slots, device, lo=0.25, hi=16.0, probes=6):
+def serving_search(prec, n_req, budget_gb, slots, device, lo=0.05, hi=0.5, probes=4):
     """The highest arrival rate the server sustains on the serving mix (same
     seed): a rate is sustained when 90% of its requests start within 2 s of
     their arrival (the queue does not grow); bisection in log rate between lo
@@ -525,7 +526,9 @@ def serving_search(prec, n_req, budget_gb, slots, device, lo=0.25, hi=16.0, prob
         good = sv["completed"] > 0 and sv["queue_wait_p90_s"] <= 2.0 and sv["failed"] == 0
         trials.append({"offered_rate_hz": r, "sustained": good, "achieved_rate_hz": sv["achieved_rate_hz"],
                        "queue_wait_p90_s": sv["queue_wait_p90_s"], "latency_p50_s": sv["latency_p50_s"],
-                       "latency_p99_s": sv["latency_p99_s"], "completed": sv["completed"]})
+                       "latency_p99_s": sv["latency_p99_s"], "completed": sv["completed"],
+                       "rejected_never_fit": sv["rejected_never_fit"], "failed": sv["failed"],
+                       "makespan_s": sv["makespan_s"]})
         if good:
             lo, ok_rate = r, r
         else:
@@ -753,6 +756,73 @@ def pca_run(device, bins_list):
         torch.cuda.empty_cache()
     out["paper_states_fraction_for_99"] = {"1bin": "<~0.40", "2bin": "<~0.20", "5bin": "<~0.10"}
     out["precision"] = "fp64 covariance, fp64 Jacobi"
+    return out
+
+
+def coupling_run(device, build_workload, snr_workload):
+    """Exact bin-averaged BB+PT couplings (App. B, Eq. CovBB; COV_COUPLING_EXACT):
+    the time to build them for a binning (cov_init with exact couplings minus
+    cov_init without, on a coarse quadrature: they depend on the binning only),
+    the spread of kappa N(l^b) (1 is the paper's 2 pi/(Omega l Delta l)), and the
+    cumulative S/N at the largest ell bin of a workload (FP64 covariance) with
+    the exact couplings against the paper's prefactor."""
+    import numpy as np
+    import torch
+    from paper_1812_07437_gb300 import native as N
+    from paper_1812_07437_gb300 import workloads
+    from paper_1812_07437_gb300.handle import Handle
+    dev = torch.device("cuda", device)
+    out = {}
+    base = workloads.get(build_workload)
+    wl = workloads.get(build_workload, bins=dict(base["bins"], n_chi=16, n_mass=12))
+    walls = {}
+    for name, cp in (("modes", N.COV_COUPLING_MODES), ("exact", N.COV_COUPLING_EXACT), ("exact2", N.COV_COUPLING_EXACT)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = Handle(wl, device=device, coupling=cp)
+        walls[name] = time.perf_counter() - t0
+        if name == "exact":
+            ne, nt = h.counts()
+            tris = []
+            lo, hi, ncols = np.inf, -np.inf, []
+            for A in range(h.n_ell):
+                cols, G = h.coupling_gram(A)
+                ncols.append(len(cols))
+                if len(cols) == 0:
+                    continue
+                tris.append((A, cols, G))
+            rd = h.row_desc()
+            tri_bins = {}
+            for r in rd[rd[:, 0] == 1]:
+                tri_bins[int(r[7])] = tuple(int(x) for x in r[1:4])
+            ntri_of = {b: int(nt[t]) for t, b in tri_bins.items()}
+            # kappa N(A) = G N(A) / (N_tri N_tri') over every pair of columns of a
+            # bin; column (Y, Z) of bin A belongs to the triangle sorted(A, Y, Z)
+            for A, cols, G in tris:
+                n = np.array([ntri_of[tuple(sorted((A, int(y), int(z))))] for y, z in cols], dtype=np.float64)
+                kn = G.astype(np.float64) * float(ne[A]) / np.outer(n, n)
+                lo, hi = min(lo, float(kn.min())), max(hi, float(kn.max()))
+            out["kappa_N_range"] = [lo, hi]
+            out["columns_per_bin"] = [min(ncols), max(ncols)]
+        h.close()
+    out["build_workload"] = build_workload
+    out["build_s"] = min(walls["exact"], walls["exact2"]) - walls["modes"]
+    res = {}
+    for name, cp in (("modes", N.COV_COUPLING_MODES), ("exact", N.COV_COUPLING_EXACT)):
+        h = Handle(workloads.get(snr_workload), device=device, coupling=cp)
+        D = torch.zeros(h.M, dtype=torch.float64, device=dev)
+        C = torch.zeros(h.M, h.M, dtype=torch.float64, device=dev)
+        h.spectra(D)
+        h.assemble(C, N.COV_TERMS_ALL, N.COV_FP64)
+        res[name] = {w: float(h.snr(C, D, k)[-1]) for w, k in (("P", N.COV_WHICH_P), ("B", N.COV_WHICH_B),
+                                                                 ("joint", N.COV_WHICH_JOINT))}
+        del C, D
+        h.close()
+        torch.cuda.empty_cache()
+    out["snr_workload"] = snr_workload
+    out["snr_at_lmax"] = res
+    out["snr_rel_change"] = {w: res["exact"][w] / res["modes"][w] - 1.0 for w in res["modes"]}
+    out["precision"] = "fp64 covariance"
     return out
 
 
@@ -1045,6 +1115,11 @@ def run_ours(args):
             out["pca"] = pca_run(local, [int(x) for x in args.pca_bins.split(",") if x])
         except Exception as e:  # noqa: BLE001
             out["pca"] = {"error": f"{type(e).__name__}: {e}"}
+    if not args.no_coupling and packed and rank == 0 and world == 1:
+        try:
+            out["coupling_exact"] = coupling_run(local, args.workload, "cfg2_5bin")
+        except Exception as e:  # noqa: BLE001
+            out["coupling_exact"] = {"error": f"{type(e).__name__}: {e}"}
     # optional stages: a failure is recorded in the line instead of losing it
     if args.model_a and rank == 0 and world == 1:
         try:

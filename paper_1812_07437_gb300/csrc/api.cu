@@ -225,7 +225,8 @@ static void free_all(cov_handle* h) {
                   h->C2,    h->C3,    h->tc_status, h->Thi,   h->Tlo,    h->Tscale, h->Trows,     h->Tmat,
                   h->Srows, h->cosmo_d, h->Fsig,  h->Esig,    h->Msig,   h->FsigT,  h->EsigT,     h->MsigT,
                   h->invN,  h->omN,   h->work,    h->chol_scratch, h->chol_status, h->mb, h->omb, h->cs,
-                  h->cw,    h->sigF,  h->ac,      h->bmask,   h->gblk,   h->wait_flag, h->pca_buf};
+                  h->cw,    h->sigF,  h->ac,      h->bmask,   h->gblk,   h->wait_flag, h->pca_buf,
+                  h->kap,   h->kgram, h->kcol,    h->kn,      h->koff};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->tile_ring) cudaFree(h->tile_ring);
@@ -340,8 +341,10 @@ extern "C" int cov_init(const cov_cosmology* cosmo, const cov_nz* nz, const cov_
   h->row_order = opts ? opts->order : COV_ORDER_NATURAL;
   h->tc_kernel = (opts && opts->tc_kernel == COV_TC_SINGLE) ? 0 : -1;
   h->chol_kernel = (opts && opts->chol_kernel == COV_CHOL_TILE) ? 1 : 0;
-  if (h->row_set < 0 || h->row_set > 2 || h->row_order < 0 || h->row_order > 1) {
-    g_init_err = "invalid row set or row order";
+  h->coupling = opts ? opts->coupling : COV_COUPLING_MODES;
+  if (h->row_set < 0 || h->row_set > 2 || h->row_order < 0 || h->row_order > 1 ||
+      (h->coupling != COV_COUPLING_MODES && h->coupling != COV_COUPLING_EXACT)) {
+    g_init_err = "invalid row set, row order or coupling";
     delete h;
     return COV_ERR_INVALID;
   }
@@ -388,7 +391,8 @@ extern "C" int cov_init(const cov_cosmology* cosmo, const cov_nz* nz, const cov_
     delete h;
     return COV_ERR_CUDA;
   }
-  if ((rc = wl_quadrature(h, s)) == COV_OK && (rc = wl_tables(h, s)) == COV_OK) rc = wl_counts(h, s);
+  if ((rc = wl_quadrature(h, s)) == COV_OK && (rc = wl_tables(h, s)) == COV_OK && (rc = wl_counts(h, s)) == COV_OK)
+    rc = wl_couplings(h, s);  // the exact BB+PT couplings, when asked for (binning only: once)
   e = cudaStreamSynchronize(s);
   if (rc == COV_OK && e != cudaSuccess) rc = wl_cuda(h, e, "cov_init tables");
   cudaStreamDestroy(s);
@@ -416,11 +420,8 @@ extern "C" int cov_update(cov_handle* h, const cov_cosmology* cosmo, void* strea
   int tk = wl_stage_begin(h, ST_TABLES, s);
   int rc = wl_tables(h, s);
   wl_stage_end(h, tk, s);
-  if (rc == COV_OK) {
-    tk = wl_stage_begin(h, ST_COUNTS, s);
-    rc = wl_counts(h, s);
-    wl_stage_end(h, tk, s);
-  }
+  // the integer counts (and the exact couplings) depend on the binning only:
+  // cov_init computed them once
   return rc;
 }
 
