@@ -125,11 +125,19 @@ typedef struct {
                      /* COV_CHOL_AUTO (persistent, 128 x 32 tiles, epilogue   */
                      /* overlapping the next tile's MMAs) or COV_CHOL_TILE    */
                      /* (one CTA per 128 x 64 tile); bit-identical results    */
+  int coupling;      /* coupling of the BB+PT terms (Eq. CovBB):             */
+                     /* COV_COUPLING_MODES: 1/N(l^b) with the exact mode     */
+                     /* count, the paper's prefactor 2 pi/(Omega l Delta l)  */
+                     /* at its continuum value; COV_COUPLING_EXACT: the      */
+                     /* exact lattice sum over the shared leg, see           */
+                     /* cov_coupling_gram (built once, at cov_init)          */
 } cov_opts;
 #define COV_TC_AUTO 0
 #define COV_TC_SINGLE 1
 #define COV_CHOL_AUTO 0
 #define COV_CHOL_TILE 1
+#define COV_COUPLING_MODES 0
+#define COV_COUPLING_EXACT 1
 
 typedef struct cov_handle cov_handle;
 
@@ -158,6 +166,28 @@ int cov_layout(const cov_handle* h, int64_t* M, int64_t* n_P, int64_t* n_B, int6
  * (Eq. PSest) and N_tri for the n_tri closed triples (App. B, first
  * equality of the N_tri definition).  Synchronises the stream. */
 int cov_counts(cov_handle* h, int64_t* N_ell, int64_t* N_tri, void* stream);
+
+/* Exact bin-averaged coupling of the BB+PT terms (App. B: the binned
+ * bispectrum estimator and Eq. CovBB).  A BB or PT Wick term joins leg x of
+ * triangle bin tau to leg y of tau', both in ell bin A; with the polyspectra
+ * constant over the bins its exact coupling is
+ *   kappa = sum_{q in A} n_{tau,x}(q) n_{tau',y}(q) / (N_tri(tau) N_tri(tau')),
+ * n_{tau,x}(q) = #{p in Y : q + p in Z} the number of lattice triangles of tau
+ * whose leg x is the mode q ({Y, Z} the bins of the other two legs).  n
+ * depends on A and the unordered pair {Y, Z} only: bin A has one column per
+ * pair (Y <= Z) such that sorted (A, Y, Z) is a closed triple, in order of
+ * first appearance over the triples and their legs.  With
+ * opts->coupling == COV_COUPLING_EXACT, cov_init computes for every bin the
+ * integer Gram matrix G_A[c][c'] = sum_q n_c(q) n_c'(q) (int64, exact) and
+ * cov_assemble uses kappa = G / (N_tri N_tri') in place of 1/N(l^b).
+ *
+ * cov_coupling_gram copies bin `ell_bin`'s columns and Gram matrix to host
+ * memory: on entry *ncol is the capacity of cols (2 * capacity int32: Y, Z)
+ * and gram (capacity^2 int64, row-major, both halves); on return *ncol is the
+ * number of columns, and nothing is copied if the capacity was too small (or
+ * cols or gram is NULL).  COV_ERR_INVALID if the handle was created without
+ * COV_COUPLING_EXACT or ell_bin is out of range.  Synchronises the stream. */
+int cov_coupling_gram(cov_handle* h, int ell_bin, int* ncol, int32_t* cols, int64_t* gram, void* stream);
 
 /* Predict the data vector: d_D[M] (device) receives P_ij(l) (Eqs.
  * nProjection, PspHMtot2) and B_ijk(l1,l2,l3) (Eq. BspHMtot) in the layout

@@ -41,6 +41,12 @@ struct GatherArgs {
   const double* invN;    // 1 / N(l^b)
   const double* omN;     // Omega / N_tri(t)
   const uint64_t* bmask; // ell bins present in each 32-row block
+  // exact BB+PT couplings (null: 1 / N(l^b)): kappa of leg x of triangle t and
+  // leg y of t' in bin A at kap[koff[A] + kcol[3 t + x] kn[A] + kcol[3 t' + y]]
+  const double* kap;
+  const int32_t* kcol;
+  const int32_t* kn;
+  const int64_t* koff;
 };
 
 // 1 / N(l^b) and Omega / N_tri(t) from the exact integer counts, once per
@@ -69,7 +75,9 @@ __device__ double gather_element(const GatherArgs& g, const int32_t* ra, const i
         for (int y = 0; y < 3; ++y) {
           if (ba[x] != bb[y]) continue;
           int x1 = (x + 1) % 3, x2 = (x + 2) % 3, y1 = (y + 1) % 3, y2 = (y + 2) % 3;
-          double iN = g.invN[ba[x]];
+          const int A = ba[x];
+          const double iN = g.kap ? g.kap[g.koff[A] + (int64_t)g.kcol[3 * ra[7] + x] * g.kn[A] + g.kcol[3 * rb[7] + y]]
+                                  : g.invN[A];
           double bbv = b1h(g, ra[7], tb[y], ta[x1], ta[x2]) * b1h(g, rb[7], ta[x], tb[y1], tb[y2]);
           int64_t r1 = leg_pair(ba[x1] * g.nt + ta[x1], ba[x2] * g.nt + ta[x2], g.nleg);
           int64_t r2 = leg_pair(bb[y1] * g.nt + tb[y1], bb[y2] * g.nt + tb[y2], g.nleg);
@@ -313,8 +321,8 @@ static int gather_args(cov_handle* h, unsigned terms, GatherArgs* g, cudaStream_
   }
   k_inv_counts<<<1, 256, 0, s>>>(h->nl, h->ntri, h->omega, h->Nmodes, h->Ntri, h->invN, h->omN);
   WL_LAUNCH(h, "k_inv_counts");
-  *g = GatherArgs{h->nt,   h->nleg, terms, h->omega, h->rowdesc_d, h->Ps, h->B1hp, h->Tmat, h->ntrow,
-                  h->invN, h->omN,  h->bmask};
+  *g = GatherArgs{h->nt,   h->nleg, terms, h->omega, h->rowdesc_d, h->Ps,   h->B1hp, h->Tmat, h->ntrow,
+                  h->invN, h->omN,  h->bmask, h->kap,  h->kcol,      h->kn,   h->koff};
   return COV_OK;
 }
 

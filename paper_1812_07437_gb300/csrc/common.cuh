@@ -141,6 +141,20 @@ struct cov_handle {
   // per leg-bin signature s (P: ell bin; B: nl + triangle): F[s][n][q] / 2^E[s][n] in FP32,
   // E[s][n], and the FP64 row-block maximum max_q |F[s][n][q]|
   double *invN = nullptr, *omN = nullptr;  // 1 / N(l^b), Omega / N_tri(t)
+  // exact BB+PT couplings (COV_COUPLING_EXACT): per ell bin A one column per
+  // pair (Y, Z) of other-leg bins, the int64 Gram matrix of their leg counts
+  // (lower half) and kappa = G / (N_tri N_tri') (both halves, FP64)
+  int coupling = 0;                 // COV_COUPLING_*
+  std::vector<int32_t> kcol_h;      // [ntri][3] column of each leg in its bin
+  std::vector<int32_t> kn_h;        // [nl] columns of each bin
+  std::vector<int64_t> koff_h;      // [nl + 1] offset of each bin's ncol x ncol block
+  std::vector<int32_t> kyz_h;       // per bin, per column: Y, Z
+  std::vector<int32_t> ktri_h;      // per bin, per column: its triangle
+  std::vector<int64_t> kcoff_h;     // [nl + 1] first column of each bin
+  double* kap = nullptr;
+  unsigned long long* kgram = nullptr;
+  int32_t *kcol = nullptr, *kn = nullptr;
+  int64_t* koff = nullptr;
   uint64_t* bmask = nullptr;  // ell bins present in each 32-row block (the product terms skip the rest)
   bool bmask_ready = false;
   int4* gblk = nullptr;       // 32 x 32 sub-blocks of the Gaussian-term diagonal blocks, by first row
@@ -227,6 +241,9 @@ void wl_stage_end(cov_handle* h, int token, cudaStream_t s);
 int wl_quadrature(cov_handle* h, cudaStream_t s);  // tables.cu
 int wl_tables(cov_handle* h, cudaStream_t s);   // tables.cu
 int wl_counts(cov_handle* h, cudaStream_t s);   // counts.cu
+int wl_couplings(cov_handle* h, cudaStream_t s);  // coupling.cu: exact BB+PT couplings (synchronises s)
+void wl_coupling_plan(cov_handle* h);             // coupling.cu: columns per bin (host)
+size_t wl_coupling_bytes(const cov_handle* h);    // coupling.cu: resident bytes of the exact couplings
 int wl_spectra(cov_handle* h, double* d_D, cudaStream_t s);  // spectra.cu
 int wl_assemble(cov_handle* h, double* d_C, int64_t ldc, unsigned terms, int precision, cudaStream_t s);
 int wl_snr_tiles(cov_handle* h, double* Ct, const double* D, double* h_snr, cudaStream_t s);  // chol.cu

@@ -19,10 +19,11 @@ def _stream_ptr(stream):
 
 class Handle:
     def __init__(self, wl, device=0, hbm_budget=0, rows=N.COV_ROWS_JOINT, order=N.COV_ORDER_NATURAL,
-                 tc_kernel=N.COV_TC_AUTO, chol_kernel=N.COV_CHOL_AUTO):
+                 tc_kernel=N.COV_TC_AUTO, chol_kernel=N.COV_CHOL_AUTO, coupling=N.COV_COUPLING_MODES):
         self.L = N.lib()
         cs, ns, bs = N.structs_from_workload(wl)
-        opts = N.cov_opts(int(device), int(hbm_budget), int(rows), int(order), int(tc_kernel), int(chol_kernel))
+        opts = N.cov_opts(int(device), int(hbm_budget), int(rows), int(order), int(tc_kernel), int(chol_kernel),
+                          int(coupling))
         h = C.c_void_p()
         N.check(self.L.cov_init(C.byref(cs), C.byref(ns), C.byref(bs), C.byref(opts), C.byref(h)))
         self.h = h
@@ -55,6 +56,18 @@ class Handle:
         N.check(self.L.cov_counts(self.h, ne.ctypes.data_as(C.c_void_p), nt.ctypes.data_as(C.c_void_p),
                                   _stream_ptr(stream)), self.h)
         return ne, nt[: self.n_tri]
+
+    def coupling_gram(self, ell_bin, stream=None):
+        """Columns (Y, Z) of ell bin `ell_bin` and the exact Gram matrix of
+        their leg counts (int64), for a handle made with COV_COUPLING_EXACT."""
+        n = C.c_int(0)
+        N.check(self.L.cov_coupling_gram(self.h, int(ell_bin), C.byref(n), None, None, _stream_ptr(stream)), self.h)
+        cols = np.zeros((max(n.value, 1), 2), dtype=np.int32)
+        gram = np.zeros((max(n.value, 1), max(n.value, 1)), dtype=np.int64)
+        N.check(self.L.cov_coupling_gram(self.h, int(ell_bin), C.byref(n), cols.ctypes.data_as(C.c_void_p),
+                                         gram.ctypes.data_as(C.c_void_p), _stream_ptr(stream)), self.h)
+        k = n.value
+        return cols[:k], gram[:k, :k]
 
     def table(self, name, stream=None):
         cnt = C.c_int64()

@@ -44,6 +44,8 @@ COV_TC_AUTO = 0
 COV_TC_SINGLE = 1
 COV_CHOL_AUTO = 0
 COV_CHOL_TILE = 1
+COV_COUPLING_MODES = 0
+COV_COUPLING_EXACT = 1
 
 COV_CONC_DUFFY = 0
 COV_CONC_BULLOCK = 1
@@ -52,7 +54,7 @@ EXPORTED = ["cov_init", "cov_update", "cov_layout", "cov_counts", "cov_spectra",
             "cov_assemble_band", "cov_table", "cov_profile", "cov_stage_times", "cov_stage_name", "cov_snr_noalloc",
             "cov_last_error", "cov_free", "cov_snr_tiles", "cov_batch_snr", "cov_server_create", "cov_server_submit", "cov_server_wait",
             "cov_server_error", "cov_server_stats_get", "cov_server_clock", "cov_request_footprint",
-            "cov_server_free", "cov_wait_selftest", "cov_pca"]
+            "cov_server_free", "cov_wait_selftest", "cov_pca", "cov_coupling_gram"]
 
 COV_REQ_QUEUED = 0
 COV_REQ_RUNNING = 1
@@ -81,7 +83,7 @@ class cov_bins(C.Structure):
 
 class cov_opts(C.Structure):
     _fields_ = [("device", C.c_int), ("hbm_budget", C.c_size_t), ("rows", C.c_int), ("order", C.c_int),
-                ("tc_kernel", C.c_int), ("chol_kernel", C.c_int)]
+                ("tc_kernel", C.c_int), ("chol_kernel", C.c_int), ("coupling", C.c_int)]
 
 
 COV_BATCH_TUNE = 1
@@ -156,6 +158,7 @@ def lib():
         L.cov_snr_noalloc.argtypes = [P, i64, P, i64, P, C.c_int, P, P, P]
         L.cov_wait_selftest.argtypes = [P, C.c_uint, C.c_int, P]
         L.cov_pca.argtypes = [P, P, i64, P, P, P, P, P, C.POINTER(cov_pca_info), P]
+        L.cov_coupling_gram.argtypes = [P, C.c_int, C.POINTER(C.c_int), P, P, P]
         L.cov_last_error.argtypes = [P]
         L.cov_last_error.restype = C.c_char_p
         L.cov_free.argtypes = [P]
