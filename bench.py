@@ -50,7 +50,8 @@ def parse():
     p.add_argument("--no-snr-run", action="store_true")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-batch", action="store_true")
-    p.add_argument("--batch-bins", default="3,5", help="tomographic bin counts of the batched Fisher run")
+    p.add_argument("--batch-bins", default="3,5",
+                   help="tomographic bin counts of the batched Fisher run (n_t:n for the first n cosmologies only)")
     p.add_argument("--snr-10bin", action="store_true",
                    help="also time the P and B cumulative S/N of the workload itself (besides the joint one), "
                         "in place on packed tiles, per --snr-rows")
@@ -548,16 +549,20 @@ def batch_run(prec, device, bins_list):
     from paper_1812_07437_gb300 import native as N
     from paper_1812_07437_gb300 import workloads
     from paper_1812_07437_gb300.handle import Handle
-    cos = workloads.fisher_cosmologies()
+    cos_all = workloads.fisher_cosmologies()
     dev = torch.device("cuda", device)
-    out = {"cosmologies": len(cos), "ell_bins": 16, "n_chi": 256, "n_mass": 128}
-    for k, nt in enumerate(bins_list):
+    out = {"cosmologies": len(cos_all), "ell_bins": 16, "n_chi": 256, "n_mass": 128}
+    for k, ent in enumerate(bins_list):
+        # "nt" runs every cosmology; "nt:n" the first n (a timing sample of a large set-up)
+        nt, _, ncos = str(ent).partition(":")
+        nt = int(nt)
+        cos = cos_all[: int(ncos)] if ncos else cos_all
         wl = workloads.fisher_workload(nt)
         h = Handle(wl, device=device)
         st = torch.cuda.Stream(device=dev)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        snr, _, info = h.batch_snr(cos, precision=prec, tune=True, stream=st)
+        snr, _, info = h.batch_snr(cos, precision=prec, tune=not ncos, stream=st)
         total = time.perf_counter() - t0
         el = h.M * (h.M + 1) // 2
         r = {"M": h.M, "total_s": total, "first_ms": info["first_ms"], "capture_ms": info["capture_ms"],
@@ -567,7 +572,8 @@ def batch_run(prec, device, bins_list):
                        "candidate_ms": info["candidate_ms"],
                        "candidates": ["pairs g8 look-ahead persistent", "pairs g4", "pairs g16", "one CTA per tile",
                                       "no look-ahead", "one-tile Cholesky update"]},
-             "elements_per_s_replays": el / (info["replay_ms"] / 1e3), "snr_joint_fiducial": float(snr[0, 2, -1])}
+             "elements_per_s_replays": el / (info["replay_ms"] / 1e3), "snr_joint_fiducial": float(snr[0, 2, -1]),
+             "cosmologies": len(cos)}
         if k == 0:
             D = torch.zeros(h.M, dtype=torch.float64, device=dev)
             C = torch.zeros(h.M, h.M, dtype=torch.float64, device=dev)
@@ -1102,7 +1108,7 @@ def run_ours(args):
                                 note="joint vector; P-only and B-only with --snr-10bin")
         torch.cuda.empty_cache()
     if not args.no_batch and packed and rank == 0 and world == 1:
-        out["fisher_batch"] = batch_run(prec, local, [int(x) for x in args.batch_bins.split(",") if x])
+        out["fisher_batch"] = batch_run(prec, local, [x for x in args.batch_bins.split(",") if x])
     if args.snr_10bin and rank == 0 and world == 1:
         sets = {"joint": N.COV_ROWS_JOINT, "B": N.COV_ROWS_B, "P": N.COV_ROWS_P}
         sp = prec if args.snr_precision == "auto" else (N.COV_FP64 if args.snr_precision == "fp64" else

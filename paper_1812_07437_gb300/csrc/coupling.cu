@@ -16,13 +16,15 @@
 //                  (q, c): for each row of p the admissible x of p form at
 //                  most 2 x 2 integer intervals, intersected exactly (the row
 //                  tables of counts.cu).  Column-major int32 matrix Nm[c][q],
-//                  with the weighted column sums (= N_tri, checked) and the
-//                  column maxima (the int64 bound, checked).
-//  * k_gram        G[c][c'] = sum_q w_q Nm[c][q] Nm[c'][q], int64, lower
-//                  half: 32 x 32 output tiles per block over chunks of
-//                  orbits, partial sums added atomically (all terms >= 0).
+//                  with the weighted column sums (= N_tri, checked).
+//  * k_gram        G[c][c'] = sum_q w_q Nm[c][q] Nm[c'][q], exact in unsigned
+//                  64-bit, lower half: 32 x 32 output tiles per block over
+//                  chunks of orbits, partial sums added atomically (all terms
+//                  >= 0), with an FP64 shadow of each sum.  The entries come
+//                  close to 2^63 at l_max = 5000 (cfg2_5bin: 2^62.7).
 //  * k_kappa       kappa[c][c'] = G / (N_tri(c) N_tri(c')) in FP64, both
-//                  halves.
+//                  halves; an entry at or beyond 2^63 (by its shadow) is an
+//                  error.
 #include <algorithm>
 
 #include "common.cuh"
@@ -62,10 +64,9 @@ __device__ __forceinline__ int intervals_of(int2 row, int* lo, int* hi) {
 __global__ void __launch_bounds__(LC_THREADS) k_leg_counts(int rmax, const int32_t* __restrict__ tab,
                                                            const int2* __restrict__ orb, int64_t norb,
                                                            const ColDesc* __restrict__ cols, int32_t* Nm,
-                                                           unsigned long long* colsum, int* colmax) {
+                                                           unsigned long long* colsum) {
   extern __shared__ int2 rows_sh[];  // [2][rmax + 1]: rows (x_outer, x_inner) of Y and Z
   __shared__ unsigned long long wsh[LC_THREADS / 32];
-  __shared__ int msh[LC_THREADS / 32];
   const int c = blockIdx.y;
   const ColDesc cd = cols[c];
   const size_t stride = (size_t)rmax + 1;
@@ -79,7 +80,6 @@ __global__ void __launch_bounds__(LC_THREADS) k_leg_counts(int rmax, const int32
   const int2* rz = rows_sh + stride;
   const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long ws = 0;
-  int mx = 0;
   if (o < norb) {
     const int2 q = orb[o];
     const int x1 = q.x, y1 = q.y;
@@ -98,32 +98,21 @@ __global__ void __launch_bounds__(LC_THREADS) k_leg_counts(int rmax, const int32
           if (hi >= lo) n += hi - lo + 1;
         }
     }
-    Nm[(size_t)c * norb + o] = (int32_t)n;
+    Nm[(size_t)c * norb + o] = (int32_t)n;  // n <= N(Y) < 2^31 (checked on the host)
     ws = (unsigned long long)n * ((y1 == 0 || y1 == x1) ? 4ull : 8ull);
-    mx = (int)n;
   }
   ws = warp_sum(ws);
-  for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-    wsh[w] = ws;
-    msh[w] = mx;
-  }
+  if ((threadIdx.x & 31) == 0) wsh[threadIdx.x >> 5] = ws;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long t = 0;
-    int m = 0;
-    for (int k = 0; k < LC_THREADS / 32; ++k) {
-      t += wsh[k];
-      m = max(m, msh[k]);
-    }
+    for (int k = 0; k < LC_THREADS / 32; ++k) t += wsh[k];
     if (t) atomicAdd(&colsum[c], t);
-    if (m) atomicMax(&colmax[c], m);
   }
 }
 
 __global__ void __launch_bounds__(256) k_gram(const int32_t* __restrict__ Nm, const int2* __restrict__ orb,
-                                              int64_t norb, int ncol, unsigned long long* G) {
+                                              int64_t norb, int ncol, unsigned long long* G, double* Gf) {
   __shared__ int32_t sa[32][33], sb[32][33];
   __shared__ int ssh[32];
   // lower tile (ti, tj), ti >= tj, of the ncol x ncol output
@@ -133,7 +122,8 @@ __global__ void __launch_bounds__(256) k_gram(const int32_t* __restrict__ Nm, co
   while ((ti + 1) * (ti + 2) / 2 <= id) ++ti;
   const int64_t tj = id - ti * (ti + 1) / 2;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  long long acc[4] = {0, 0, 0, 0};
+  unsigned long long acc[4] = {0, 0, 0, 0};
+  double accf[4] = {0.0, 0.0, 0.0, 0.0};  // FP64 shadow of the same sums: detects an entry beyond 2^63
   const int64_t o0 = (int64_t)blockIdx.y * GRAM_CHUNK, o1 = min(norb, o0 + GRAM_CHUNK);
   for (int64_t ob = o0; ob < o1; ob += 32) {
     for (int e = threadIdx.x; e < 1024; e += 256) {
@@ -155,26 +145,38 @@ __global__ void __launch_bounds__(256) k_gram(const int32_t* __restrict__ Nm, co
     __syncthreads();
 #pragma unroll 4
     for (int j = 0; j < 32; ++j) {
-      const long long b = sb[tx][j];
+      const unsigned long long b = (unsigned)sb[tx][j];
       const int sh = ssh[j];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) acc[k] += ((long long)sa[ty + 8 * k][j] * b) << sh;
+      for (int k = 0; k < 4; ++k) {
+        const unsigned long long p = ((unsigned long long)(unsigned)sa[ty + 8 * k][j] * b) << sh;
+        acc[k] += p;
+        accf[k] += (double)p;
+      }
     }
     __syncthreads();
   }
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int64_t r = ti * 32 + ty + 8 * k, c = tj * 32 + tx;
-    if (r < ncol && c < ncol && r >= c && acc[k] != 0) atomicAdd(&G[(size_t)r * ncol + c], (unsigned long long)acc[k]);
+    if (r < ncol && c < ncol && r >= c && acc[k] != 0) {
+      atomicAdd(&G[(size_t)r * ncol + c], acc[k]);
+      atomicAdd(&Gf[(size_t)r * ncol + c], accf[k]);
+    }
   }
 }
 
-__global__ void k_kappa(int ncol, const unsigned long long* __restrict__ G, const int32_t* __restrict__ ctri,
-                        const int64_t* __restrict__ Ntri, double* kap) {
+// kappa = G / (N_tri N_tri'); an entry whose 64-bit sum wrapped or reached
+// 2^63 (its FP64 shadow disagrees, or is that large) raises *bad
+__global__ void k_kappa(int ncol, const unsigned long long* __restrict__ G, const double* __restrict__ Gf,
+                        const int32_t* __restrict__ ctri, const int64_t* __restrict__ Ntri, double* kap, int* bad) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)ncol * ncol) return;
   const int r = (int)(idx / ncol), c = (int)(idx % ncol);
-  const unsigned long long g = r >= c ? G[(size_t)r * ncol + c] : G[(size_t)c * ncol + r];
+  const size_t l = r >= c ? (size_t)r * ncol + c : (size_t)c * ncol + r;
+  const unsigned long long g = G[l];
+  const double gf = Gf[l];
+  if (gf >= 9.2e18 || g >= (1ull << 63) || fabs(__ull2double_rn(g) - gf) > 1e-9 * gf) atomicExch(bad, 1);
   kap[idx] = __ll2double_rn((long long)g) / (__ll2double_rn(Ntri[ctri[r]]) * __ll2double_rn(Ntri[ctri[c]]));
 }
 
@@ -253,6 +255,9 @@ int wl_couplings(cov_handle* h, cudaStream_t s) {
     ooff[A + 1] = (int64_t)orb.size();
   }
   const int64_t ncol_all = h->kcoff_h[nl], sq = h->koff_h[nl];
+  // a leg count is at most the lattice points of one annulus, < 3.2 (rmax + 1)^2
+  if (3.2 * ((double)h->rmax + 1.0) * ((double)h->rmax + 1.0) >= 2147483647.0)
+    return wl_fail(h, COV_ERR_INVALID, "exact couplings: l_max / l_f too large for 32-bit leg counts");
   std::vector<ColDesc> cd((size_t)ncol_all);
   for (int64_t k = 0; k < ncol_all; ++k) {
     const int Y = h->kyz_h[2 * k], Z = h->kyz_h[2 * k + 1];
@@ -263,16 +268,17 @@ int wl_couplings(cov_handle* h, cudaStream_t s) {
     nm_bytes = std::max(nm_bytes, (size_t)4 * (size_t)(ooff[A + 1] - ooff[A]) * (size_t)h->kn_h[A]);
   const size_t resident = wl_coupling_bytes(h);
   const size_t transient = nm_bytes + sizeof(int2) * orb.size() + sizeof(ColDesc) * cd.size() +
-                           (8 + 4 + 4) * (size_t)ncol_all;
+                           (8 + 4) * (size_t)ncol_all + 8 * (size_t)sq;
   if (h->budget && h->allocated + resident + transient > h->budget)
     return wl_fail(h, COV_ERR_NOMEM, "hbm_budget exceeded by the exact couplings");
-  DevTmp d_orb, d_cd, d_nm, d_sum, d_max, d_ctri;
+  DevTmp d_orb, d_cd, d_nm, d_sum, d_ctri, d_gf, d_bad;
   WL_CHECK(h, cudaMalloc(&d_orb.p, sizeof(int2) * std::max<size_t>(orb.size(), 1)));
   WL_CHECK(h, cudaMalloc(&d_cd.p, sizeof(ColDesc) * (size_t)ncol_all));
   WL_CHECK(h, cudaMalloc(&d_nm.p, nm_bytes));
   WL_CHECK(h, cudaMalloc(&d_sum.p, 8 * (size_t)ncol_all));
-  WL_CHECK(h, cudaMalloc(&d_max.p, 4 * (size_t)ncol_all));
   WL_CHECK(h, cudaMalloc(&d_ctri.p, 4 * (size_t)ncol_all));
+  WL_CHECK(h, cudaMalloc(&d_gf.p, 8 * (size_t)sq));
+  WL_CHECK(h, cudaMalloc(&d_bad.p, sizeof(int)));
   WL_CHECK(h, cudaMalloc(&h->kgram, 8 * (size_t)sq));
   WL_CHECK(h, cudaMalloc(&h->kap, 8 * (size_t)sq));
   WL_CHECK(h, cudaMalloc(&h->kcol, 4 * h->kcol_h.size()));
@@ -287,8 +293,9 @@ int wl_couplings(cov_handle* h, cudaStream_t s) {
   WL_CHECK(h, cudaMemcpyAsync(h->kn, h->kn_h.data(), 4 * (size_t)nl, cudaMemcpyHostToDevice, s));
   WL_CHECK(h, cudaMemcpyAsync(h->koff, h->koff_h.data(), 8 * (size_t)(nl + 1), cudaMemcpyHostToDevice, s));
   WL_CHECK(h, cudaMemsetAsync(d_sum.p, 0, 8 * (size_t)ncol_all, s));
-  WL_CHECK(h, cudaMemsetAsync(d_max.p, 0, 4 * (size_t)ncol_all, s));
   WL_CHECK(h, cudaMemsetAsync(h->kgram, 0, 8 * (size_t)sq, s));
+  WL_CHECK(h, cudaMemsetAsync(d_gf.p, 0, 8 * (size_t)sq, s));
+  WL_CHECK(h, cudaMemsetAsync(d_bad.p, 0, sizeof(int), s));
   const size_t shb = sizeof(int2) * 2 * ((size_t)h->rmax + 1);
   if (shb > 48 * 1024)
     WL_CHECK(h, cudaFuncSetAttribute(k_leg_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
@@ -299,40 +306,31 @@ int wl_couplings(cov_handle* h, cudaStream_t s) {
     const int2* o = (const int2*)d_orb.p + ooff[A];
     const ColDesc* c = (const ColDesc*)d_cd.p + h->kcoff_h[A];
     unsigned long long* csum = (unsigned long long*)d_sum.p + h->kcoff_h[A];
-    int* cmax = (int*)d_max.p + h->kcoff_h[A];
     dim3 g1((unsigned)((norb + LC_THREADS - 1) / LC_THREADS), (unsigned)ncol);
-    k_leg_counts<<<g1, LC_THREADS, shb, s>>>(h->rmax, h->rowtab, o, norb, c, (int32_t*)d_nm.p, csum, cmax);
+    k_leg_counts<<<g1, LC_THREADS, shb, s>>>(h->rmax, h->rowtab, o, norb, c, (int32_t*)d_nm.p, csum);
     const int64_t nt = (ncol + 31) / 32;
     dim3 g2((unsigned)(nt * (nt + 1) / 2), (unsigned)((norb + GRAM_CHUNK - 1) / GRAM_CHUNK));
-    k_gram<<<g2, 256, 0, s>>>((const int32_t*)d_nm.p, o, norb, ncol, h->kgram + h->koff_h[A]);
+    k_gram<<<g2, 256, 0, s>>>((const int32_t*)d_nm.p, o, norb, ncol, h->kgram + h->koff_h[A],
+                              (double*)d_gf.p + h->koff_h[A]);
     const int64_t nn = (int64_t)ncol * ncol;
-    k_kappa<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(ncol, h->kgram + h->koff_h[A],
+    k_kappa<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(ncol, h->kgram + h->koff_h[A], (double*)d_gf.p + h->koff_h[A],
                                                          (const int32_t*)d_ctri.p + h->kcoff_h[A], h->Ntri,
-                                                         h->kap + h->koff_h[A]);
+                                                         h->kap + h->koff_h[A], (int*)d_bad.p);
     WL_LAUNCH(h, "exact coupling kernels");
   }
   // checks: every column sums to the N_tri of its triangle (the counting
-  // kernel's own result), and no Gram entry can leave int64:
-  // G[c][c'] <= max_q n_c'(q) * sum_q w_q n_c(q) = max n_c' * N_tri(c)
+  // kernel's own result); no Gram entry left int64 (the FP64 shadow sums)
   std::vector<unsigned long long> csum((size_t)ncol_all);
-  std::vector<int> cmax((size_t)ncol_all);
   std::vector<int64_t> ntri_h((size_t)h->ntri);
+  int bad = 0;
   WL_CHECK(h, cudaMemcpyAsync(csum.data(), d_sum.p, 8 * (size_t)ncol_all, cudaMemcpyDeviceToHost, s));
-  WL_CHECK(h, cudaMemcpyAsync(cmax.data(), d_max.p, 4 * (size_t)ncol_all, cudaMemcpyDeviceToHost, s));
   WL_CHECK(h, cudaMemcpyAsync(ntri_h.data(), h->Ntri, 8 * (size_t)h->ntri, cudaMemcpyDeviceToHost, s));
+  WL_CHECK(h, cudaMemcpyAsync(&bad, d_bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   WL_CHECK(h, cudaStreamSynchronize(s));
-  for (int A = 0; A < nl; ++A) {
-    int64_t bigsum = 0;
-    int bigmax = 0;
-    for (int64_t k = h->kcoff_h[A]; k < h->kcoff_h[A + 1]; ++k) {
-      if ((int64_t)csum[k] != ntri_h[h->ktri_h[k]])
-        return wl_fail(h, COV_ERR_CUDA, "exact couplings: a leg-count column does not sum to its N_tri");
-      bigsum = std::max(bigsum, ntri_h[h->ktri_h[k]]);
-      bigmax = std::max(bigmax, cmax[k]);
-    }
-    if ((unsigned __int128)bigmax * (unsigned __int128)bigsum >= ((unsigned __int128)1 << 63))
-      return wl_fail(h, COV_ERR_INVALID, "exact couplings: a Gram entry could exceed int64 for this binning");
-  }
+  for (int64_t k = 0; k < ncol_all; ++k)
+    if ((int64_t)csum[k] != ntri_h[h->ktri_h[k]])
+      return wl_fail(h, COV_ERR_CUDA, "exact couplings: a leg-count column does not sum to its N_tri");
+  if (bad) return wl_fail(h, COV_ERR_INVALID, "exact couplings: a Gram entry exceeds int64 for this binning");
   return COV_OK;
 }
 

@@ -6,7 +6,8 @@ dictionaries of the workloads module.  Output:
 tests/golden/coupling_<workload>.txt, per ell bin A a line
 "A <bin> <ncol> <sha256>" (the sha256 of the ncol x ncol Gram matrix as
 little-endian int64, row-major, columns in the order of the lines below),
-then one line "C <Y> <Z> <G_cc> <sum_c' G_cc'>" per column.
+then one line "C <Y> <Z> <G_cc> <sum_c' G_cc'>" per column (the row sum as an exact
+integer: the entries reach 2^62.7 and a row sum can pass 2^63).
 
     python tests/golden/make_coupling.py cfg2_5bin cfg3_10bin
 """
@@ -45,7 +46,7 @@ def main(names):
             for A in range(len(s_lo)):
                 fh.write(f"A {A} {len(cols[A])} {digest(G[A])}\n")
                 for c, (Y, Z) in enumerate(cols[A]):
-                    fh.write(f"C {Y} {Z} {int(G[A][c, c])} {int(G[A][c].sum())}\n")
+                    fh.write(f"C {Y} {Z} {int(G[A][c, c])} {sum(int(v) for v in G[A][c])}\n")
         print(path)
 
 
