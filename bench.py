@@ -50,8 +50,9 @@ def parse():
     p.add_argument("--no-snr-run", action="store_true")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-batch", action="store_true")
-    p.add_argument("--batch-bins", default="3,5",
-                   help="tomographic bin counts of the batched Fisher run (n_t:n for the first n cosmologies only)")
+    p.add_argument("--batch-bins", default="3,5,10:2",
+                   help="tomographic bin counts of the batched Fisher run (n_t:n for the first n cosmologies only; "
+                        "the 10-bin set-up takes ~23 s per cosmology, so the default times two of its 64)")
     p.add_argument("--snr-10bin", action="store_true",
                    help="also time the P and B cumulative S/N of the workload itself (besides the joint one), "
                         "in place on packed tiles, per --snr-rows")
@@ -321,6 +322,11 @@ def packed_tiles(M):
     return nt * (nt + 1) // 2
 
 
+# 2.75 GB per band at cfg3_10bin: 16 bands of 8.3 GB copied to larger pinned
+# buffers measured 30% slower end to end
+E2E_BANDS = 48
+
+
 def band_cuts(M, n_chunks):
     """Tile-row boundaries giving bands of roughly equal tile counts."""
     import math
@@ -390,8 +396,8 @@ def timed(stream, fn, steps, h, world):
 # fingerprinted.
 TRAFFIC = {
     # workload: (bytes per band call, fingerprint at capture); profiles/k_syrk_pair_cfg3_4bin.md
-    "cfg3_4bin": (23.68e9, "c8a3a44e0073fa0d"),
-    "cfg3_10bin": (23.68e9 * 251695 / 1326, "c8a3a44e0073fa0d"),  # scaled by tiles from cfg3_4bin
+    "cfg3_4bin": (28.18e9, "f06215df88edc9d3"),
+    "cfg3_10bin": (28.18e9 * 251695 / 1326, "f06215df88edc9d3"),  # scaled by tiles from cfg3_4bin
 }
 
 
@@ -932,7 +938,7 @@ def run_ours(args):
             clocks = clk.stop()
             # e2e through the public API: the covariance streamed to the host in
             # bands of about equal size, band k+1 computed while band k is copied
-            cuts = band_cuts(M, 48)
+            cuts = band_cuts(M, E2E_BANDS)
             bands = list(zip(cuts[:-1], cuts[1:]))
             nmax = max(packed_tiles(b) - packed_tiles(a) for a, b in bands) * TILE * TILE
             dbuf = [torch.empty(nmax, dtype=torch.float64, device=dev) for _ in range(2)]

@@ -41,6 +41,22 @@ static cudaEvent_t ev_get(cov_handle* h) {
   return e;
 }
 
+// The handle's side stream (and the two events that order it against the
+// caller's stream), created once.  Its work is the short critical chain beside
+// a long tensor-core launch on the caller's stream (the per-element products
+// of the previous sub-band; the next Cholesky panel), so it runs at the
+// greatest priority: the block scheduler then places its blocks before the
+// long launch's pending ones as SM room frees up.
+int wl_side_stream(cov_handle* h) {
+  if (h->side) return COV_OK;
+  int least = 0, greatest = 0;
+  WL_CHECK(h, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  WL_CHECK(h, cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, greatest));
+  WL_CHECK(h, cudaEventCreateWithFlags(&h->ev_cols, cudaEventDisableTiming));
+  WL_CHECK(h, cudaEventCreateWithFlags(&h->ev_panel, cudaEventDisableTiming));
+  return COV_OK;
+}
+
 int wl_stage_begin(cov_handle* h, int stage, cudaStream_t s) {
   if (!h->prof) return -1;
   StageEvent se{stage, ev_get(h), ev_get(h)};

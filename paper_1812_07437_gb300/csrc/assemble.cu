@@ -544,11 +544,7 @@ int wl_assemble_band(cov_handle* h, int64_t row0, int64_t nrows, OutMap out, uns
   };
   if (precision != COV_FP64 && (terms & COV_TERM_1H)) {
     const int nssc = (terms & COV_TERM_SSC) ? h->nchi : 0;
-    if (!h->side) {
-      WL_CHECK(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
-      WL_CHECK(h, cudaEventCreateWithFlags(&h->ev_cols, cudaEventDisableTiming));
-      WL_CHECK(h, cudaEventCreateWithFlags(&h->ev_panel, cudaEventDisableTiming));
-    }
+    if ((rc = wl_side_stream(h))) return rc;
     // sub-band cuts at tile rows, about equal numbers of tiles each
     const int64_t ta = row0 / 256, tb = (row1 + 255) / 256;
     const int nsub = (int)std::min<int64_t>(8, tb - ta);

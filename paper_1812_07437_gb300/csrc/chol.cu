@@ -94,15 +94,34 @@ __global__ void k_potrf_diag(OutMap W, int64_t k0, int kb, int* status) {
     }
 }
 
-// The same factorisation with the rank-1 updates enumerated through a table:
-// the pairs (i, l), l <= i < 64, ordered by l descending, so that step j's
-// active pairs (l > j) are the first T_j = (63 - j)(64 - j) / 2 entries.  All
-// 256 threads work on active elements only (a warp-wide FP64 instruction
-// costs the same with idle lanes), with one shared-memory read to decode.
-__global__ void __launch_bounds__(256) k_potrf_table(OutMap W, int64_t k0, int kb, int* status) {
+// The same factorisation with the pivot of step j + 1 taken off the critical
+// path.  Once column j is scaled, lane 0 of warp 0 applies column j to the
+// next diagonal entry and takes its square root and reciprocal, while warps
+// 1-7 apply column j to the other active pairs.  The pairs (i, l),
+// l <= i < 64, are enumerated through a table ordered by l descending, so that
+// step j's active pairs (l > j) are its first (63 - j)(64 - j) / 2 entries and
+// the next diagonal entry (j + 1, j + 1) is entry (62 - j)(63 - j) / 2.  Every
+// element receives the same FMAs, scalings and square roots in the same order
+// as in the plain right-looking loop, so the factor is the same bit for bit;
+// each step has two barriers instead of three, and its square root and
+// division run beside its update.  (FP64 work is kept on single lanes or
+// spread over all four schedulers: on this part a warp-wide FP64 instruction
+// confined to one scheduler is slow.)
+__device__ __forceinline__ void potrf_pivot(double (*L)[NB + 1], double* inv, int j, int* status) {
+  double d = L[j][j];
+  if (!(d > 0.0)) {
+    atomicExch(status, 1);
+    d = 1.0;
+  }
+  const double r = sqrt(d);
+  L[j][j] = r;
+  inv[j] = 1.0 / r;
+}
+
+__global__ void __launch_bounds__(256) k_potrf_la(OutMap W, int64_t k0, int kb, int* status) {
   __shared__ double L[NB][NB + 1];
+  __shared__ double inv[NB];
   __shared__ uint16_t pr[NB * (NB + 1) / 2];
-  __shared__ double inv_sh;
   // pair table: l = 63, 62, ..., 0; for each l, i = l .. 63
   for (int l = 0; l < NB; ++l) {
     const int base = (NB - 1 - l) * (NB - l) / 2;  // entries before column l (columns l+1..63)
@@ -113,25 +132,26 @@ __global__ void __launch_bounds__(256) k_potrf_table(OutMap W, int64_t k0, int k
     L[i][l] = (i < kb && l <= i) ? *W.at(k0 + i, k0 + l) : 0.0;
   }
   __syncthreads();
+  if (threadIdx.x == 0) potrf_pivot(L, inv, 0, status);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5;
   for (int j = 0; j < kb; ++j) {
-    if (threadIdx.x == 0) {
-      double d = L[j][j];
-      if (!(d > 0.0)) {
-        atomicExch(status, 1);
-        d = 1.0;
+    const double s = inv[j];
+    for (int i = j + 1 + (int)threadIdx.x; i < kb; i += blockDim.x) L[i][j] *= s;
+    __syncthreads();
+    if (warp == 0) {
+      if (threadIdx.x == 0 && j + 1 < kb) {
+        L[j + 1][j + 1] -= L[j + 1][j] * L[j + 1][j];
+        potrf_pivot(L, inv, j + 1, status);
       }
-      const double r = sqrt(d);
-      L[j][j] = r;
-      inv_sh = 1.0 / r;  // one FP64 division per step, shared by all threads
-    }
-    __syncthreads();
-    const double inv = inv_sh;
-    for (int i = j + 1 + (int)threadIdx.x; i < kb; i += blockDim.x) L[i][j] *= inv;
-    __syncthreads();
-    const int tj = (NB - 1 - j) * (NB - j) / 2;  // active pairs: l > j
-    for (int e = threadIdx.x; e < tj; e += blockDim.x) {
-      const int pe = pr[e], i = pe & 255, l = pe >> 8;
-      L[i][l] -= L[i][j] * L[l][j];
+    } else {
+      const int tj = (NB - 1 - j) * (NB - j) / 2;        // active pairs: l > j
+      const int skip = (NB - 2 - j) * (NB - 1 - j) / 2;  // (j + 1, j + 1): lane 0 of warp 0
+      for (int e = (int)threadIdx.x - 32; e < tj; e += (int)blockDim.x - 32) {
+        if (e == skip) continue;
+        const int pe = pr[e], i = pe & 255, l = pe >> 8;
+        L[i][l] -= L[i][j] * L[l][j];
+      }
     }
     __syncthreads();
   }
@@ -256,12 +276,7 @@ static int chol_scratch(cov_handle* h, int64_t Ms, size_t* one_buf) {
     h->allocated += need_sc;
   }
   if (!h->chol_status) WL_CHECK(h, cudaMalloc(&h->chol_status, sizeof(int)));
-  if (!h->side) {
-    WL_CHECK(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
-    WL_CHECK(h, cudaEventCreateWithFlags(&h->ev_cols, cudaEventDisableTiming));
-    WL_CHECK(h, cudaEventCreateWithFlags(&h->ev_panel, cudaEventDisableTiming));
-  }
-  return COV_OK;
+  return wl_side_stream(h);
 }
 
 // Blocked right-looking Cholesky of the leading Ms x Ms block of the
@@ -285,8 +300,12 @@ static int factor_and_prefix(cov_handle* h, OutMap Wm, int64_t Ms, const int64_t
   uint8_t* bufs[2] = {(uint8_t*)h->chol_scratch, (uint8_t*)h->chol_scratch + one_buf};
   auto panel = [&](int64_t k0, cudaStream_t st_) -> int {
     int kb = (int)std::min<int64_t>(NB, Ms - k0);
-    k_potrf_table<<<1, 256, 0, st_>>>(Wm, k0, kb, st);
+    k_potrf_la<<<1, 256, 0, st_>>>(Wm, k0, kb, st);
     int64_t r0 = k0 + kb, r1 = Ms + 1;
+    if (wl_chol_fused_panel(h, Wm)) {
+      WL_LAUNCH(h, "k_potrf_la");
+      return wl_chol_trsm_slice(h, Wm, k0, kb, r0, r1, bufs[(k0 / NB) & 1], st_);
+    }
     if (r1 > r0)
       k_trsm_rows4<<<(unsigned)(((r1 - r0) * 4 + TR4_THREADS - 1) / TR4_THREADS), TR4_THREADS, 0, st_>>>(Wm, k0, kb,
                                                                                                      r0, r1);

@@ -6,7 +6,8 @@
 //     exact power of two 2^-e (e from its largest entry) and cut into
 //     S = 6 fixed-point slices, x 2^-e = sum_t d_t 2^(-7-8t), d_t integers in
 //     [-128, 128] stored exactly as BF16; the residual is below 2^-48 of the row
-//     maximum.
+//     maximum.  The digits are the balanced base-256 digits of the integer
+//     X = RN(x 2^(47 - e)), taken by integer operations from the bits of x.
 //   * k_chol_update: per 128 x 64 lower tile of the trailing matrix, the
 //     products d_t(i) . d_u(j) over the panel's K = 64 are exact in FP32
 //     (|d d| <= 2^14, 64 terms -> 2^20), and so are their sums over the pairs
@@ -39,6 +40,51 @@
 #define CS_SMEM (CS_STAGE + CS_CTILE + 1024)
 #define CS_SPIN (1u << 22)
 
+// X = RN(x 2^(47 - e)) (ties to even) for |x| < 2^e, by integer operations on
+// the bits of x (x = m 2^(E' - 1075), m the 53-bit significand): |X| <= 2^47.
+// The FP64 pipe of this part is narrow, and any exact digit scheme of the
+// same X gives the same slices' value.
+__device__ __forceinline__ long long slice_int(double x, int e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FFu);
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (E ? (1ull << 52) : 0ull);
+  const int sh = 1028 + e - (E ? E : 1);  // X = RN(m / 2^sh); sh >= 6 unless the row holds only subnormals
+  unsigned long long q;
+  if (sh <= 0) {
+    q = m << (-sh < 63 ? -sh : 63);
+  } else if (sh >= 64) {
+    q = 0;
+  } else {
+    q = m >> sh;
+    const unsigned long long rem = m & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (q & 1ull))) ++q;
+  }
+  return (b >> 63) ? -(long long)q : (long long)q;
+}
+
+// BF16 bits of an integer |d| <= 255 (exact: at most 8 significant bits)
+__device__ __forceinline__ unsigned short bf16_bits_of_int(int d) {
+  if (d == 0) return 0;
+  const unsigned a = (unsigned)(d < 0 ? -d : d);
+  const int p = 31 - __clz((int)a);  // leading bit
+  const unsigned bits = ((unsigned)(127 + p) << 7) | ((a << (7 - p)) & 0x7Fu);
+  return (unsigned short)(bits | (d < 0 ? 0x8000u : 0u));
+}
+
+// the six balanced base-256 digits of X (d_0 most significant): d_1..d_5 in
+// [-128, 127], d_0 in [-128, 128] since |X| <= 2^47; written as BF16 to
+// out + t * stride
+__device__ __forceinline__ void slice_store(long long X, __nv_bfloat16* out, size_t stride) {
+#pragma unroll
+  for (int t = CS_S - 1; t >= 1; --t) {
+    int lo = (int)(X & 255);
+    lo = lo >= 128 ? lo - 256 : lo;
+    X = (X - lo) >> 8;
+    out[(size_t)t * stride] = __ushort_as_bfloat16(bf16_bits_of_int(lo));
+  }
+  out[0] = __ushort_as_bfloat16(bf16_bits_of_int((int)X));
+}
+
 // slices of the panel rows r0..r1-1 (columns k0..k0+kb-1 of the workspace);
 // rows up to the padded count are written (zeros past r1)
 __global__ void k_chol_slice(const OutMap W, int64_t k0, int kb, int64_t r0, int64_t nrows, int64_t nrows_pad,
@@ -56,15 +102,10 @@ __global__ void k_chol_slice(const OutMap W, int64_t k0, int kb, int64_t r0, int
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   int e = 0;
   if (mx > 0.0) frexp(mx, &e);
-  double s0 = ldexp(x0, 7 - e), s1 = ldexp(x1, 7 - e);  // |s| < 128
-  for (int t = 0; t < CS_S; ++t) {
-    double d0 = rint(s0), d1 = rint(s1);
-    s0 = (s0 - d0) * 256.0;
-    s1 = (s1 - d1) * 256.0;
-    __nv_bfloat16* out = slices + ((size_t)t * nrows_pad + r) * CS_K;
-    out[lane] = __float2bfloat16_rn((float)d0);
-    out[lane + 32] = __float2bfloat16_rn((float)d1);
-  }
+  const size_t stride = (size_t)nrows_pad * CS_K;
+  __nv_bfloat16* out = slices + (size_t)r * CS_K;
+  slice_store(slice_int(x0, e), out + lane, stride);
+  slice_store(slice_int(x1, e), out + lane + 32, stride);
   if (lane == 0) rexp[r] = e;
 }
 
@@ -751,16 +792,77 @@ __global__ void k_chol_slice_abs(const OutMap W, int64_t k0, int kb, int64_t sba
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   int e = 0;
   if (mx > 0.0) frexp(mx, &e);
-  double s0 = ldexp(x0, 7 - e), s1 = ldexp(x1, 7 - e);  // |s| < 128
-  for (int t = 0; t < CS_S; ++t) {
-    double d0 = rint(s0), d1 = rint(s1);
-    s0 = (s0 - d0) * 256.0;
-    s1 = (s1 - d1) * 256.0;
-    __nv_bfloat16* out = slices + ((size_t)t * pad + i) * CS_K;
-    out[lane] = __float2bfloat16_rn((float)d0);
-    out[lane + 32] = __float2bfloat16_rn((float)d1);
-  }
+  const size_t stride = (size_t)pad * CS_K;
+  __nv_bfloat16* out = slices + (size_t)i * CS_K;
+  slice_store(slice_int(x0, e), out + lane, stride);
+  slice_store(slice_int(x1, e), out + lane + 32, stride);
   if (lane == 0) rexp[i] = e;
+}
+
+// The panel solve and the slicing in one pass, in the persistent update's
+// 128-aligned slice layout: each row sbase + i (i < pad) inside [r0, r1)
+// solves x L11^T = a by forward substitution (four lanes per row, lane q
+// owning the entries j = q mod 4, the solved entry of column l passed to the
+// group by a shuffle), is written back, and is cut into slices from the same
+// registers; rows outside [r0, r1) get zero slices.  The arithmetic of both
+// steps is that of the two separate passes (k_trsm_rows4, k_chol_slice_abs),
+// so the factor and the slices are the same bit for bit, one launch and one
+// read of the panel rows fewer.
+#define TS_THREADS 128
+__global__ void __launch_bounds__(TS_THREADS) k_trsm_slice(OutMap W, int64_t k0, int kb, int64_t sbase, int64_t r0,
+                                                           int64_t r1, int64_t pad, __nv_bfloat16* slices,
+                                                           int* rexp) {
+  __shared__ double L[CS_K][CS_K + 1];
+  __shared__ double invd[CS_K];
+  for (int e = threadIdx.x; e < CS_K * CS_K; e += blockDim.x) {
+    const int i = e >> 6, l = e & 63;
+    L[i][l] = (i < kb && l <= i) ? *W.at(k0 + i, k0 + l) : 0.0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kb; i += blockDim.x) invd[i] = 1.0 / L[i][i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, q = lane & 3, g4 = lane & ~3;
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 4;
+  const int64_t r = sbase + i;
+  const bool in = i < pad;
+  const bool valid = in && r >= r0 && r < r1;
+  double* row = valid ? W.at(r, k0) : nullptr;
+  double a[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) a[m] = (valid && q + 4 * m < kb) ? row[q + 4 * m] : 0.0;
+#pragma unroll
+  for (int l = 0; l < CS_K; ++l) {
+    if (l >= kb) break;
+    if (q == (l & 3)) a[l >> 2] *= invd[l];
+    const double xl = __shfl_sync(0xffffffffu, a[l >> 2], g4 + (l & 3));
+#pragma unroll
+    for (int m = (l + 1) / 4; m < 16; ++m) {
+      const int j = q + 4 * m;
+      if (j > l) a[m] = fma(-xl, L[j][l], a[m]);
+    }
+  }
+  if (valid) {
+#pragma unroll
+    for (int m = 0; m < 16; ++m)
+      if (q + 4 * m < kb) row[q + 4 * m] = a[m];
+  }
+  // slicing: the row's largest magnitude over its four lanes, then six slices
+#pragma unroll
+  for (int m = 0; m < 16; ++m)
+    if (q + 4 * m >= kb) a[m] = 0.0;
+  double mx = 0.0;
+#pragma unroll
+  for (int m = 0; m < 16; ++m) mx = fmax(mx, fabs(a[m]));
+  mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+  mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+  int e = 0;
+  if (mx > 0.0) frexp(mx, &e);
+  if (!in) return;
+  const size_t stride = (size_t)pad * CS_K;
+  __nv_bfloat16* out = slices + (size_t)i * CS_K + q;
+#pragma unroll
+  for (int m = 0; m < 16; ++m) slice_store(slice_int(a[m], e), out + 4 * m, stride);
+  if (q == 0) rexp[i] = e;
 }
 
 // whether the persistent kernel serves this workspace: it addresses the FP64
@@ -802,6 +904,22 @@ int wl_chol_slice(cov_handle* h, OutMap W, int64_t k0, int kb, int64_t r0, int64
   int* rexp = (int*)((uint8_t*)buf + (size_t)CS_S * pad * CS_K * 2);
   k_chol_slice<<<(unsigned)((pad + 7) / 8), 256, 0, s>>>(W, k0, kb, r0, n, pad, slices, rexp);
   WL_LAUNCH(h, "k_chol_slice");
+  return COV_OK;
+}
+
+bool wl_chol_fused_panel(const cov_handle* h, const OutMap& W) { return pu_usable(h, W); }
+
+// the panel solve of rows r0..r1-1 against the factored diagonal block at k0,
+// fused with their slicing (only where wl_chol_fused_panel holds)
+int wl_chol_trsm_slice(cov_handle* h, OutMap W, int64_t k0, int kb, int64_t r0, int64_t r1, void* buf,
+                       cudaStream_t s) {
+  if (r1 <= r0) return COV_OK;
+  const int64_t sbase = r0 / CS_BI * CS_BI, pad = (r1 - sbase + CS_BI - 1) / CS_BI * CS_BI;
+  __nv_bfloat16* slices = (__nv_bfloat16*)buf;
+  int* rexp = (int*)((uint8_t*)buf + (size_t)CS_S * pad * CS_K * 2);
+  // four threads per row: pad / 32 blocks of 128 threads cover the pad rows exactly
+  k_trsm_slice<<<(unsigned)(pad * 4 / TS_THREADS), TS_THREADS, 0, s>>>(W, k0, kb, sbase, r0, r1, pad, slices, rexp);
+  WL_LAUNCH(h, "k_trsm_slice");
   return COV_OK;
 }
 

@@ -266,6 +266,10 @@ size_t wl_handle_bytes(const cov_handle* h);
 void wl_set_global_error(const std::string& msg);  // api.cu: read by cov_last_error(NULL)
 size_t wl_chol_tc_bytes(int64_t n);  // chol_tc.cu
 int wl_chol_slice(cov_handle* h, OutMap W, int64_t k0, int kb, int64_t r0, int64_t r1, void* buf, cudaStream_t s);
+bool wl_chol_fused_panel(const cov_handle* h, const OutMap& W);  // chol_tc.cu
+int wl_side_stream(cov_handle* h);  // api.cu: the handle's high-priority side stream
+int wl_chol_trsm_slice(cov_handle* h, OutMap W, int64_t k0, int kb, int64_t r0, int64_t r1, void* buf,
+                       cudaStream_t s);
 int wl_chol_update(cov_handle* h, OutMap W, int64_t r0, int64_t r1, const void* buf, int tj0, int ntj, int* status,
                    cudaStream_t s);
 int wl_syrk_tc_rows(cov_handle* h, const void* hi, const void* lo, const double* rscale, int64_t rows, int Kp,
