@@ -96,26 +96,28 @@ __global__ void k_potrf_diag(OutMap W, int64_t k0, int kb, int* status) {
 
 // The same factorisation with the pivot of step j + 1 taken off the critical
 // path.  Once column j is scaled, lane 0 of warp 0 applies column j to the
-// next diagonal entry and takes its square root and reciprocal, while warps
-// 1-7 apply column j to the other active pairs.  The pairs (i, l),
-// l <= i < 64, are enumerated through a table ordered by l descending, so that
-// step j's active pairs (l > j) are its first (63 - j)(64 - j) / 2 entries and
-// the next diagonal entry (j + 1, j + 1) is entry (62 - j)(63 - j) / 2.  Every
-// element receives the same FMAs, scalings and square roots in the same order
-// as in the plain right-looking loop, so the factor is the same bit for bit;
-// each step has two barriers instead of three, and its square root and
-// division run beside its update.  (FP64 work is kept on single lanes or
-// spread over all four schedulers: on this part a warp-wide FP64 instruction
-// confined to one scheduler is slow.)
+// next diagonal entry and takes its pivot, while warps 1-7 apply column j to
+// the other active pairs.  The pairs (i, l), l <= i < 64, are enumerated
+// through a table ordered by l descending, so that step j's active pairs
+// (l > j) are its first (63 - j)(64 - j) / 2 entries and the next diagonal
+// entry (j + 1, j + 1) is entry (62 - j)(63 - j) / 2.  Every element receives
+// the same FMAs and scalings in the same order as in the plain right-looking
+// loop; each step has two barriers instead of three, and its pivot runs beside
+// its update.  On this part a dependent FP64 operation takes 64 cycles or more
+// and one warp issues at most one FP64 instruction per 64 cycles (idle lanes
+// cost the same as active ones), so the update is spread over seven warps and
+// the sequential pivot chain is kept short: 1 / sqrt(d) by the reciprocal
+// square root and sqrt(d) as d times it (within 2 ulp of the rounded root;
+// ~430 cycles together) instead of a square root and a division (~600 + ~360).
 __device__ __forceinline__ void potrf_pivot(double (*L)[NB + 1], double* inv, int j, int* status) {
   double d = L[j][j];
   if (!(d > 0.0)) {
     atomicExch(status, 1);
     d = 1.0;
   }
-  const double r = sqrt(d);
-  L[j][j] = r;
-  inv[j] = 1.0 / r;
+  const double ir = rsqrt(d);
+  L[j][j] = d * ir;
+  inv[j] = ir;
 }
 
 __global__ void __launch_bounds__(256) k_potrf_la(OutMap W, int64_t k0, int kb, int* status) {

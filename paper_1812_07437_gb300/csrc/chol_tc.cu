@@ -801,14 +801,18 @@ __global__ void k_chol_slice_abs(const OutMap W, int64_t k0, int kb, int64_t sba
 
 // The panel solve and the slicing in one pass, in the persistent update's
 // 128-aligned slice layout: each row sbase + i (i < pad) inside [r0, r1)
-// solves x L11^T = a by forward substitution (four lanes per row, lane q
-// owning the entries j = q mod 4, the solved entry of column l passed to the
-// group by a shuffle), is written back, and is cut into slices from the same
-// registers; rows outside [r0, r1) get zero slices.  The arithmetic of both
-// steps is that of the two separate passes (k_trsm_rows4, k_chol_slice_abs),
-// so the factor and the slices are the same bit for bit, one launch and one
-// read of the panel rows fewer.
+// solves x L11^T = a by forward substitution, is written back, and is cut into
+// slices from the same registers; rows outside [r0, r1) get zero slices.
+// Eight lanes per row, lane q owning the entries j = q mod 8: at column l the
+// owner scales its entry by 1 / L11[l][l] and passes it to the row's other
+// lanes by a shuffle, and each lane subtracts x_l L11[j][l] from its entries
+// j > l, so every entry receives the FMAs and the scaling of the plain forward
+// substitution in its order.  On this part one warp issues at most one FP64
+// instruction per 64 cycles and an SM needs four warps to fill its FP64 pipe,
+// so rows are spread thin: 16 rows per block of four warps, one block per
+// ~16 rows of the panel.  The slice digits are integer work (slice_int).
 #define TS_THREADS 128
+#define TS_LANES 8
 __global__ void __launch_bounds__(TS_THREADS) k_trsm_slice(OutMap W, int64_t k0, int kb, int64_t sbase, int64_t r0,
                                                            int64_t r1, int64_t pad, __nv_bfloat16* slices,
                                                            int* rexp) {
@@ -821,47 +825,48 @@ __global__ void __launch_bounds__(TS_THREADS) k_trsm_slice(OutMap W, int64_t k0,
   __syncthreads();
   for (int i = threadIdx.x; i < kb; i += blockDim.x) invd[i] = 1.0 / L[i][i];
   __syncthreads();
-  const int lane = threadIdx.x & 31, q = lane & 3, g4 = lane & ~3;
-  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 4;
+  constexpr int NE = CS_K / TS_LANES;  // entries per lane
+  const int lane = threadIdx.x & 31, q = lane & (TS_LANES - 1), g = lane & ~(TS_LANES - 1);
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TS_LANES;
   const int64_t r = sbase + i;
   const bool in = i < pad;
   const bool valid = in && r >= r0 && r < r1;
   double* row = valid ? W.at(r, k0) : nullptr;
-  double a[16];
+  double a[NE];
 #pragma unroll
-  for (int m = 0; m < 16; ++m) a[m] = (valid && q + 4 * m < kb) ? row[q + 4 * m] : 0.0;
+  for (int m = 0; m < NE; ++m) a[m] = (valid && q + TS_LANES * m < kb) ? row[q + TS_LANES * m] : 0.0;
 #pragma unroll
   for (int l = 0; l < CS_K; ++l) {
     if (l >= kb) break;
-    if (q == (l & 3)) a[l >> 2] *= invd[l];
-    const double xl = __shfl_sync(0xffffffffu, a[l >> 2], g4 + (l & 3));
+    if (q == (l % TS_LANES)) a[l / TS_LANES] *= invd[l];
+    const double xl = __shfl_sync(0xffffffffu, a[l / TS_LANES], g + (l % TS_LANES));
 #pragma unroll
-    for (int m = (l + 1) / 4; m < 16; ++m) {
-      const int j = q + 4 * m;
+    for (int m = (l + 1) / TS_LANES; m < NE; ++m) {
+      const int j = q + TS_LANES * m;
       if (j > l) a[m] = fma(-xl, L[j][l], a[m]);
     }
   }
   if (valid) {
 #pragma unroll
-    for (int m = 0; m < 16; ++m)
-      if (q + 4 * m < kb) row[q + 4 * m] = a[m];
+    for (int m = 0; m < NE; ++m)
+      if (q + TS_LANES * m < kb) row[q + TS_LANES * m] = a[m];
   }
-  // slicing: the row's largest magnitude over its four lanes, then six slices
+  // slicing: the row's largest magnitude over its eight lanes, then six slices
 #pragma unroll
-  for (int m = 0; m < 16; ++m)
-    if (q + 4 * m >= kb) a[m] = 0.0;
+  for (int m = 0; m < NE; ++m)
+    if (q + TS_LANES * m >= kb) a[m] = 0.0;
   double mx = 0.0;
 #pragma unroll
-  for (int m = 0; m < 16; ++m) mx = fmax(mx, fabs(a[m]));
-  mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-  mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+  for (int m = 0; m < NE; ++m) mx = fmax(mx, fabs(a[m]));
+#pragma unroll
+  for (int o = 1; o < TS_LANES; o <<= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   int e = 0;
   if (mx > 0.0) frexp(mx, &e);
   if (!in) return;
   const size_t stride = (size_t)pad * CS_K;
   __nv_bfloat16* out = slices + (size_t)i * CS_K + q;
 #pragma unroll
-  for (int m = 0; m < 16; ++m) slice_store(slice_int(a[m], e), out + 4 * m, stride);
+  for (int m = 0; m < NE; ++m) slice_store(slice_int(a[m], e), out + TS_LANES * m, stride);
   if (q == 0) rexp[i] = e;
 }
 
@@ -917,8 +922,9 @@ int wl_chol_trsm_slice(cov_handle* h, OutMap W, int64_t k0, int kb, int64_t r0, 
   const int64_t sbase = r0 / CS_BI * CS_BI, pad = (r1 - sbase + CS_BI - 1) / CS_BI * CS_BI;
   __nv_bfloat16* slices = (__nv_bfloat16*)buf;
   int* rexp = (int*)((uint8_t*)buf + (size_t)CS_S * pad * CS_K * 2);
-  // four threads per row: pad / 32 blocks of 128 threads cover the pad rows exactly
-  k_trsm_slice<<<(unsigned)(pad * 4 / TS_THREADS), TS_THREADS, 0, s>>>(W, k0, kb, sbase, r0, r1, pad, slices, rexp);
+  // eight threads per row: pad / 16 blocks of 128 threads cover the pad rows exactly
+  k_trsm_slice<<<(unsigned)(pad * TS_LANES / TS_THREADS), TS_THREADS, 0, s>>>(W, k0, kb, sbase, r0, r1, pad, slices,
+                                                                              rexp);
   WL_LAUNCH(h, "k_trsm_slice");
   return COV_OK;
 }
