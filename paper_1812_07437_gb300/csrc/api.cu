@@ -242,7 +242,7 @@ static void free_all(cov_handle* h) {
                   h->Srows, h->cosmo_d, h->Fsig,  h->Esig,    h->Msig,   h->FsigT,  h->EsigT,     h->MsigT,
                   h->invN,  h->omN,   h->work,    h->chol_scratch, h->chol_status, h->mb, h->omb, h->cs,
                   h->cw,    h->sigF,  h->ac,      h->bmask,   h->gblk,   h->wait_flag, h->pca_buf,
-                  h->kap,   h->kgram, h->kcol,    h->kn,      h->koff};
+                  h->kap,   h->kgram, h->kcol,    h->kn,      h->koff,      h->plist};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->tile_ring) cudaFree(h->tile_ring);
@@ -331,6 +331,8 @@ int wl_request_bytes(const cov_nz* nz, const cov_bins* bins, int precision, unsi
   b += (M + 8) * (M + 1) * 8 + 2 * ((wl_chol_tc_bytes((int64_t)M + 1) + 255) / 256 * 256) + M * 4;
   size_t t = (std::max(M, nt) + 255) / 256 + 1;
   b += WL_TILE_CACHE * (t * (t + 1) / 2) * 8;                    // launch-order ring
+  const size_t nb32 = (M + 31) / 32;
+  if (terms & (COV_TERM_BBPT | COV_TERM_PB)) b += nb32 * (nb32 + 1) / 2 * 4;  // product-term block list (bound)
   b += (size_t)64 << 20;                                         // small buffers, allocation granularity
   *M_out = h.M;
   *bytes = b;

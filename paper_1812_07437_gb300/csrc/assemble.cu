@@ -106,7 +106,10 @@ __device__ double gather_element(const GatherArgs& g, const int32_t* ra, const i
 
 // lower-triangle tile index -> (ti, tj), ti >= tj
 __device__ __forceinline__ void tri_tile(int64_t id, int64_t* ti, int64_t* tj) {
-  int64_t i = (int64_t)((sqrt(8.0 * (double)id + 1.0) - 1.0) * 0.5);
+  // an FP32 estimate (the FP64 square root costs ~600 cycles on this part),
+  // corrected to the exact row by the two integer searches
+  int64_t i = (int64_t)((sqrtf(8.0f * (float)id + 1.0f) - 1.0f) * 0.5f);
+  if (i < 0) i = 0;
   while (i * (i + 1) / 2 > id) --i;
   while ((i + 1) * (i + 2) / 2 <= id) ++i;
   *ti = i;
@@ -131,13 +134,12 @@ __global__ void k_block_masks(int64_t M, int nl, const int32_t* rd, uint64_t* bm
   bm[blk] = m;
 }
 
-__global__ void k_gather(GatherArgs g, int64_t M, OutMap out, int accumulate, int64_t tile_off) {
-  __shared__ int32_t rdA[32 * 8], rdB[32 * 8];
-  int64_t ti, tj;
-  tri_tile((int64_t)blockIdx.x + tile_off, &ti, &tj);
+// The BB+PT and PB products of the 32 x 32 lower block (ti, tj), rows below M
+// only; added to the stored value (accumulate) or stored.  With no ell bin
+// common to the two row blocks every product is zero there.
+__device__ __forceinline__ void gather_block(const GatherArgs& g, int64_t M, OutMap out, int accumulate, int64_t ti,
+                                             int64_t tj, int32_t* rdA, int32_t* rdB) {
   int64_t a0 = ti * 32, b0 = tj * 32;
-  // BB+PT and PB need a leg of one row and a leg of the other in the same ell
-  // bin: with no common bin in the two blocks every element is zero here
   const bool none = (g.bmask[ti] & g.bmask[tj]) == 0;
   if (none && accumulate) return;
   int tid = threadIdx.y * 32 + threadIdx.x;
@@ -157,6 +159,23 @@ __global__ void k_gather(GatherArgs g, int64_t M, OutMap out, int accumulate, in
     double* p = out.at(a, b);
     *p = accumulate ? *p + v : v;
   }
+}
+
+// every lower block of a band (tile_off: the band's first block)
+__global__ void k_gather(GatherArgs g, int64_t M, OutMap out, int accumulate, int64_t tile_off) {
+  __shared__ int32_t rdA[32 * 8], rdB[32 * 8];
+  int64_t ti, tj;
+  tri_tile((int64_t)blockIdx.x + tile_off, &ti, &tj);
+  gather_block(g, M, out, accumulate, ti, tj, rdA, rdB);
+}
+
+// only the listed blocks, those whose row blocks share an ell bin (24% of the
+// lower blocks at the 10-bin workload), added to the stored values: no block
+// of the grid is spent on the others
+__global__ void k_gather_list(GatherArgs g, int64_t M, OutMap out, const uint32_t* __restrict__ list) {
+  __shared__ int32_t rdA[32 * 8], rdB[32 * 8];
+  const uint32_t pk = list[blockIdx.x];
+  gather_block(g, M, out, 1, (int64_t)(pk >> 16), (int64_t)(pk & 0xFFFFu), rdA, rdB);
 }
 
 // ---- Gaussian terms on the diagonal blocks ------------------------------------
@@ -367,6 +386,48 @@ static int gauss_blocks(cov_handle* h, cudaStream_t s) {
   return COV_OK;
 }
 
+// The 32 x 32 lower blocks whose two row blocks share an ell bin, in row-block
+// order, packed as (ti << 16) | tj, with the index of each row block's first
+// listed block on the host: the only blocks where the BB+PT and PB products
+// can be non-zero.  Built once per handle from the row table (the bins of each
+// row block as k_block_masks forms them) and uploaded on the stream of the
+// kernel that reads it.  Layouts with more than 64 ell bins or 65536 row
+// blocks keep the full grid.
+static int product_blocks(cov_handle* h, cudaStream_t s) {
+  if (h->plist || h->plist_off) return COV_OK;
+  const int64_t M = h->M, nb = (M + 31) / 32;
+  if (h->nl > 64 || nb > 65536) {
+    h->plist_off = true;
+    return COV_OK;
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  WL_CHECK(h, cudaStreamIsCapturing(s, &cap));
+  if (cap != cudaStreamCaptureStatusNone)
+    return wl_fail(h, COV_ERR_INVALID, "product-term block list not built before stream capture");
+  std::vector<uint64_t> bm((size_t)nb, 0);
+  for (int64_t a = 0; a < M; ++a) {
+    const int32_t* r = &h->rowdesc[8 * a];
+    uint64_t m = 1ull << r[1];
+    if (r[0] == 1) m |= (1ull << r[2]) | (1ull << r[3]);
+    bm[(size_t)(a / 32)] |= m;
+  }
+  std::vector<uint32_t> v;
+  h->plist_start.assign((size_t)nb + 1, 0);
+  for (int64_t ti = 0; ti < nb; ++ti) {
+    h->plist_start[(size_t)ti] = (int64_t)v.size();
+    for (int64_t tj = 0; tj <= ti; ++tj)
+      if (bm[(size_t)ti] & bm[(size_t)tj]) v.push_back((uint32_t)((ti << 16) | tj));
+  }
+  h->plist_start[(size_t)nb] = (int64_t)v.size();
+  int rc;
+  if ((rc = ensure(h, (void**)&h->plist, sizeof(uint32_t) * std::max<size_t>(v.size(), 1), "product-term block list")))
+    return rc;
+  if (!v.empty())
+    WL_CHECK(h, cudaMemcpyAsync(h->plist, v.data(), sizeof(uint32_t) * v.size(), cudaMemcpyHostToDevice, s));
+  // the pageable source is staged before the call returns, so v may go
+  return COV_OK;
+}
+
 // Gaussian terms of rows [r0, r1) (added; after the contraction and k_gather)
 static int gauss(cov_handle* h, const GatherArgs& g, int64_t r0, int64_t r1, OutMap out, cudaStream_t s) {
   if (!(g.terms & COV_TERM_G) || r1 <= r0) return COV_OK;
@@ -537,8 +598,15 @@ int wl_assemble_band(cov_handle* h, int64_t row0, int64_t nrows, OutMap out, uns
   GatherArgs g;
   if ((rc = gather_args(h, terms, &g, s))) return rc;
   const int acc = (terms & COV_TERM_1H) ? 1 : 0;
+  if (acc && (terms & (COV_TERM_BBPT | COV_TERM_PB)))
+    if ((rc = product_blocks(h, s))) return rc;
   auto gather = [&](int64_t r0, int64_t r1, cudaStream_t st) {
     int64_t t0 = r0 / 32, t1 = (r1 + 31) / 32;
+    if (acc && h->plist) {
+      const int64_t first = h->plist_start[(size_t)t0], last = h->plist_start[(size_t)t1];
+      if (last > first) k_gather_list<<<(unsigned)(last - first), dim3(32, 8), 0, st>>>(g, r1, out, h->plist + first);
+      return;
+    }
     int64_t off = t0 * (t0 + 1) / 2;
     k_gather<<<(unsigned)(t1 * (t1 + 1) / 2 - off), dim3(32, 8), 0, st>>>(g, r1, out, acc, off);
   };

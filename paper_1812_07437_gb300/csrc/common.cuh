@@ -158,6 +158,9 @@ struct cov_handle {
   uint64_t* bmask = nullptr;  // ell bins present in each 32-row block (the product terms skip the rest)
   bool bmask_ready = false;
   int4* gblk = nullptr;       // 32 x 32 sub-blocks of the Gaussian-term diagonal blocks, by first row
+  uint32_t* plist = nullptr;  // 32 x 32 lower blocks whose row blocks share an ell bin, (ti << 16) | tj
+  std::vector<int64_t> plist_start;  // (host) index of row block ti's first listed block; nb + 1 entries
+  bool plist_off = false;     // the list does not serve this layout (more than 64 ell bins or 65536 row blocks)
   std::vector<int64_t> gblk_row;  // (host) first row of each sub-block, ascending
   // launch orders of the tensor-core contraction, by tile-row range
   struct TileOrder {
