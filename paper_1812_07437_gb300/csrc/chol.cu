@@ -149,10 +149,26 @@ __global__ void __launch_bounds__(256) k_potrf_la(OutMap W, int64_t k0, int kb, 
     } else {
       const int tj = (NB - 1 - j) * (NB - j) / 2;        // active pairs: l > j
       const int skip = (NB - 2 - j) * (NB - 1 - j) / 2;  // (j + 1, j + 1): lane 0 of warp 0
-      for (int e = (int)threadIdx.x - 32; e < tj; e += (int)blockDim.x - 32) {
-        if (e == skip) continue;
-        const int pe = pr[e], i = pe & 255, l = pe >> 8;
-        L[i][l] -= L[i][j] * L[l][j];
+      const int nt = (int)blockDim.x - 32;
+      // four pairs per thread at once: their loads and FMAs overlap (one warp
+      // issues one FP64 instruction per 64 cycles, the latency of each)
+      for (int e0 = (int)threadIdx.x - 32; e0 < tj; e0 += 4 * nt) {
+        int ii[4], ll[4];
+        bool ok[4];
+        double acc[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int e = e0 + k * nt;
+          ok[k] = e < tj && e != skip;
+          const int pe = pr[ok[k] ? e : 0];
+          ii[k] = pe & 255;
+          ll[k] = pe >> 8;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[k] = fma(-L[ii[k]][j], L[ll[k]][j], L[ii[k]][ll[k]]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (ok[k]) L[ii[k]][ll[k]] = acc[k];
       }
     }
     __syncthreads();
