@@ -359,9 +359,9 @@ def launches_per_step(which_sizes, n_tri, split, packed=False, n_sub=8):
     snr = 0
     for ms in which_sizes:
         nb = (ms + 63) // 64
-        # pack, first panel (diagonal block, panel solve, slices), per further panel two update launches
-        # (look-ahead) and the next panel's three kernels, the last update, the prefix sums
-        snr += 1 + 3 + 5 * (nb - 1) + 1 + 1
+        # pack, first panel (diagonal block, then the panel solve fused with the slicing), per further panel
+        # two update launches (look-ahead) and the next panel's two kernels, the last update, the prefix sums
+        snr += 1 + 2 + 4 * (nb - 1) + 1 + 1
     return tables + counts + spectra + assemble + snr
 
 

@@ -774,31 +774,6 @@ size_t wl_chol_tc_bytes(int64_t n) {
   return (size_t)CS_S * pad * CS_K * 2 + (size_t)pad * sizeof(int);
 }
 
-// slices of rows sbase + i (i < pad) of the panel columns k0..k0+kb-1, zero for
-// rows outside [r0, r1) (the persistent kernel's 128-aligned layout)
-__global__ void k_chol_slice_abs(const OutMap W, int64_t k0, int kb, int64_t sbase, int64_t r0, int64_t r1,
-                                 int64_t pad, __nv_bfloat16* slices, int* rexp) {
-  int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  int lane = threadIdx.x & 31;
-  if (i >= pad) return;
-  const int64_t r = sbase + i;
-  double x0 = 0.0, x1 = 0.0;
-  if (r >= r0 && r < r1) {
-    const double* row = W.at(r, k0);
-    if (lane < kb) x0 = row[lane];
-    if (lane + 32 < kb) x1 = row[lane + 32];
-  }
-  double mx = fmax(fabs(x0), fabs(x1));
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  int e = 0;
-  if (mx > 0.0) frexp(mx, &e);
-  const size_t stride = (size_t)pad * CS_K;
-  __nv_bfloat16* out = slices + (size_t)i * CS_K;
-  slice_store(slice_int(x0, e), out + lane, stride);
-  slice_store(slice_int(x1, e), out + lane + 32, stride);
-  if (lane == 0) rexp[i] = e;
-}
-
 // The panel solve and the slicing in one pass, in the persistent update's
 // 128-aligned slice layout: each row sbase + i (i < pad) inside [r0, r1)
 // solves x L11^T = a by forward substitution, is written back, and is cut into
@@ -896,14 +871,7 @@ static int pu_num_sms() {
 int wl_chol_slice(cov_handle* h, OutMap W, int64_t k0, int kb, int64_t r0, int64_t r1, void* buf, cudaStream_t s) {
   int64_t n = r1 - r0;
   if (n <= 0) return COV_OK;
-  if (pu_usable(h, W)) {
-    const int64_t sbase = r0 / CS_BI * CS_BI, pad = (r1 - sbase + CS_BI - 1) / CS_BI * CS_BI;
-    __nv_bfloat16* slices = (__nv_bfloat16*)buf;
-    int* rexp = (int*)((uint8_t*)buf + (size_t)CS_S * pad * CS_K * 2);
-    k_chol_slice_abs<<<(unsigned)((pad + 7) / 8), 256, 0, s>>>(W, k0, kb, sbase, r0, r1, pad, slices, rexp);
-    WL_LAUNCH(h, "k_chol_slice_abs");
-    return COV_OK;
-  }
+  // (where the persistent kernel serves the workspace, wl_chol_trsm_slice cuts the slices)
   int64_t pad = (n + CS_BI - 1) / CS_BI * CS_BI;
   __nv_bfloat16* slices = (__nv_bfloat16*)buf;
   int* rexp = (int*)((uint8_t*)buf + (size_t)CS_S * pad * CS_K * 2);
